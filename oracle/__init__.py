@@ -1,0 +1,29 @@
+"""CPU oracle for the matrix-free Poisson operator of Kronbichler & Wall,
+"A performance comparison of continuous and discontinuous Galerkin methods
+with fast multigrid solvers" (arXiv:1611.03029).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this
+package: only the test suite, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it.  It
+shares no code, tables or helpers with the CUDA library in
+``paper_1611_03029_gb300``; the two meet only through the vector layouts
+documented in ``include/mfpoisson.h``.
+
+The oracle is deliberately plain: it assembles the stiffness matrix element
+by element from full 3D basis-function products at Gauss points (no sum
+factorisation), stores it as a sparse matrix and solves with textbook
+iterations, all in float64.  Every function cites the passage of the paper
+it follows.
+
+Modules
+  fem      reference element, mesh/mapping, cell and SIPG face assembly,
+           load vector, L2 error (Sec. 2, 2.1, 2.2; Eq. 4, 6, 7, 12)
+  mg       Jacobi diagonal, Chebyshev smoother, CG-Lanczos eigenvalue
+           estimate, transfer, coarse Chebyshev solve, V-cycle, PCG (Sec. 4.1)
+  adjoint  assembled coefficient derivative and dL/da (not in the paper)
+  rows     sampled rows of the operator for large meshes (Eq. 12)
+
+Parity status: every function is pinned by tests in tests/test_oracle_*.py
+except the mixed-precision V-cycle internals, which have no oracle at all
+(parity unpinned; only the final float64 residual is checked).
+"""
