@@ -1,0 +1,402 @@
+"""Benchmark of the GB300 matrix-free Poisson multigrid solver.
+
+Workload (default): continuous Q4 and SIPG DG_Q4 on 32^3 cells of the curved
+mesh x -> x + 0.1 sin(pi x) sin(pi y) sin(pi z), float64 throughout,
+manufactured sine right-hand side.  One step = one V-cycle preconditioned
+CG solve to 1e-10 relative residual of each discretization (every stage of
+the hot path: cell and face kernels, Jacobi-Chebyshev smoothing, transfer,
+coarse solve, fused CG updates and reductions).  `value` = dofs solved per
+second over both solves (float64); the JSON line also carries the operator
+apply throughput (MDoF/s) in float64 and float32 and the mixed-precision
+solve rate.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("MDoF/s operator apply; solve DoF/s to 1e-10 rel. residual, "
+          "FP64 vs mixed")
+N_CELLS, DEGREE, AMP = 32, 4, 0.1
+RTOL = 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=N_CELLS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", "-i", str(self.idx),
+                     "--query-gpu=" + self.QUERY,
+                     "--format=csv,noheader,nounits"],
+                    capture_output=True, text=True, timeout=5).stdout
+                for line in out.strip().splitlines():
+                    f = [x.strip() for x in line.split(",")]
+                    if len(f) >= 9:
+                        self.samples.append(f)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(s[1]) for s in self.samples if s[1].replace(
+            ".", "").isdigit())
+        mx = max(float(s[2]) for s in self.samples if s[2].replace(
+            ".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for nm, v in zip(names, s[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of one operator application
+# ---------------------------------------------------------------------------
+def apply_flops(disc, k, ncells, curved):
+    """Floating-point operations of one apply, counted from the algorithm:
+    12 sum-factorization sweeps of p^4 FMAs per cell, the quadrature-point
+    operation (21 flops curved, 5 Cartesian) and, for SIPG, the face work
+    (per face and side 15 p^3 FMAs Cartesian / 21 p^3 curved)."""
+    p = k + 1
+    cell = 2 * 12 * p ** 4 + (21 if curved else 5) * p ** 3 + 2 * p ** 3
+    if disc == "dg":
+        cell += 6 * 2 * (21 if curved else 15) * p ** 3
+    return float(cell) * ncells
+
+
+def apply_bytes(disc, k, n, curved, word=8):
+    """Compulsory DRAM bytes of one apply: source read, destination written
+    (CG: plus the zero fill), stored geometry (6 words per cell point) and,
+    for curved SIPG, 7 words per face point plus one per face."""
+    p = k + 1
+    ncells = n ** 3
+    ndofs = (n * k + 1) ** 3 if disc == "cg" else ncells * p ** 3
+    b = 2 * ndofs * word + (ndofs * word if disc == "cg" else 0)
+    if curved:
+        b += 6 * ncells * p ** 3 * word
+        if disc == "dg":
+            nf = 3 * n * n * (n + 1)
+            b += (7 * p * p + 1) * nf * word
+    return float(b)
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU baseline / reference arm): bounded sample of the workload
+# ---------------------------------------------------------------------------
+def oracle_sample_setup(n=8):
+    from oracle import fem, mg
+    out = []
+    for disc in ("cg", "dg"):
+        P = fem.Problem(n, n, n, DEGREE, disc=disc, mapping="sine", amp=AMP)
+        V = mg.VCycle(P)
+        b = fem.load_vector(P, fem.sine_forcing)
+        out.append((P, V, b))
+    return out
+
+
+def oracle_sample_solve(setup):
+    from oracle import mg
+    dofs = 0
+    its = []
+    for P, V, b in setup:
+        x, it, rr = mg.pcg(V.levels[-1].A, b, V.apply, rtol=RTOL)
+        dofs += P.n_dofs
+        its.append(it)
+    return dofs, its
+
+
+def cpu_baseline(n=8):
+    t0 = time.time()
+    setup = oracle_sample_setup(n)
+    t_setup = time.time() - t0
+    t0 = time.time()
+    dofs, its = oracle_sample_solve(setup)
+    t = time.time() - t0
+    return {"value": dofs / t, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": "oracle assembled-matrix V-cycle PCG to 1e-10, CG and "
+                      "SIPG Q4 on the same curved map with %d^3 cells "
+                      "(%d dofs, its %s); solve time only (setup %.1f s "
+                      "excluded, as on the GPU); scipy sparse products run "
+                      "on one thread" % (n, dofs, its, t_setup)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if world > 1 and rank != 0:
+        return
+    setup = oracle_sample_setup(8)
+    for _ in range(args.warmup):
+        oracle_sample_solve(setup)
+    times = []
+    dofs = 0
+    for _ in range(args.steps):
+        t0 = time.time()
+        dofs, its = oracle_sample_solve(setup)
+        times.append(time.time() - t0)
+    tm = sum(times) / len(times)
+    v = dofs / tm
+    line = {"metric": METRIC, "value": v, "unit": "DoF/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tm * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "Q4 CG + SIPG DG_Q4, curved sine map, "
+                       "8^3-cell bounded sample of the 32^3 workload",
+                       "cells": 8, "degree": DEGREE, "rtol": RTOL},
+            "cpu_baseline": {"value": v, "unit": "DoF/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "8^3 cells CG+SIPG Q4 curved, "
+                                       "solve only"},
+            "e2e": {"value": v, "unit": "DoF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    from paper_1611_03029_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    from paper_1611_03029_gb300 import mfpoisson as M
+
+    n = args.cells
+    stream = torch.cuda.current_stream()
+    ops = {}
+    for disc in ("cg", "dg"):
+        ops[disc] = M.Poisson(n, n, n, DEGREE, disc=disc, mapping="sine",
+                              map_param=AMP)
+    mixed = {disc: M.Poisson(n, n, n, DEGREE, disc=disc, mapping="sine",
+                             map_param=AMP, mg_precision="fp32")
+             for disc in ("cg", "dg")}
+    b = {d: ops[d].rhs(0) for d in ops}
+    x = {d: torch.empty_like(b[d]) for d in ops}
+    N = {d: ops[d].n_dofs() for d in ops}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
+                        device="cuda")
+
+    def step(opset):
+        its = {}
+        for d in ("cg", "dg"):
+            _, it, rel = opset[d].solve(b[d], x[d], rtol=RTOL, max_it=200)
+            its[d] = (it[0], rel[0])
+        return its
+
+    for _ in range(args.warmup):
+        step(ops)
+    # --- timed region: K steps, L2 flushed before each -------------------
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    _, _, l0 = ops["cg"].counters()
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        step_ms = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            its = step(ops)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    _, _, l1 = ops["cg"].counters()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    dofs_step = N["cg"] + N["dg"]
+    value = dofs_step * world / (ms * 1e-3)
+
+    # --- mixed-precision solve rate (same workload, float32 V-cycle) -----
+    for _ in range(2):
+        step(mixed)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+        enable_timing=True)
+    e0.record(stream)
+    its_mixed = step(mixed)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mixed_ms = e0.elapsed_time(e1)
+
+    # --- operator apply throughput, per kernel, CUDA events ---------------
+    apply = {}
+    for prec, opset, dt in (("f64", ops, torch.float64),
+                            ("f32", mixed, torch.float32)):
+        for d in ("cg", "dg"):
+            src = torch.randn(N[d], dtype=dt, device="cuda")
+            dst = torch.empty_like(src)
+            for _ in range(3):
+                opset[d].apply(src, dst)
+            reps = 20 if prec == "f64" else 50
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+                enable_timing=True)
+            flush.fill_(1.0)
+            a0.record(stream)
+            for _ in range(reps):
+                opset[d].apply(src, dst)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            t = a0.elapsed_time(a1) / reps * 1e-3
+            equiv = n ** 3 * DEGREE ** 3
+            apply[prec + "_" + d] = {
+                "ms": t * 1e3, "MDoF_s": N[d] / t / 1e6,
+                "equiv_MDoF_s": equiv / t / 1e6,
+                "GFLOP_s": apply_flops(d, DEGREE, n ** 3, True) / t / 1e9,
+                "GB_s": apply_bytes(d, DEGREE, n, True,
+                                    8 if prec == "f64" else 4) / t / 1e9}
+
+    # --- end to end through the C ABI with host buffers ------------------
+    hb = {d: b[d].cpu().pin_memory() for d in ops}
+    hx = {d: torch.empty(N[d], dtype=torch.float64).pin_memory() for d in ops}
+    db = {d: torch.empty_like(b[d]) for d in ops}
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for d in ("cg", "dg"):
+        db[d].copy_(hb[d], non_blocking=True)
+        ops[d].solve(db[d], x[d], rtol=RTOL, max_it=200)
+        hx[d].copy_(x[d], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = load_peaks()
+    # dominant kernel: the float64 SIPG apply (largest share of the step);
+    # float64 sum factorization is bound by the FP64 pipe ("alu").
+    fp64_peak = float(os.environ.get("MFP_FP64_PEAK_GFLOPS", "0")) or None
+    dom = apply["f64_dg"]
+    roof = {"kernel": "k_apply<P=5,double,DG,curved>", "bound": "alu",
+            "achieved": dom["GFLOP_s"] / 1e3, "peak": None,
+            "unit": "TFLOP/s", "frac": None, "traffic": None,
+            "peak_source": "FP64 pipe peak from the unit-count derivation"}
+    if fp64_peak:
+        roof["peak"] = fp64_peak / 1e3
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "CG Q4 + SIPG DG_Q4 V-cycle PCG solves to "
+                   "1e-10, 32^3 cells, curved map amplitude 0.1",
+                   "cells": n, "degree": DEGREE, "dofs_cg": N["cg"],
+                   "dofs_dg": N["dg"], "rtol": RTOL,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iterations": {d: its[d][0] for d in its},
+        "solve_ms": None,
+        "mixed": {"ms_per_step": mixed_ms,
+                  "value": dofs_step / (mixed_ms * 1e-3),
+                  "iterations": {d: its_mixed[d][0] for d in its_mixed},
+                  "speedup_vs_fp64": ms / mixed_ms},
+        "apply": apply,
+        "roofline": roof,
+        "e2e": {"value": dofs_step / (e2e_ms * 1e-3), "unit": "DoF/s",
+                "h2d_bytes_per_step": 8 * dofs_step,
+                "d2h_bytes_per_step": 8 * dofs_step},
+        "gpu_launches": int((l1 - l0) // max(args.steps, 1)),
+        "gpu_launches_scope": "per timed step",
+        "clocks": clk.summary(),
+        "peaks": {"hbm_gbs": peaks.get("hbm_gbs")},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(8)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * mfpoisson.h - C ABI of the GB300 matrix-free high-order Poisson library.
+ *
+ * The library evaluates the operator of -div(kappa grad u) = f (Sec. 2,
+ * Eq. 1) on a structured hexahedral brick of the unit cube without
+ * assembling a matrix: cell integrals by sum factorization (Sec. 3, Eq. 12)
+ * for continuous Q_k elements (Sec. 2.1, Eq. 4) and for the symmetric
+ * interior penalty DG method (Sec. 2.2, Eq. 6, boundary extension Eq. 7),
+ * and solves with CG preconditioned by a geometric multigrid V-cycle with
+ * Chebyshev-Jacobi smoothing (Sec. 4.1).
+ *
+ * General conventions
+ *  - Every pointer argument named *_dev is DEVICE memory on the context's
+ *    device, owned by the caller, contiguous, aligned to at least 16 bytes,
+ *    and must stay valid until the work queued on `stream` has finished.
+ *    Pointers named *_host are host memory read or written before return.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is queued asynchronously unless stated otherwise.
+ *  - Every call returns an mfp_status.  On failure nothing is written to
+ *    the outputs that the status does not describe, and the message is
+ *    available from mfp_last_error() (per thread).
+ *  - The library owns all level data (geometry, diagonals, scratch) and
+ *    frees it in mfp_destroy().
+ *
+ * Vector layouts (level l of a context; level n_levels-1 is the finest)
+ *  - cells c = cx + nx*(cy + ny*cz), cell size 1/nx x 1/ny x 1/nz;
+ *  - local node / quadrature point a = ax + p*ay + p*p*az, p = k+1, x fastest;
+ *  - CG (disc = MFP_CG): one value per node of the (nx k+1)(ny k+1)(nz k+1)
+ *    grid, x fastest; boundary nodes are present and carry the identity
+ *    rows / columns of the eliminated Dirichlet conditions (Sec. 2.1);
+ *  - SIPG (disc = MFP_SIPG): cell-major blocks of p^3 nodal values;
+ *  - batched vectors (n_rhs = R > 1): entry (i, r) at [i*R + r];
+ *  - cell coefficient / gradient: [ncells][p^3] in local quadrature order;
+ *  - face coefficient / gradient: all x-normal faces, then y-, then
+ *    z-normal ones; inside one direction lexicographic (x fastest) over the
+ *    (n_x+dx) x (n_y+dy) x (n_z+dz) face grid, d* = 1 on the normal axis;
+ *    p^2 points per face, q = qa + p*qb with a < b the tangential axes.
+ *  - the nodal basis is Lagrange in the Gauss-Lobatto points, quadrature is
+ *    the (k+1)-point Gauss rule per direction (Sec. 2.1, Sec. 3).
+ */
+#ifndef MFPOISSON_H
+#define MFPOISSON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mfp_ctx mfp_ctx;
+
+typedef enum {
+  MFP_OK = 0,
+  MFP_ERR_ARG = -1,           /* invalid argument; nothing was queued      */
+  MFP_ERR_CUDA = -2,          /* a CUDA call failed; context still usable
+                                 unless the CUDA error is sticky           */
+  MFP_ERR_OOM = -3,           /* device allocation failed                  */
+  MFP_ERR_NOT_CONVERGED = -4, /* solve hit max_it; outputs hold the last
+                                 iterate, iteration count and residual     */
+  MFP_ERR_STATE = -6          /* call not valid for this context           */
+} mfp_status;
+
+enum { MFP_CG = 0, MFP_SIPG = 1 };
+enum { MFP_FP64 = 0, MFP_FP32 = 1, MFP_MIXED = 2 };
+enum { MFP_MAP_IDENTITY = 0, MFP_MAP_SINE = 1 };
+
+typedef struct {
+  int nx, ny, nz;        /* fine-level cells per axis (>= 1)                */
+  int degree;            /* k in 1..8                                      */
+  int disc;              /* MFP_CG or MFP_SIPG                              */
+  int n_levels;          /* multigrid levels; 0 = halve while every count
+                            is even and >= 4 (coarsest has >= 2 cells/axis);
+                            each coarsening needs all counts even          */
+  int mapping;           /* MFP_MAP_IDENTITY: affine brick (one Jacobian per
+                            level); MFP_MAP_SINE: x -> x + map_param
+                            sin(pi x) sin(pi y) sin(pi z) (1,1,1), degree-k
+                            isoparametric interpolation through the
+                            Gauss-Lobatto support points (Sec. 2)           */
+  double map_param;      /* amplitude for MFP_MAP_SINE (|amp| < 1/(pi sqrt 3)) */
+  double kappa;          /* constant coefficient (> 0) until
+                            mfp_set_coefficient is called                   */
+  double penalty_factor; /* SIPG: sigma_F = penalty_factor (k+1)^2 / h_F with
+                            1/h_F = (|F|/|K-| + |F|/|K+|)/2 (|F|/|K| on the
+                            boundary); Sec. 2.2 (paper value: 3)            */
+  int mg_precision;      /* V-cycle arithmetic: MFP_FP64 or MFP_FP32; the
+                            outer CG, its residuals and dot products are
+                            always float64 (MFP_MIXED is a synonym of FP32) */
+  int cheb_degree;       /* Chebyshev smoother degree (Sec. 4.1: 5)         */
+  int eig_cg_iters;      /* CG iterations of the eigenvalue estimate (15)   */
+} mfp_desc;
+
+/* Fill `desc` with the defaults (1 cell, k=1, CG, identity map, kappa 1,
+ * penalty_factor 1, FP64 V-cycle, Chebyshev degree 5, 15 CG iterations). */
+void mfp_desc_default(mfp_desc* desc);
+
+/* Create a context on the current CUDA device: builds every multigrid level
+ * (geometry at quadrature points, inverse Jacobi diagonal, eigenvalue
+ * estimates and Chebyshev parameters; Sec. 4.1 "setup").  Synchronises
+ * `stream`.  *out receives an opaque handle owned by the library. */
+mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out);
+
+/* Free all device and host memory of the context (synchronises the device
+ * work of the context first).  NULL is accepted. */
+mfp_status mfp_destroy(mfp_ctx* ctx);
+
+/* Number of levels of the context. */
+int mfp_n_levels(const mfp_ctx* ctx);
+
+/* Sizes on `level` (0 = coarsest): dofs, cell quadrature points
+ * (ncells p^3) and face quadrature points (nfaces p^2).  NULL outputs are
+ * skipped. */
+mfp_status mfp_sizes(const mfp_ctx* ctx, int level, int64_t* n_dofs,
+                     int64_t* n_cell_qp, int64_t* n_face_qp);
+
+/* Replace the coefficient by per-quadrature-point values on the finest
+ * level: a_cell_dev [ncells][p^3], a_face_dev [nfaces][p^2] (the face
+ * values are used by the SIPG face terms and may be NULL for CG).  All
+ * values must be > 0.  Coarser levels receive the quadrature-weighted mean
+ * over the children of each coarse cell / coarse face; every level's
+ * geometry, diagonal and eigenvalue estimate are rebuilt.  Synchronises. */
+mfp_status mfp_set_coefficient(mfp_ctx* ctx, const double* a_cell_dev,
+                               const double* a_face_dev, void* stream);
+
+/* Load vector b_i = sum_q w_q det J f(x_q) phi_i(x_q) on the finest level
+ * (Eq. 4 / Eq. 6 right-hand side, homogeneous Dirichlet data), written to
+ * b_dev[i * stride] (stride >= 1, e.g. R for column r of a batch when the
+ * pointer is offset by r).  f_kind 0: f = 3 pi^2 sin(pi x) sin(pi y)
+ * sin(pi z) (params unused); f_kind 1: f = sum_j A_j exp(-|x - c_j|^2 /
+ * w_j^2) with params_host = n_terms blocks (c_x, c_y, c_z, w, A).  Zero on
+ * constrained (CG boundary) dofs. */
+mfp_status mfp_rhs(mfp_ctx* ctx, int f_kind, const double* params_host,
+                   int n_terms, double* b_dev, int64_t stride, void* stream);
+
+/* dst = A src on `level` (Eq. 12, plus the SIPG face terms of Eq. 6/7 and
+ * identity rows / columns for CG Dirichlet nodes).  prec MFP_FP64 takes
+ * double vectors, MFP_FP32 float vectors (FP32 level data must exist, i.e.
+ * mg_precision FP32).  n_rhs = R >= 1 applies to R right-hand sides in the
+ * batched layout in one launch.  src and dst must not alias. */
+mfp_status mfp_apply(mfp_ctx* ctx, int level, int prec, const void* src_dev,
+                     void* dst_dev, int n_rhs, void* stream);
+
+/* Inverse of diag(A) on `level` in precision `prec` (copied to diag_dev,
+ * n_dofs values): the Jacobi diagonal of Sec. 4.1, 1 on constrained dofs. */
+mfp_status mfp_inverse_diagonal(mfp_ctx* ctx, int level, int prec,
+                                void* diag_dev, void* stream);
+
+/* Eigenvalue estimates of D^{-1}A on `level` from the Lanczos tridiagonal of
+ * `eig_cg_iters` Jacobi-PCG steps (Sec. 4.1), and the Chebyshev interval
+ * [lo, hi] and degree used there (coarsest level: coarse solve). */
+mfp_status mfp_level_info(const mfp_ctx* ctx, int level, double* lam_max,
+                          double* lam_min, double* cheb_lo, double* cheb_hi,
+                          int* cheb_degree);
+
+/* Transfer between level `level` (fine) and level-1 (coarse): prolongation
+ * (geometric embedding of the coarse Q_k space, Sec. 4.1) or restriction
+ * (its transpose).  Vectors in precision `prec`; single right-hand side. */
+mfp_status mfp_prolongate(mfp_ctx* ctx, int level, int prec,
+                          const void* coarse_dev, void* fine_dev,
+                          void* stream);
+mfp_status mfp_restrict(mfp_ctx* ctx, int level, int prec,
+                        const void* fine_dev, void* coarse_dev, void* stream);
+
+/* Chebyshev-Jacobi smoother of `level` (Sec. 4.1): x <- smoothed iterate for
+ * A x = b.  zero_start != 0 ignores the input x (x0 = 0, first update
+ * without an operator application).  On the coarsest level this is the
+ * coarse solve. */
+mfp_status mfp_smooth(mfp_ctx* ctx, int level, int prec, const void* b_dev,
+                      void* x_dev, int zero_start, void* stream);
+
+/* One V-cycle z = B r on the finest level (Sec. 4.1), float64 in and out;
+ * the internal arithmetic is the context's mg_precision. */
+mfp_status mfp_vcycle(mfp_ctx* ctx, const double* r_dev, double* z_dev,
+                      int n_rhs, void* stream);
+
+/* CG preconditioned by one V-cycle from x = 0 (Sec. 4.1) for A x = b on the
+ * finest level, float64 residuals, dot products and stopping test
+ * ||b - A x||_2 <= rtol ||b||_2 (recursively updated residual), for n_rhs
+ * independent right-hand sides in the batched layout (each column stops on
+ * its own).  Synchronises `stream` once per iteration.  iters_host[n_rhs] and
+ * relres_host[n_rhs] receive the iteration counts and final relative
+ * residuals (may be NULL).  Returns MFP_ERR_NOT_CONVERGED if any column hit
+ * max_it. */
+mfp_status mfp_solve(mfp_ctx* ctx, const double* b_dev, double* x_dev,
+                     int n_rhs, double rtol, int max_it, int* iters_host,
+                     double* relres_host, void* stream);
+
+/* Gradient of L = 0.5 |u - u_t|^2 subject to A(a) u = f with respect to
+ * the per-quadrature-point coefficient a, given the forward solution u and
+ * the adjoint solution lambda of A lambda = u - u_t (A is symmetric):
+ *   dL/da_q = -lambda^T (dA/da_q) u,
+ * i.e. -w_q det J (J^{-T} grad lambda).(J^{-T} grad u) at cell points and
+ * minus the SIPG face form (Eq. 6/7) with kappa replaced by the point's
+ * indicator at face points.  g_cell_dev [ncells][p^3]; g_face_dev
+ * [nfaces][p^2] (SIPG only; may be NULL for CG).  Not in the paper. */
+mfp_status mfp_gradient(mfp_ctx* ctx, const double* u_dev,
+                        const double* lambda_dev, double* g_cell_dev,
+                        double* g_face_dev, void* stream);
+
+/* Counters: operator applications per level since creation (array of
+ * mfp_n_levels entries), V-cycles since creation, and the number of CUDA
+ * kernels this library has launched in the process.  NULL outputs are
+ * skipped. */
+mfp_status mfp_counters(const mfp_ctx* ctx, int64_t* applies_per_level,
+                        int64_t* vcycles, int64_t* kernel_launches);
+
+/* Last error message of the calling thread ("" if none). */
+const char* mfp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFPOISSON_H */

@@ -1,0 +1,773 @@
+// C ABI of the library: context and multigrid levels (Sec. 4.1 setup),
+// operator application, transfer, Chebyshev smoothing, V-cycle and the
+// V-cycle preconditioned CG (Sec. 4.1), host orchestration on one stream.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <atomic>
+#include <new>
+
+#include "mfp_internal.h"
+
+namespace mfp {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+void clear_error() { g_err.clear(); }
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+template <typename T>
+T* dalloc(int64_t n) {
+  void* p = nullptr;
+  if (n <= 0) n = 1;
+  MFP_CHECK_CUDA(cudaMalloc(&p, (size_t)n * sizeof(T)));
+  return static_cast<T*>(p);
+}
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+void dfree(void*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+cudaStream_t st(void* s) { return static_cast<cudaStream_t>(s); }
+
+int cpb_override() {
+  const char* e = std::getenv("MFP_CELLS_PER_BLOCK");
+  return e ? std::atoi(e) : 0;
+}
+
+template <typename T>
+void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
+                 cudaStream_t s) {
+  LevelData<T>& D = level_data<T>(L);
+  MFP_REQUIRE(D.valid, "level data of this precision was not built "
+                       "(mg_precision must be MFP_FP32 for float applies)");
+  if (L.disc == MFP_CG)
+    MFP_CHECK_CUDA(
+        cudaMemsetAsync(dst, 0, (size_t)L.ndofs * R * sizeof(T), s));
+  for (int r = 0; r < R; ++r) {
+    if (L.disc == MFP_CG)
+      launch_apply_cg(L, D, src, dst, R, r, cpb_override(), s);
+    else
+      launch_apply_dg(L, D, src, dst, R, r, cpb_override(), s);
+  }
+  L.applies += R;
+  (void)c;
+}
+
+void cheb_coeffs_first(const Level& L, double& c) {
+  const double theta = 0.5 * (L.cheb_hi + L.cheb_lo);
+  c = 1.0 / theta;
+}
+
+// Chebyshev smoother / coarse solve on level l (Sec. 4.1).
+template <typename T>
+void smooth(mfp_ctx* c, int l, const T* b, T* x, bool zero, int R,
+            cudaStream_t s) {
+  Level& L = c->levels[l];
+  LevelData<T>& D = level_data<T>(L);
+  T* res = static_cast<T*>(L.t_res);
+  T* d = static_cast<T*>(L.t_d);
+  const double theta = 0.5 * (L.cheb_hi + L.cheb_lo);
+  const double delta = 0.5 * (L.cheb_hi - L.cheb_lo);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  if (zero) {
+    launch_cheb_first<T>(b, D.dinv, d, x, nullptr, 1.0 / theta, L.ndofs, R,
+                         s);
+  } else {
+    apply_level<T>(c, L, x, res, R, s);
+    launch_cheb_first<T>(b, D.dinv, d, x, res, 1.0 / theta, L.ndofs, R, s);
+  }
+  for (int i = 1; i < L.cheb_degree; ++i) {
+    apply_level<T>(c, L, x, res, R, s);
+    const double rho1 = 1.0 / (2.0 * sigma - rho);
+    launch_cheb_step<T>(b, D.dinv, d, x, res, rho1 * rho, 2.0 * rho1 / delta,
+                        L.ndofs, R, s);
+    rho = rho1;
+  }
+}
+
+template <typename T>
+void prolongate(mfp_ctx* c, int l, const T* xc, T* xf, int R,
+                cudaStream_t s) {
+  for (int r = 0; r < R; ++r)
+    launch_prolongate<T>(c->levels[l], c->levels[l - 1], xc, xf, R, r, s);
+}
+template <typename T>
+void restrict_(mfp_ctx* c, int l, const T* xf, T* xc, int R, cudaStream_t s) {
+  for (int r = 0; r < R; ++r)
+    launch_restrict<T>(c->levels[l], c->levels[l - 1], xf, xc, R, r, s);
+}
+
+// V-cycle on level l for A x = b, x overwritten (zero initial guess).
+template <typename T>
+void vcycle_level(mfp_ctx* c, int l, const T* b, T* x, int R,
+                  cudaStream_t s) {
+  Level& L = c->levels[l];
+  if (l == 0) {
+    smooth<T>(c, 0, b, x, true, R, s);
+    return;
+  }
+  Level& C = c->levels[l - 1];
+  T* res = static_cast<T*>(L.t_res);
+  smooth<T>(c, l, b, x, true, R, s);
+  apply_level<T>(c, L, x, res, R, s);
+  launch_residual<T>(b, res, res, L.ndofs * R, s);
+  restrict_<T>(c, l, res, static_cast<T*>(C.t_b), R, s);
+  vcycle_level<T>(c, l - 1, static_cast<const T*>(C.t_b),
+                  static_cast<T*>(C.t_x), R, s);
+  prolongate<T>(c, l, static_cast<const T*>(C.t_x), res, R, s);
+  launch_axpy<T>(x, res, 1.0, L.ndofs * R, s);
+  smooth<T>(c, l, b, x, false, R, s);
+}
+
+void ensure_scratch(mfp_ctx* c, int R) {
+  MFP_REQUIRE(R >= 1 && R <= kMaxRhs, "n_rhs must be in 1..256");
+  const size_t vb = c->vprec == MFP_FP32 ? sizeof(float) : sizeof(double);
+  for (size_t l = 0; l < c->levels.size(); ++l) {
+    Level& L = c->levels[l];
+    if (L.scratch_rhs >= R) continue;
+    dfree(L.t_res);
+    dfree(L.t_d);
+    dfree(L.t_x);
+    dfree(L.t_b);
+    const size_t bytes = (size_t)L.ndofs * R * vb;
+    MFP_CHECK_CUDA(cudaMalloc(&L.t_res, bytes));
+    MFP_CHECK_CUDA(cudaMalloc(&L.t_d, bytes));
+    MFP_CHECK_CUDA(cudaMalloc(&L.t_x, bytes));
+    MFP_CHECK_CUDA(cudaMalloc(&L.t_b, bytes));
+    L.scratch_rhs = R;
+  }
+  if (c->cg_rhs < R) {
+    const int64_t n = c->levels.back().ndofs * (int64_t)R;
+    dfree(c->cg_r);
+    dfree(c->cg_p);
+    dfree(c->cg_ap);
+    dfree(c->cg_z);
+    dfree(c->mix_r);
+    dfree(c->mix_z);
+    c->cg_r = dalloc<double>(n);
+    c->cg_p = dalloc<double>(n);
+    c->cg_ap = dalloc<double>(n);
+    c->cg_z = dalloc<double>(n);
+    if (c->vprec == MFP_FP32) {
+      c->mix_r = dalloc<float>(n);
+      c->mix_z = dalloc<float>(n);
+    }
+    c->cg_rhs = R;
+  }
+}
+
+// V-cycle on the finest level, float64 in / out.
+void vcycle_top(mfp_ctx* c, const double* r, double* z, int R,
+                cudaStream_t s) {
+  const int top = (int)c->levels.size() - 1;
+  const int64_t n = c->levels[top].ndofs * (int64_t)R;
+  if (c->vprec == MFP_FP32) {
+    launch_to_float(r, c->mix_r, n, s);
+    vcycle_level<float>(c, top, c->mix_r, c->mix_z, R, s);
+    launch_to_double(c->mix_z, z, n, s);
+  } else {
+    vcycle_level<double>(c, top, r, z, R, s);
+  }
+  c->vcycles += R;
+}
+
+// Eigenvalue estimate of D^{-1} A on level l (Sec. 4.1): Jacobi-PCG from the
+// start vector, Lanczos tridiagonal, bisection; all on the device.
+void estimate_eigenvalues(mfp_ctx* c, int l, cudaStream_t s) {
+  Level& L = c->levels[l];
+  const int64_t n = L.ndofs;
+  double* r = c->cg_r;
+  double* z = c->cg_z;
+  double* p = c->cg_p;
+  double* ap = c->cg_ap;
+  double init[S_COUNT] = {0};
+  init[S_ACTIVE] = 1.0;
+  MFP_CHECK_CUDA(cudaMemcpyAsync(c->scal, init, sizeof(init),
+                                 cudaMemcpyHostToDevice, s));
+  launch_start_vector(L, r, s);
+  launch_jacobi(r, L.d64.dinv, z, n, 1, s);
+  MFP_CHECK_CUDA(cudaMemcpyAsync(p, z, n * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, s));
+  launch_dot(r, z, n, 1, c->red, c->scal, 0, nullptr, 0, s);
+  const int iters = c->desc.eig_cg_iters;
+  for (int j = 0; j < iters; ++j) {
+    apply_level<double>(c, L, p, ap, 1, s);
+    launch_dot(p, ap, n, 1, c->red, c->scal, 1, c->hist, j, s);
+    launch_cg_update(nullptr, r, p, ap, n, 1, c->red, c->scal, s);
+    launch_jacobi(r, L.d64.dinv, z, n, 1, s);
+    launch_dot(r, z, n, 1, c->red, c->scal, 2, c->hist, j, s);
+    launch_cg_p(p, z, n, 1, c->scal, s);
+  }
+  launch_lanczos(c->hist, c->scal, c->eig_out, s);
+  double out[2];
+  MFP_CHECK_CUDA(cudaMemcpyAsync(out, c->eig_out, sizeof(out),
+                                 cudaMemcpyDeviceToHost, s));
+  MFP_CHECK_CUDA(cudaStreamSynchronize(s));
+  L.lam_max = std::isfinite(out[0]) && out[0] > 0 ? out[0] : 1.0;
+  L.lam_min = std::isfinite(out[1]) && out[1] > 0 ? out[1] : L.lam_max;
+  if (l == 0) {
+    L.cheb_lo = 0.9 * L.lam_min;
+    L.cheb_hi = 1.2 * L.lam_max;
+    const double cond = L.cheb_hi / L.cheb_lo;
+    const double rho = (std::sqrt(cond) - 1.0) / (std::sqrt(cond) + 1.0);
+    int m = 1;
+    while (2.0 * std::pow(rho, m) / (1.0 + std::pow(rho, 2 * m)) >= 1e-3 &&
+           m < 10000)
+      ++m;
+    L.cheb_degree = m;
+  } else {
+    L.cheb_hi = 1.2 * L.lam_max;
+    L.cheb_lo = 0.06 * L.lam_max;
+    L.cheb_degree = c->desc.cheb_degree;
+  }
+  L.applies = 0;
+}
+
+void free_level(Level& L) {
+  for (LevelData<double>* D : {&L.d64}) {
+    dfree(D->G);
+    dfree(D->kcell);
+    dfree(D->kface);
+    dfree(D->fdata);
+    dfree(D->sigma);
+    dfree(D->dinv);
+  }
+  dfree(L.d32.G);
+  dfree(L.d32.kcell);
+  dfree(L.d32.kface);
+  dfree(L.d32.fdata);
+  dfree(L.d32.sigma);
+  dfree(L.d32.dinv);
+  dfree(L.vol);
+  dfree(L.t_res);
+  dfree(L.t_d);
+  dfree(L.t_x);
+  dfree(L.t_b);
+}
+
+void free_ctx(mfp_ctx* c) {
+  for (auto& L : c->levels) free_level(L);
+  dfree(c->cg_r);
+  dfree(c->cg_p);
+  dfree(c->cg_ap);
+  dfree(c->cg_z);
+  dfree(c->scal);
+  dfree(c->hist);
+  dfree(c->eig_out);
+  dfree(c->params);
+  dfree(c->red.part);
+  dfree(c->red.cnt);
+  dfree(c->mix_r);
+  dfree(c->mix_z);
+  if (c->host_scal) cudaFreeHost(c->host_scal);
+  c->host_scal = nullptr;
+}
+
+void to_float_array(const double* a, float*& b, int64_t n, cudaStream_t s) {
+  if (!a) return;
+  if (!b) b = dalloc<float>(n);
+  launch_to_float(a, b, n, s);
+}
+
+// Geometry, diagonal and eigenvalue estimate of every level.
+void build_levels(mfp_ctx* c, cudaStream_t s) {
+  const bool f32 = c->vprec == MFP_FP32;
+  for (size_t l = 0; l < c->levels.size(); ++l) {
+    Level& L = c->levels[l];
+    const int64_t P3 = (int64_t)L.p * L.p * L.p, P2 = (int64_t)L.p * L.p;
+    if (L.curved) {
+      if (!L.d64.G) L.d64.G = dalloc<double>(L.ncells * 6 * P3);
+      if (f32 && !L.d32.G) L.d32.G = dalloc<float>(L.ncells * 6 * P3);
+      if (!L.vol) L.vol = dalloc<double>(L.ncells);
+      launch_curved_cell_geometry(L, s);
+      if (L.disc == MFP_SIPG) {
+        if (!L.d64.fdata) L.d64.fdata = dalloc<double>(L.nfaces * 7 * P2);
+        if (!L.d64.sigma) L.d64.sigma = dalloc<double>(L.nfaces);
+        if (f32 && !L.d32.fdata) L.d32.fdata = dalloc<float>(L.nfaces * 7 * P2);
+        if (f32 && !L.d32.sigma) L.d32.sigma = dalloc<float>(L.nfaces);
+        launch_curved_face_geometry(L, s);
+      }
+    }
+    if (f32) {
+      to_float_array(L.d64.kcell, L.d32.kcell, L.ncells * P3, s);
+      to_float_array(L.d64.kface, L.d32.kface, L.nfaces * P2, s);
+    }
+    if (!L.d64.dinv) L.d64.dinv = dalloc<double>(L.ndofs);
+    launch_diagonal(L, L.d64.dinv, s);
+    launch_invert_diag(L, L.d64.dinv, s);
+    L.d64.valid = true;
+    if (f32) {
+      to_float_array(L.d64.dinv, L.d32.dinv, L.ndofs, s);
+      L.d32.valid = true;
+    }
+    estimate_eigenvalues(c, (int)l, s);
+  }
+  MFP_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+mfp_status guard_status(const Fail& f) { return f.st; }
+
+#define API_BEGIN \
+  try {           \
+    ::mfp::clear_error();
+#define API_END                                                      \
+  }                                                                  \
+  catch (const ::mfp::Fail& f) {                                     \
+    return f.st;                                                     \
+  }                                                                  \
+  catch (const std::bad_alloc&) {                                    \
+    ::mfp::set_error("host allocation failed");                      \
+    return MFP_ERR_OOM;                                              \
+  }                                                                  \
+  catch (...) {                                                      \
+    ::mfp::set_error("unexpected exception");                        \
+    return MFP_ERR_CUDA;                                             \
+  }                                                                  \
+  return MFP_OK;
+
+Level& get_level(mfp_ctx* c, int level) {
+  MFP_REQUIRE(c, "null context");
+  MFP_REQUIRE(level >= 0 && level < (int)c->levels.size(),
+              "level out of range");
+  return c->levels[level];
+}
+
+int prec_of(int prec) {
+  MFP_REQUIRE(prec == MFP_FP64 || prec == MFP_FP32 || prec == MFP_MIXED,
+              "prec must be MFP_FP64 or MFP_FP32");
+  return prec == MFP_FP64 ? MFP_FP64 : MFP_FP32;
+}
+
+}  // namespace
+}  // namespace mfp
+
+using namespace mfp;
+
+extern "C" {
+
+void mfp_desc_default(mfp_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->nx = d->ny = d->nz = 1;
+  d->degree = 1;
+  d->disc = MFP_CG;
+  d->n_levels = 0;
+  d->mapping = MFP_MAP_IDENTITY;
+  d->map_param = 0.0;
+  d->kappa = 1.0;
+  d->penalty_factor = 1.0;
+  d->mg_precision = MFP_FP64;
+  d->cheb_degree = 5;
+  d->eig_cg_iters = 15;
+}
+
+const char* mfp_last_error(void) { return g_err.c_str(); }
+
+mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out) {
+  mfp_ctx* c = nullptr;
+  try {
+    clear_error();
+    MFP_REQUIRE(desc && out, "null argument");
+    *out = nullptr;
+    const mfp_desc& d = *desc;
+    MFP_REQUIRE(d.nx >= 1 && d.ny >= 1 && d.nz >= 1, "cell counts must be >= 1");
+    MFP_REQUIRE(d.degree >= 1 && d.degree <= 8, "degree must be in 1..8");
+    MFP_REQUIRE(d.disc == MFP_CG || d.disc == MFP_SIPG, "unknown disc");
+    MFP_REQUIRE(d.mapping == MFP_MAP_IDENTITY || d.mapping == MFP_MAP_SINE,
+                "unknown mapping");
+    MFP_REQUIRE(d.mapping != MFP_MAP_SINE ||
+                    std::fabs(d.map_param) * 3.14159265358979 * std::sqrt(3.0) < 1.0,
+                "map_param too large: the mapping would fold");
+    MFP_REQUIRE(d.kappa > 0, "kappa must be > 0");
+    MFP_REQUIRE(d.penalty_factor > 0, "penalty_factor must be > 0");
+    MFP_REQUIRE(d.cheb_degree >= 1 && d.cheb_degree <= 64,
+                "cheb_degree must be in 1..64");
+    MFP_REQUIRE(d.eig_cg_iters >= 1 && d.eig_cg_iters <= 64,
+                "eig_cg_iters must be in 1..64");
+    MFP_REQUIRE(d.mg_precision == MFP_FP64 || d.mg_precision == MFP_FP32 ||
+                    d.mg_precision == MFP_MIXED,
+                "unknown mg_precision");
+    const int64_t cells = (int64_t)d.nx * d.ny * d.nz;
+    const int64_t p3 = (int64_t)(d.degree + 1) * (d.degree + 1) * (d.degree + 1);
+    MFP_REQUIRE(cells * p3 < (int64_t)1 << 31, "mesh too large");
+    // level count
+    int nl = d.n_levels;
+    int n0 = d.nx, n1 = d.ny, n2 = d.nz;
+    if (nl <= 0) {
+      nl = 1;
+      while (n0 % 2 == 0 && n1 % 2 == 0 && n2 % 2 == 0 && n0 >= 4 && n1 >= 4 &&
+             n2 >= 4) {
+        n0 /= 2;
+        n1 /= 2;
+        n2 /= 2;
+        ++nl;
+      }
+    } else {
+      for (int i = 1; i < nl; ++i) {
+        MFP_REQUIRE(n0 % 2 == 0 && n1 % 2 == 0 && n2 % 2 == 0,
+                    "cell counts cannot be halved n_levels-1 times");
+        n0 /= 2;
+        n1 /= 2;
+        n2 /= 2;
+      }
+    }
+    c = new mfp_ctx();
+    c->desc = d;
+    c->vprec = d.mg_precision == MFP_FP64 ? MFP_FP64 : MFP_FP32;
+    MFP_CHECK_CUDA(cudaGetDevice(&c->device));
+    c->levels.resize(nl);
+    for (int l = 0; l < nl; ++l) {
+      Level& L = c->levels[l];
+      const int sh = nl - 1 - l;
+      L.n[0] = d.nx >> sh;
+      L.n[1] = d.ny >> sh;
+      L.n[2] = d.nz >> sh;
+      L.k = d.degree;
+      L.p = d.degree + 1;
+      L.disc = d.disc;
+      L.curved = d.mapping == MFP_MAP_SINE && d.map_param != 0.0;
+      L.map_amp = L.curved ? d.map_param : 0.0;
+      L.kappa = d.kappa;
+      L.penalty = d.penalty_factor;
+      L.ncells = (int64_t)L.n[0] * L.n[1] * L.n[2];
+      for (int e = 0; e < 3; ++e) {
+        L.gdim[e] = L.n[e] * L.k + 1;
+        L.h[e] = 1.0 / L.n[e];
+      }
+      L.ndofs = d.disc == MFP_CG ? (int64_t)L.gdim[0] * L.gdim[1] * L.gdim[2]
+                                 : L.ncells * L.p * L.p * L.p;
+      int64_t off = 0;
+      for (int e = 0; e < 3; ++e) {
+        int m[3] = {L.n[0], L.n[1], L.n[2]};
+        m[e] += 1;
+        L.face_off[e] = (int)off;
+        off += (int64_t)m[0] * m[1] * m[2];
+      }
+      L.nfaces = off;
+    }
+    c->scal = dalloc<double>((int64_t)S_COUNT * kMaxRhs);
+    c->hist = dalloc<double>(128);
+    c->eig_out = dalloc<double>(2);
+    c->red.part = dalloc<double>((int64_t)kMaxRedBlocks * kMaxRhs);
+    c->red.cnt = dalloc<unsigned>(1);
+    MFP_CHECK_CUDA(cudaMemsetAsync(c->red.cnt, 0, sizeof(unsigned), st(stream)));
+    MFP_CHECK_CUDA(cudaMallocHost(&c->host_scal,
+                                  sizeof(double) * S_COUNT * kMaxRhs));
+    ensure_scratch(c, 1);
+    build_levels(c, st(stream));
+    *out = c;
+    return MFP_OK;
+  } catch (const Fail& f) {
+    if (c) {
+      free_ctx(c);
+      delete c;
+    }
+    return f.st;
+  } catch (const std::bad_alloc&) {
+    if (c) {
+      free_ctx(c);
+      delete c;
+    }
+    set_error("host allocation failed");
+    return MFP_ERR_OOM;
+  }
+}
+
+mfp_status mfp_destroy(mfp_ctx* c) {
+  if (!c) return MFP_OK;
+  cudaDeviceSynchronize();
+  free_ctx(c);
+  delete c;
+  return MFP_OK;
+}
+
+int mfp_n_levels(const mfp_ctx* c) { return c ? (int)c->levels.size() : 0; }
+
+mfp_status mfp_sizes(const mfp_ctx* c, int level, int64_t* n_dofs,
+                     int64_t* n_cell_qp, int64_t* n_face_qp) {
+  API_BEGIN
+  Level& L = get_level(const_cast<mfp_ctx*>(c), level);
+  const int64_t p = L.p;
+  if (n_dofs) *n_dofs = L.ndofs;
+  if (n_cell_qp) *n_cell_qp = L.ncells * p * p * p;
+  if (n_face_qp) *n_face_qp = L.nfaces * p * p;
+  API_END
+}
+
+mfp_status mfp_set_coefficient(mfp_ctx* c, const double* a_cell,
+                               const double* a_face, void* stream) {
+  API_BEGIN
+  MFP_REQUIRE(c && a_cell, "null argument");
+  MFP_REQUIRE(c->desc.disc == MFP_CG || a_face,
+              "SIPG needs the face coefficient");
+  cudaStream_t s = st(stream);
+  const int nl = (int)c->levels.size();
+  for (int l = nl - 1; l >= 0; --l) {
+    Level& L = c->levels[l];
+    const int64_t P3 = (int64_t)L.p * L.p * L.p, P2 = (int64_t)L.p * L.p;
+    if (!L.d64.kcell) L.d64.kcell = dalloc<double>(L.ncells * P3);
+    if (!L.d64.kface) L.d64.kface = dalloc<double>(L.nfaces * P2);
+    if (l == nl - 1) {
+      MFP_CHECK_CUDA(cudaMemcpyAsync(L.d64.kcell, a_cell,
+                                     L.ncells * P3 * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s));
+      if (a_face)
+        MFP_CHECK_CUDA(cudaMemcpyAsync(L.d64.kface, a_face,
+                                       L.nfaces * P2 * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s));
+      else
+        launch_fill<double>(L.d64.kface, 1.0, L.nfaces * P2, s);
+    } else {
+      launch_coarsen_coefficient(c->levels[l + 1], L, s);
+    }
+  }
+  c->has_coef = true;
+  build_levels(c, s);
+  API_END
+}
+
+mfp_status mfp_rhs(mfp_ctx* c, int f_kind, const double* params, int nterms,
+                   double* b, int64_t stride, void* stream) {
+  API_BEGIN
+  MFP_REQUIRE(c && b, "null argument");
+  MFP_REQUIRE(f_kind == 0 || f_kind == 1, "unknown f_kind");
+  MFP_REQUIRE(stride >= 1, "stride must be >= 1");
+  cudaStream_t s = st(stream);
+  if (f_kind == 1) {
+    MFP_REQUIRE(params && nterms >= 1 && nterms <= 4096, "bad Gaussian terms");
+    if (c->params_cap < nterms) {
+      dfree(c->params);
+      c->params = dalloc<double>(5 * (int64_t)nterms);
+      c->params_cap = nterms;
+    }
+    MFP_CHECK_CUDA(cudaMemcpyAsync(c->params, params,
+                                   5 * sizeof(double) * nterms,
+                                   cudaMemcpyHostToDevice, s));
+    MFP_CHECK_CUDA(cudaStreamSynchronize(s));  // host params may go away
+  }
+  launch_rhs(c->levels.back(), f_kind, c->params, nterms, b, stride, s);
+  API_END
+}
+
+mfp_status mfp_apply(mfp_ctx* c, int level, int prec, const void* src,
+                     void* dst, int n_rhs, void* stream) {
+  API_BEGIN
+  Level& L = get_level(c, level);
+  MFP_REQUIRE(src && dst && src != dst, "src / dst must be distinct non-null");
+  MFP_REQUIRE(n_rhs >= 1 && n_rhs <= kMaxRhs, "n_rhs must be in 1..256");
+  if (prec_of(prec) == MFP_FP64)
+    apply_level<double>(c, L, static_cast<const double*>(src),
+                        static_cast<double*>(dst), n_rhs, st(stream));
+  else
+    apply_level<float>(c, L, static_cast<const float*>(src),
+                       static_cast<float*>(dst), n_rhs, st(stream));
+  API_END
+}
+
+mfp_status mfp_inverse_diagonal(mfp_ctx* c, int level, int prec, void* out,
+                                void* stream) {
+  API_BEGIN
+  Level& L = get_level(c, level);
+  MFP_REQUIRE(out, "null argument");
+  if (prec_of(prec) == MFP_FP64) {
+    MFP_CHECK_CUDA(cudaMemcpyAsync(out, L.d64.dinv, L.ndofs * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st(stream)));
+  } else {
+    MFP_REQUIRE(L.d32.valid, "no float level data (mg_precision FP64)");
+    MFP_CHECK_CUDA(cudaMemcpyAsync(out, L.d32.dinv, L.ndofs * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, st(stream)));
+  }
+  API_END
+}
+
+mfp_status mfp_level_info(const mfp_ctx* c, int level, double* lam_max,
+                          double* lam_min, double* lo, double* hi,
+                          int* degree) {
+  API_BEGIN
+  Level& L = get_level(const_cast<mfp_ctx*>(c), level);
+  if (lam_max) *lam_max = L.lam_max;
+  if (lam_min) *lam_min = L.lam_min;
+  if (lo) *lo = L.cheb_lo;
+  if (hi) *hi = L.cheb_hi;
+  if (degree) *degree = L.cheb_degree;
+  API_END
+}
+
+mfp_status mfp_prolongate(mfp_ctx* c, int level, int prec, const void* xc,
+                          void* xf, void* stream) {
+  API_BEGIN
+  get_level(c, level);
+  MFP_REQUIRE(level >= 1, "level must be >= 1");
+  MFP_REQUIRE(xc && xf, "null argument");
+  if (prec_of(prec) == MFP_FP64)
+    prolongate<double>(c, level, static_cast<const double*>(xc),
+                       static_cast<double*>(xf), 1, st(stream));
+  else
+    prolongate<float>(c, level, static_cast<const float*>(xc),
+                      static_cast<float*>(xf), 1, st(stream));
+  API_END
+}
+
+mfp_status mfp_restrict(mfp_ctx* c, int level, int prec, const void* xf,
+                        void* xc, void* stream) {
+  API_BEGIN
+  get_level(c, level);
+  MFP_REQUIRE(level >= 1, "level must be >= 1");
+  MFP_REQUIRE(xc && xf, "null argument");
+  if (prec_of(prec) == MFP_FP64)
+    restrict_<double>(c, level, static_cast<const double*>(xf),
+                      static_cast<double*>(xc), 1, st(stream));
+  else
+    restrict_<float>(c, level, static_cast<const float*>(xf),
+                     static_cast<float*>(xc), 1, st(stream));
+  API_END
+}
+
+mfp_status mfp_smooth(mfp_ctx* c, int level, int prec, const void* b,
+                      void* x, int zero_start, void* stream) {
+  API_BEGIN
+  get_level(c, level);
+  MFP_REQUIRE(b && x && b != x, "b / x must be distinct non-null");
+  const int pr = prec_of(prec);
+  MFP_REQUIRE(pr == c->vprec || pr == MFP_FP64,
+              "float smoothing needs mg_precision MFP_FP32");
+  if (pr == MFP_FP64) {
+    MFP_REQUIRE(c->vprec == MFP_FP64,
+                "float64 smoothing needs mg_precision MFP_FP64 scratch");
+    smooth<double>(c, level, static_cast<const double*>(b),
+                   static_cast<double*>(x), zero_start != 0, 1, st(stream));
+  } else {
+    smooth<float>(c, level, static_cast<const float*>(b),
+                  static_cast<float*>(x), zero_start != 0, 1, st(stream));
+  }
+  API_END
+}
+
+mfp_status mfp_vcycle(mfp_ctx* c, const double* r, double* z, int n_rhs,
+                      void* stream) {
+  API_BEGIN
+  MFP_REQUIRE(c && r && z && r != z, "r / z must be distinct non-null");
+  ensure_scratch(c, n_rhs);
+  vcycle_top(c, r, z, n_rhs, st(stream));
+  API_END
+}
+
+mfp_status mfp_solve(mfp_ctx* c, const double* b, double* x, int R,
+                     double rtol, int max_it, int* iters_out,
+                     double* relres_out, void* stream) {
+  API_BEGIN
+  MFP_REQUIRE(c && b && x && b != x, "b / x must be distinct non-null");
+  MFP_REQUIRE(rtol > 0 && max_it >= 1, "rtol must be > 0, max_it >= 1");
+  ensure_scratch(c, R);
+  cudaStream_t s = st(stream);
+  Level& L = c->levels.back();
+  const int64_t n = L.ndofs;
+  double* h = c->host_scal;
+  // |b|^2, x = 0, r = b
+  std::vector<double> init((size_t)S_COUNT * R, 0.0);
+  for (int r = 0; r < R; ++r) init[(size_t)S_ACTIVE * R + r] = 1.0;
+  MFP_CHECK_CUDA(cudaMemcpyAsync(c->scal, init.data(),
+                                 init.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+  launch_dot(b, b, n, R, c->red, c->scal, 3, nullptr, 0, s);
+  MFP_CHECK_CUDA(cudaMemcpyAsync(h, c->scal + (size_t)S_BN2 * R,
+                                 R * sizeof(double), cudaMemcpyDeviceToHost,
+                                 s));
+  MFP_CHECK_CUDA(cudaMemsetAsync(x, 0, n * R * sizeof(double), s));
+  MFP_CHECK_CUDA(cudaMemcpyAsync(c->cg_r, b, n * R * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, s));
+  MFP_CHECK_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> bn2(h, h + R);
+  std::vector<int> its(R, 0);
+  std::vector<double> rel(R, 0.0);
+  std::vector<char> active(R, 1);
+  int n_active = R;
+  for (int r = 0; r < R; ++r)
+    if (bn2[r] == 0.0) {
+      active[r] = 0;
+      --n_active;
+    }
+  auto upload_active = [&]() {
+    for (int r = 0; r < R; ++r) h[r] = active[r] ? 1.0 : 0.0;
+    MFP_CHECK_CUDA(cudaMemcpyAsync(c->scal + (size_t)S_ACTIVE * R, h,
+                                   R * sizeof(double),
+                                   cudaMemcpyHostToDevice, s));
+    MFP_CHECK_CUDA(cudaStreamSynchronize(s));  // h is reused below
+  };
+  upload_active();
+  vcycle_top(c, c->cg_r, c->cg_z, R, s);
+  MFP_CHECK_CUDA(cudaMemcpyAsync(c->cg_p, c->cg_z, n * R * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, s));
+  launch_dot(c->cg_r, c->cg_z, n, R, c->red, c->scal, 0, nullptr, 0, s);
+  const double tol2 = rtol * rtol;
+  int it = 0;
+  while (n_active > 0 && it < max_it) {
+    ++it;
+    apply_level<double>(c, L, c->cg_p, c->cg_ap, R, s);
+    launch_dot(c->cg_p, c->cg_ap, n, R, c->red, c->scal, 1, nullptr, 0, s);
+    launch_cg_update(x, c->cg_r, c->cg_p, c->cg_ap, n, R, c->red, c->scal, s);
+    MFP_CHECK_CUDA(cudaMemcpyAsync(h, c->scal + (size_t)S_RN2 * R,
+                                   R * sizeof(double), cudaMemcpyDeviceToHost,
+                                   s));
+    MFP_CHECK_CUDA(cudaStreamSynchronize(s));
+    bool changed = false;
+    for (int r = 0; r < R; ++r) {
+      if (!active[r]) continue;
+      its[r] = it;
+      rel[r] = std::sqrt(h[r] / bn2[r]);
+      if (h[r] <= tol2 * bn2[r]) {
+        active[r] = 0;
+        --n_active;
+        changed = true;
+      }
+    }
+    if (n_active == 0) break;
+    if (changed) upload_active();
+    vcycle_top(c, c->cg_r, c->cg_z, R, s);
+    launch_dot(c->cg_r, c->cg_z, n, R, c->red, c->scal, 2, nullptr, 0, s);
+    launch_cg_p(c->cg_p, c->cg_z, n, R, c->scal, s);
+  }
+  MFP_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (iters_out)
+    for (int r = 0; r < R; ++r) iters_out[r] = its[r];
+  if (relres_out)
+    for (int r = 0; r < R; ++r) relres_out[r] = rel[r];
+  if (n_active > 0) {
+    set_error("CG did not reach the tolerance within max_it iterations");
+    return MFP_ERR_NOT_CONVERGED;
+  }
+  API_END
+}
+
+mfp_status mfp_gradient(mfp_ctx* c, const double* u, const double* lam,
+                        double* gc, double* gf, void* stream) {
+  API_BEGIN
+  MFP_REQUIRE(c && u && lam && gc, "null argument");
+  MFP_REQUIRE(c->desc.disc == MFP_CG || gf, "SIPG needs g_face");
+  launch_gradient(c->levels.back(), u, lam, gc, gf, st(stream));
+  API_END
+}
+
+mfp_status mfp_counters(const mfp_ctx* c, int64_t* applies, int64_t* vcyc,
+                        int64_t* launches) {
+  API_BEGIN
+  MFP_REQUIRE(c, "null context");
+  if (launches) *launches = g_launches.load();
+  if (applies)
+    for (size_t l = 0; l < c->levels.size(); ++l)
+      applies[l] = c->levels[l].applies;
+  if (vcyc) *vcyc = c->vcycles;
+  API_END
+}
+
+}  // extern "C"

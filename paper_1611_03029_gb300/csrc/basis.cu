@@ -1,0 +1,136 @@
+// Host-side 1D reference-element tables on [0, 1] (Sec. 2.1, Sec. 3),
+// computed once in long double and rounded to float64 / float32.
+#include <cmath>
+#include <mutex>
+
+#include "mfp_internal.h"
+
+namespace mfp {
+namespace {
+
+using ld = long double;
+
+// Legendre P_n(x) and P_n'(x) by the three-term recurrence.
+void legendre(int n, ld x, ld& P, ld& dP) {
+  ld p0 = 1, p1 = x;
+  if (n == 0) {
+    P = 1;
+    dP = 0;
+    return;
+  }
+  for (int m = 1; m < n; ++m) {
+    ld p2 = ((2 * m + 1) * x * p1 - m * p0) / (m + 1);
+    p0 = p1;
+    p1 = p2;
+  }
+  P = p1;
+  // n (x P_n - P_{n-1}) / (x^2 - 1); only used away from +-1
+  dP = n * (x * p1 - p0) / (x * x - 1);
+}
+
+// Gauss-Legendre points / weights on [-1, 1]: roots of P_n by Newton.
+void gauss(int n, ld* x, ld* w) {
+  const ld pi = 3.14159265358979323846264338327950288L;
+  for (int i = 0; i < n; ++i) {
+    ld t = -std::cos(pi * (i + 0.75L) / (n + 0.5L));
+    for (int it = 0; it < 100; ++it) {
+      ld P, dP;
+      legendre(n, t, P, dP);
+      ld dt = P / dP;
+      t -= dt;
+      if (std::fabs(dt) < 1e-19L) break;
+    }
+    ld P, dP;
+    legendre(n, t, P, dP);
+    x[i] = t;
+    w[i] = 2 / ((1 - t * t) * dP * dP);
+  }
+}
+
+// Gauss-Lobatto points on [-1, 1]: +-1 and the roots of P_k', by Newton with
+// P_k'' from Legendre's equation (1-x^2) P'' = 2 x P' - k(k+1) P.
+void lobatto(int k, ld* x) {
+  const ld pi = 3.14159265358979323846264338327950288L;
+  x[0] = -1;
+  x[k] = 1;
+  for (int i = 1; i < k; ++i) {
+    ld t = -std::cos(pi * i / k);
+    for (int it = 0; it < 100; ++it) {
+      ld P, dP;
+      legendre(k, t, P, dP);
+      ld d2P = (2 * t * dP - k * (k + 1) * P) / (1 - t * t);
+      ld dt = dP / d2P;
+      t -= dt;
+      if (std::fabs(dt) < 1e-19L) break;
+    }
+    x[i] = t;
+  }
+}
+
+ld lagrange(const ld* nodes, int n, int j, ld x) {
+  ld v = 1;
+  for (int m = 0; m < n; ++m)
+    if (m != j) v *= (x - nodes[m]) / (nodes[j] - nodes[m]);
+  return v;
+}
+
+ld lagrange_deriv(const ld* nodes, int n, int j, ld x) {
+  ld s = 0;
+  for (int m = 0; m < n; ++m) {
+    if (m == j) continue;
+    ld t = 1 / (nodes[j] - nodes[m]);
+    for (int l = 0; l < n; ++l)
+      if (l != j && l != m) t *= (x - nodes[l]) / (nodes[j] - nodes[l]);
+    s += t;
+  }
+  return s;
+}
+
+template <typename T>
+void fill(DevTab<T>& t, int k) {
+  const int p = k + 1;
+  ld xl[kMaxP], xg[kMaxP], wg[kMaxP];
+  lobatto(k, xl);
+  gauss(p, xg, wg);
+  // map to [0, 1]
+  for (int i = 0; i < p; ++i) {
+    xl[i] = (xl[i] + 1) / 2;
+    xg[i] = (xg[i] + 1) / 2;
+    wg[i] = wg[i] / 2;
+  }
+  for (int i = 0; i < kMaxP * kMaxP; ++i)
+    t.S[i] = t.D[i] = t.Dphi[i] = t.E0[i] = t.E1[i] = 0;
+  for (int i = 0; i < kMaxP; ++i) t.dphi0[i] = t.dphi1[i] = t.w[i] = 0;
+  for (int q = 0; q < p; ++q) {
+    t.w[q] = (T)wg[q];
+    t.g[q] = (T)xg[q];
+    t.x[q] = (T)xl[q];
+    for (int j = 0; j < p; ++j) {
+      t.S[q * p + j] = (T)lagrange(xl, p, j, xg[q]);
+      t.Dphi[q * p + j] = (T)lagrange_deriv(xl, p, j, xg[q]);
+      t.D[q * p + j] = (T)lagrange_deriv(xg, p, j, xg[q]);
+      t.E0[q * p + j] = (T)lagrange(xl, p, j, xl[q] / 2);
+      t.E1[q * p + j] = (T)lagrange(xl, p, j, (1 + xl[q]) / 2);
+    }
+  }
+  for (int j = 0; j < p; ++j) {
+    t.dphi0[j] = (T)lagrange_deriv(xl, p, j, 0.0L);
+    t.dphi1[j] = (T)lagrange_deriv(xl, p, j, 1.0L);
+  }
+}
+
+}  // namespace
+
+const HostTables& host_tables() {
+  static HostTables tabs;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (int k = 1; k <= 8; ++k) {
+      fill(tabs.d[k - 1], k);
+      fill(tabs.f[k - 1], k);
+    }
+  });
+  return tabs;
+}
+
+}  // namespace mfp

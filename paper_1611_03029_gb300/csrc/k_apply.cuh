@@ -1,0 +1,495 @@
+// Matrix-free operator evaluation by sum factorization (Sec. 3, Eq. 12) for
+// continuous Q_k (Eq. 4) and SIPG (Eq. 6, boundary extension Eq. 7).
+//
+// Mapping: a thread block owns `cpb` cells; each cell is worked on by p*p
+// threads.  In every 1D sweep a thread owns one line of p values along the
+// sweep direction and keeps it in registers, so each sweep is p^2 FMAs per
+// thread with the 1D matrix as constant-bank operands; lines change
+// direction through shared memory.  Per cell:
+//   gather -> S (z, y, x) -> collocation derivative D (x, y, z) at the Gauss
+//   points -> t_q = G_q grad u_q (kappa, w, det J, J^{-1} J^{-T}) ->
+//   D^T (z, y, x) -> S^T (x, y, z) -> scatter.
+// CG scatters with atomics into the node grid (boundary rows are identity);
+// SIPG adds the six face integrals of its own test functions (each interior
+// face is evaluated once from either side, with that side's outward normal;
+// Eq. 6 visits each face twice in the same way) and stores its block.
+#pragma once
+
+#include "dev_tables.cuh"
+
+namespace mfp {
+namespace {
+
+template <typename T>
+struct ApplyArgs {
+  const T* __restrict__ src;
+  T* __restrict__ dst;
+  int n[3];
+  int ncells;
+  int g[3];          // CG node grid
+  int face_off[3];
+  const T* __restrict__ G;      // curved: [cell][6][p^3]
+  const T* __restrict__ kcell;  // [cell][p^3] or null
+  const T* __restrict__ kface;  // [face][p^2] or null
+  const T* __restrict__ fdata;  // curved SIPG: [face][7][p^2]
+  const T* __restrict__ sigma;  // curved SIPG: [face]
+  T kappa;
+  T gs[3];  // Cartesian: |K| / h_d^2
+  T ns[3];  // Cartesian: 1 / h_d
+  T fa[3];  // Cartesian: face area of a d-face
+  T sg[3];  // Cartesian: penalty of a d-face
+  int stride;  // batched layout: value i of column r at [i*stride + r]
+  int col;
+};
+
+template <int P>
+__device__ __forceinline__ int idx3(int x, int y, int z) {
+  return x + P * (y + P * z);
+}
+
+// node (layer l along axis D, tangential coordinates a < b)
+template <int P, int D>
+__device__ __forceinline__ int fnode(int l, int a, int b) {
+  if constexpr (D == 0) return l + P * (a + P * b);
+  if constexpr (D == 1) return a + P * (l + P * b);
+  return a + P * (b + P * l);
+}
+
+template <typename T, int P, bool DG>
+__host__ __device__ constexpr int cell_smem_elems() {
+  return (DG ? 4 : 3) * P * P * P + (DG ? 8 * P * P : 0);
+}
+template <int P>
+__host__ __device__ constexpr int table_smem_elems() {
+  return 3 * P * P + 3 * P;
+}
+
+// One face of the own cell (axis D, side S: 0 lower, 1 upper).  Adds the
+// face integrals tested with the own cell's basis into Aq (nodal values).
+template <int P, typename T, bool CURVED, int D, int S>
+__device__ __forceinline__ void face_contrib(
+    const ApplyArgs<T>& a, bool active, int cx, int cy, int cz, const T* U,
+    T* Aq, T* FS, const T* sS, const T* sD, const T* s0, const T* s1,
+    const T* sw, int ta, int tb) {
+  constexpr int P2 = P * P, P3 = P2 * P;
+  constexpr int T1 = D == 0 ? 1 : 0;
+  constexpr int T2 = D == 2 ? 1 : 2;
+  const int t = ta + P * tb;
+  int m[3] = {a.n[0], a.n[1], a.n[2]};
+  m[D] += 1;
+  int fc[3] = {cx, cy, cz};
+  fc[D] += S;
+  const int f = a.face_off[D] + fc[0] + m[0] * (fc[1] + m[1] * fc[2]);
+  int nbc[3] = {cx, cy, cz};
+  nbc[D] += S ? 1 : -1;
+  const bool bnd = nbc[D] < 0 || nbc[D] >= a.n[D];
+  const int nb = bnd ? 0 : nbc[0] + a.n[0] * (nbc[1] + a.n[1] * nbc[2]);
+  const T* dS = S ? s1 : s0;  // own slope at its face
+  const T* dN = S ? s0 : s1;  // neighbour slope at its face
+  constexpr int lo = S ? P - 1 : 0;
+  constexpr int ln = S ? 0 : P - 1;
+  // F1: nodal face values and reference normal slopes of both sides
+  {
+    T vo = U[fnode<P, D>(lo, ta, tb)];
+    T dno = T(0);
+#pragma unroll
+    for (int l = 0; l < P; ++l) dno = fma(dS[l], U[fnode<P, D>(l, ta, tb)], dno);
+    T vn = T(0), dnn = T(0);
+    if (!bnd && active) {
+      const T* sp = a.src;
+      const size_t cb = (size_t)nb * P3;
+#pragma unroll
+      for (int l = 0; l < P; ++l) {
+        T u = sp[(cb + fnode<P, D>(l, ta, tb)) * a.stride + a.col];
+        dnn = fma(dN[l], u, dnn);
+        if (l == ln) vn = u;
+      }
+    }
+    FS[0 * P2 + t] = vo;
+    FS[1 * P2 + t] = dno;
+    FS[2 * P2 + t] = vn;
+    FS[3 * P2 + t] = dnn;
+  }
+  __syncthreads();
+  // F2: interpolate along the first tangential axis (a)
+#pragma unroll
+  for (int arr = 0; arr < 4; ++arr) {
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      s = fma(sS[ta * P + j], FS[arr * P2 + j + P * tb], s);
+    FS[(4 + arr) * P2 + t] = s;
+  }
+  __syncthreads();
+  // F3: along the second tangential axis (b)
+  T q[4];
+#pragma unroll
+  for (int arr = 0; arr < 4; ++arr) {
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      s = fma(sS[tb * P + j], FS[(4 + arr) * P2 + ta + P * j], s);
+    q[arr] = s;
+  }
+  __syncthreads();
+  if constexpr (CURVED) {
+    FS[0 * P2 + t] = q[0];
+    FS[2 * P2 + t] = q[2];
+    __syncthreads();
+  }
+  // flux at face quadrature point (ta, tb)
+  {
+    const T kap = a.kface ? a.kface[(size_t)f * P2 + t] : a.kappa;
+    T uo = q[0], un = q[2], dno, dnn, dA, sig;
+    T gvec[3] = {T(0), T(0), T(0)};  // own outward n J^{-T}... in xi coords
+    if constexpr (!CURVED) {
+      const T sgn = S ? T(1) : T(-1);
+      dA = sw[ta] * sw[tb] * a.fa[D];
+      sig = a.sg[D];
+      dno = sgn * a.ns[D] * q[1];
+      dnn = bnd ? dno : sgn * a.ns[D] * q[3];
+      gvec[D] = sgn * a.ns[D];
+    } else {
+      const T* fd = a.fdata + (size_t)f * 7 * P2;
+      dA = fd[t];
+      sig = a.sigma[f];
+      T go[3], gn[3];
+      go[D] = q[1];
+      gn[D] = q[3];
+      T s1o = T(0), s2o = T(0), s1n = T(0), s2n = T(0);
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        s1o = fma(sD[ta * P + j], FS[0 * P2 + j + P * tb], s1o);
+        s2o = fma(sD[tb * P + j], FS[0 * P2 + ta + P * j], s2o);
+        s1n = fma(sD[ta * P + j], FS[2 * P2 + j + P * tb], s1n);
+        s2n = fma(sD[tb * P + j], FS[2 * P2 + ta + P * j], s2n);
+      }
+      go[T1] = s1o;
+      go[T2] = s2o;
+      gn[T1] = s1n;
+      gn[T2] = s2n;
+      T nL[3], nR[3];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        nL[e] = fd[(1 + e) * P2 + t];
+        nR[e] = fd[(4 + e) * P2 + t];
+      }
+      if constexpr (S == 1) {  // own cell is the left one: outward = +n
+        dno = nL[0] * go[0] + nL[1] * go[1] + nL[2] * go[2];
+        dnn = nR[0] * gn[0] + nR[1] * gn[1] + nR[2] * gn[2];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) gvec[e] = nL[e];
+      } else {  // own cell is the right one: outward = -n
+        dno = -(nR[0] * go[0] + nR[1] * go[1] + nR[2] * go[2]);
+        dnn = -(nL[0] * gn[0] + nL[1] * gn[1] + nL[2] * gn[2]);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) gvec[e] = -nR[e];
+      }
+      if (bnd) dnn = dno;
+    }
+    if (bnd) un = -uo;  // mirror state u+ = -u-, grad u+ = grad u- (Eq. 7)
+    const T kdA = kap * dA;
+    const T jump = uo - un;
+    const T avg = T(0.5) * (dno + dnn);
+    const T cv = kdA * (sig * jump - avg);
+    const T cg = T(-0.5) * kdA * jump;
+    FS[4 * P2 + t] = cv;
+    FS[5 * P2 + t] = cg * gvec[D];
+    FS[6 * P2 + t] = cg * gvec[T1];
+    FS[7 * P2 + t] = cg * gvec[T2];
+  }
+  __syncthreads();
+  // tangential test slopes fold into the face-layer values
+  T vq = FS[4 * P2 + t];
+  if constexpr (CURVED) {
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      vq = fma(sD[j * P + ta], FS[6 * P2 + j + P * tb], vq);
+      vq = fma(sD[j * P + tb], FS[7 * P2 + ta + P * j], vq);
+    }
+  }
+  FS[0 * P2 + t] = vq;
+  FS[1 * P2 + t] = FS[5 * P2 + t];
+  __syncthreads();
+  // S^T along a
+#pragma unroll
+  for (int arr = 0; arr < 2; ++arr) {
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      s = fma(sS[j * P + ta], FS[arr * P2 + j + P * tb], s);
+    FS[(2 + arr) * P2 + t] = s;
+  }
+  __syncthreads();
+  // S^T along b and distribution onto the own nodes of line (ta, tb)
+  {
+    T vf = T(0), nf = T(0);
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      vf = fma(sS[j * P + tb], FS[2 * P2 + ta + P * j], vf);
+      nf = fma(sS[j * P + tb], FS[3 * P2 + ta + P * j], nf);
+    }
+    Aq[fnode<P, D>(lo, ta, tb)] += vf;
+#pragma unroll
+    for (int l = 0; l < P; ++l) Aq[fnode<P, D>(l, ta, tb)] += dS[l] * nf;
+  }
+  __syncthreads();
+}
+
+template <int P, typename T, bool DG, bool CURVED>
+__global__ void k_apply(const ApplyArgs<T> a) {
+  constexpr int P2 = P * P, P3 = P2 * P;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int cpb = blockDim.x / P2;
+  const int lc = threadIdx.x / P2;
+  const int t = threadIdx.x - lc * P2;
+  const int ta = t % P, tb = t / P;
+  T* base = sm + (size_t)lc * cell_smem_elems<T, P, DG>();
+  T* Aq = base;
+  T* GX = base + P3;
+  T* GY = base + 2 * P3;
+  T* U = base + 3 * P3;   // DG: nodal input
+  T* FS = base + 4 * P3;  // DG: face scratch [8][p^2]
+  T* tabs = sm + (size_t)cpb * cell_smem_elems<T, P, DG>();
+  T* sS = tabs;
+  T* sD = tabs + P2;
+  T* sDphi = tabs + 2 * P2;
+  T* s0 = tabs + 3 * P2;
+  T* s1 = s0 + P;
+  T* sw = s1 + P;
+  load_tables_shared<T, P>(sS, sD, sDphi, s0, s1, sw);
+  __syncthreads();
+  const int gx0 = a.g[0], gy0 = a.g[1], gz0 = a.g[2];
+
+  for (int cbase = blockIdx.x * cpb; cbase < a.ncells;
+       cbase += gridDim.x * cpb) {
+    const int cell = cbase + lc;
+    const bool active = cell < a.ncells;
+    const int cc = active ? cell : 0;
+    const int cx = cc % a.n[0];
+    const int cy = (cc / a.n[0]) % a.n[1];
+    const int cz = cc / (a.n[0] * a.n[1]);
+    T r[P], o[P];
+    // ---- gather the z-line (x = ta, y = tb)
+    if constexpr (DG) {
+#pragma unroll
+      for (int z = 0; z < P; ++z) {
+        const size_t gi = (size_t)cc * P3 + idx3<P>(ta, tb, z);
+        r[z] = active ? a.src[gi * a.stride + a.col] : T(0);
+        U[idx3<P>(ta, tb, z)] = r[z];
+      }
+    } else {
+      const int X = cx * (P - 1) + ta, Y = cy * (P - 1) + tb;
+      const bool bxy = X == 0 || X == gx0 - 1 || Y == 0 || Y == gy0 - 1;
+#pragma unroll
+      for (int z = 0; z < P; ++z) {
+        const int Z = cz * (P - 1) + z;
+        const bool con = bxy || Z == 0 || Z == gz0 - 1;
+        const size_t gi = (size_t)X + (size_t)gx0 * (Y + (size_t)gy0 * Z);
+        r[z] = (active && !con) ? a.src[gi * a.stride + a.col] : T(0);
+      }
+    }
+    // ---- values at Gauss points: z (registers), y, x
+    mv<T, P, T_S>(r, o);
+#pragma unroll
+    for (int z = 0; z < P; ++z) Aq[idx3<P>(ta, tb, z)] = o[z];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(ta, j, tb)];
+    mv<T, P, T_S>(r, o);
+#pragma unroll
+    for (int j = 0; j < P; ++j) Aq[idx3<P>(ta, j, tb)] = o[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(j, ta, tb)];
+    mv<T, P, T_S>(r, o);
+#pragma unroll
+    for (int j = 0; j < P; ++j) Aq[idx3<P>(j, ta, tb)] = o[j];
+    mv<T, P, T_D>(o, r);
+#pragma unroll
+    for (int j = 0; j < P; ++j) GX[idx3<P>(j, ta, tb)] = r[j];
+    __syncthreads();
+    // ---- reference gradient: y into GY, z kept in registers
+#pragma unroll
+    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(ta, j, tb)];
+    mv<T, P, T_D>(r, o);
+#pragma unroll
+    for (int j = 0; j < P; ++j) GY[idx3<P>(ta, j, tb)] = o[j];
+    T gz[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(ta, tb, j)];
+    mv<T, P, T_D>(r, gz);
+    __syncthreads();
+    // ---- quadrature-point operation t = G_q grad u (Eq. 12)
+    {
+      const T wab = sw[ta] * sw[tb];
+#pragma unroll
+      for (int qz = 0; qz < P; ++qz) {
+        const int q = idx3<P>(ta, tb, qz);
+        const T ux = GX[q], uy = GY[q], uz = gz[qz];
+        const T kap = a.kcell ? a.kcell[(size_t)cc * P3 + q] : a.kappa;
+        T tx, ty, tz;
+        if constexpr (CURVED) {
+          const T* Gp = a.G + (size_t)cc * 6 * P3 + q;
+          const T g0 = Gp[0], g1 = Gp[P3], g2 = Gp[2 * P3], g3 = Gp[3 * P3],
+                  g4 = Gp[4 * P3], g5 = Gp[5 * P3];
+          tx = kap * (g0 * ux + g1 * uy + g2 * uz);
+          ty = kap * (g1 * ux + g3 * uy + g4 * uz);
+          tz = kap * (g2 * ux + g4 * uy + g5 * uz);
+        } else {
+          const T wk = kap * wab * sw[qz];
+          tx = wk * a.gs[0] * ux;
+          ty = wk * a.gs[1] * uy;
+          tz = wk * a.gs[2] * uz;
+        }
+        GX[q] = tx;
+        GY[q] = ty;
+        r[qz] = tz;
+      }
+      mtv<T, P, T_D>(r, o);
+#pragma unroll
+      for (int j = 0; j < P; ++j) Aq[idx3<P>(ta, tb, j)] = o[j];
+    }
+    __syncthreads();
+    // ---- transposed derivative y (added), x (added) then S^T x, y, z
+#pragma unroll
+    for (int j = 0; j < P; ++j) r[j] = GY[idx3<P>(ta, j, tb)];
+    mtv<T, P, T_D>(r, o);
+#pragma unroll
+    for (int j = 0; j < P; ++j) Aq[idx3<P>(ta, j, tb)] += o[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < P; ++j) r[j] = GX[idx3<P>(j, ta, tb)];
+    mtv<T, P, T_D>(r, o);
+#pragma unroll
+    for (int j = 0; j < P; ++j) o[j] += Aq[idx3<P>(j, ta, tb)];
+    mtv<T, P, T_S>(o, r);
+#pragma unroll
+    for (int j = 0; j < P; ++j) Aq[idx3<P>(j, ta, tb)] = r[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(ta, j, tb)];
+    mtv<T, P, T_S>(r, o);
+#pragma unroll
+    for (int j = 0; j < P; ++j) Aq[idx3<P>(ta, j, tb)] = o[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(ta, tb, j)];
+    mtv<T, P, T_S>(r, o);
+    // ---- scatter
+    if constexpr (!DG) {
+      const int X = cx * (P - 1) + ta, Y = cy * (P - 1) + tb;
+      const bool bxy = X == 0 || X == gx0 - 1 || Y == 0 || Y == gy0 - 1;
+      if (active) {
+#pragma unroll
+        for (int z = 0; z < P; ++z) {
+          const int Z = cz * (P - 1) + z;
+          const bool con = bxy || Z == 0 || Z == gz0 - 1;
+          const size_t gi =
+              ((size_t)X + (size_t)gx0 * (Y + (size_t)gy0 * Z)) * a.stride +
+              a.col;
+          if (con)
+            a.dst[gi] = a.src[gi];  // identity row (same value from all cells)
+          else
+            atomicAdd(a.dst + gi, o[z]);
+        }
+      }
+      __syncthreads();
+    } else {
+#pragma unroll
+      for (int z = 0; z < P; ++z) Aq[idx3<P>(ta, tb, z)] = o[z];
+      __syncthreads();
+      face_contrib<P, T, CURVED, 0, 0>(a, active, cx, cy, cz, U, Aq, FS, sS,
+                                       sD, s0, s1, sw, ta, tb);
+      face_contrib<P, T, CURVED, 0, 1>(a, active, cx, cy, cz, U, Aq, FS, sS,
+                                       sD, s0, s1, sw, ta, tb);
+      face_contrib<P, T, CURVED, 1, 0>(a, active, cx, cy, cz, U, Aq, FS, sS,
+                                       sD, s0, s1, sw, ta, tb);
+      face_contrib<P, T, CURVED, 1, 1>(a, active, cx, cy, cz, U, Aq, FS, sS,
+                                       sD, s0, s1, sw, ta, tb);
+      face_contrib<P, T, CURVED, 2, 0>(a, active, cx, cy, cz, U, Aq, FS, sS,
+                                       sD, s0, s1, sw, ta, tb);
+      face_contrib<P, T, CURVED, 2, 1>(a, active, cx, cy, cz, U, Aq, FS, sS,
+                                       sD, s0, s1, sw, ta, tb);
+      if (active) {
+#pragma unroll
+        for (int z = 0; z < P; ++z) {
+          const size_t gi = (size_t)cc * P3 + idx3<P>(ta, tb, z);
+          a.dst[gi * a.stride + a.col] = Aq[idx3<P>(ta, tb, z)];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+inline int default_cpb(int p) {
+  switch (p) {
+    case 2: return 32;
+    case 3: return 12;
+    case 4: return 8;
+    case 5: return 4;
+    case 6: return 3;
+    case 7: return 2;
+    case 8: return 2;
+    default: return 1;
+  }
+}
+
+template <int P, typename T, bool DG, bool CURVED>
+void run_apply(const ApplyArgs<T>& a, int cpb, cudaStream_t s) {
+  constexpr int P2 = P * P;
+  const size_t smem =
+      ((size_t)cpb * cell_smem_elems<T, P, DG>() + table_smem_elems<P>()) *
+      sizeof(T);
+  auto kern = k_apply<P, T, DG, CURVED>;
+  if (smem > 48 * 1024)
+    MFP_CHECK_CUDA(cudaFuncSetAttribute(
+        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  MFP_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, kern, cpb * P2, smem));
+  if (per_sm < 1) per_sm = 1;
+  const int64_t need = (a.ncells + cpb - 1) / cpb;
+  const int64_t cap = (int64_t)per_sm * sm_count();
+  const int grid = (int)(need < cap ? need : cap);
+  if (grid <= 0) return;
+  kern<<<grid, cpb * P2, smem, s>>>(a);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+
+template <typename T>
+ApplyArgs<T> make_apply_args(const Level& L, const LevelData<T>& D,
+                             const T* src, T* dst) {
+  ApplyArgs<T> a{};
+  a.src = src;
+  a.dst = dst;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = L.n[d];
+    a.g[d] = L.gdim[d];
+    a.face_off[d] = L.face_off[d];
+  }
+  a.ncells = (int)L.ncells;
+  a.G = D.G;
+  a.kcell = D.kcell;
+  a.kface = D.kface;
+  a.fdata = D.fdata;
+  a.sigma = D.sigma;
+  a.kappa = (T)L.kappa;
+  const double vol = L.h[0] * L.h[1] * L.h[2];
+  const double pen = L.penalty * (double)L.p * L.p;
+  for (int d = 0; d < 3; ++d) {
+    a.gs[d] = (T)(vol / (L.h[d] * L.h[d]));
+    a.ns[d] = (T)(1.0 / L.h[d]);
+    a.fa[d] = (T)(vol / L.h[d]);
+    a.sg[d] = (T)(pen / L.h[d]);
+  }
+  a.stride = 1;
+  a.col = 0;
+  return a;
+}
+
+}  // namespace
+}  // namespace mfp

@@ -1,0 +1,663 @@
+// Vector kernels of the solver (Sec. 4.1): Chebyshev-Jacobi updates, level
+// transfer by the tensorial geometric embedding, fused CG updates with
+// deterministic two-stage reductions finished on the device, and the
+// bisection for the extreme eigenvalues of the Lanczos tridiagonal.
+#include "dev_tables.cuh"
+
+namespace mfp {
+namespace {
+
+constexpr int kVecThreads = 256;
+
+inline int vec_grid(int64_t n) {
+  int64_t b = (n + kVecThreads - 1) / kVecThreads;
+  int64_t cap = (int64_t)sm_count() * 8;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+#define GRID_STRIDE(i, n)                                                 \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
+       i += (int64_t)gridDim.x * blockDim.x)
+
+template <typename T>
+__global__ void k_fill(T* x, T v, int64_t n) {
+  GRID_STRIDE(i, n) x[i] = v;
+}
+
+__global__ void k_invert_diag(double* d, int64_t n, int g0, int g1, int g2,
+                              int cg) {
+  GRID_STRIDE(i, n) {
+    bool con = false;
+    if (cg) {
+      const int64_t ix = i % g0, iy = (i / g0) % g1,
+                    iz = i / ((int64_t)g0 * g1);
+      con = ix == 0 || iy == 0 || iz == 0 || ix == g0 - 1 || iy == g1 - 1 ||
+            iz == g2 - 1;
+    }
+    d[i] = con ? 1.0 : 1.0 / d[i];
+  }
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b,
+                           int64_t n) {
+  GRID_STRIDE(i, n) b[i] = (float)a[i];
+}
+__global__ void k_to_double(const float* __restrict__ a,
+                            double* __restrict__ b, int64_t n) {
+  GRID_STRIDE(i, n) b[i] = (double)a[i];
+}
+
+// Chebyshev (Sec. 4.1; three-term recurrence on D^{-1} A):
+//   first update: d = c D^{-1} (b - A x)   (ax == null: x = 0, residual b)
+//   later:        d = cd d + cr D^{-1} (b - A x);   x += d.
+// Vectors hold nrhs interleaved columns; dinv has one entry per row.
+template <typename T>
+__global__ void k_cheb_first(const T* __restrict__ b,
+                             const T* __restrict__ dinv, T* __restrict__ d,
+                             T* __restrict__ x, const T* __restrict__ ax, T c,
+                             int64_t n, int nrhs) {
+  GRID_STRIDE(i, n * nrhs) {
+    const T r = ax ? b[i] - ax[i] : b[i];
+    const T di = c * dinv[i / nrhs] * r;
+    d[i] = di;
+    x[i] = ax ? x[i] + di : di;
+  }
+}
+
+template <typename T>
+__global__ void k_cheb_step(const T* __restrict__ b,
+                            const T* __restrict__ dinv, T* __restrict__ d,
+                            T* __restrict__ x, const T* __restrict__ ax, T cd,
+                            T cr, int64_t n, int nrhs) {
+  GRID_STRIDE(i, n * nrhs) {
+    const T di = cd * d[i] + cr * dinv[i / nrhs] * (b[i] - ax[i]);
+    d[i] = di;
+    x[i] += di;
+  }
+}
+
+template <typename T>
+__global__ void k_residual(const T* b, const T* ax, T* r, int64_t n) {
+  GRID_STRIDE(i, n) r[i] = b[i] - ax[i];
+}
+
+template <typename T>
+__global__ void k_axpy(T* __restrict__ y, const T* __restrict__ x, T a,
+                       int64_t n) {
+  GRID_STRIDE(i, n) y[i] += a * x[i];
+}
+
+// ---------------------------------------------------------------------------
+// Transfer (Sec. 4.1: geometric embedding, done tensorially).  One block per
+// coarse cell.  1D embedding E [M][p]: CG M = 2k+1 fine nodes inside the
+// coarse cell (rows 0..k from the left child, k..2k from the right one, the
+// middle row shared); SIPG M = 2p (left child's p rows, then right child's).
+// ---------------------------------------------------------------------------
+struct XferArgs {
+  int nc[3];  // coarse cells per axis
+  int gc[3];  // coarse CG grid
+  int gf[3];  // fine CG grid
+  int nf[3];  // fine cells per axis
+  int dg;
+  int stride;  // columns (batched layout)
+  int col;
+};
+
+template <typename T, int P>
+__device__ __forceinline__ T emb(int o, int r, int j) {
+  if constexpr (std::is_same<T, double>::value)
+    return o ? c_tab64[P - 2].E1[r * P + j] : c_tab64[P - 2].E0[r * P + j];
+  else
+    return o ? c_tab32[P - 2].E1[r * P + j] : c_tab32[P - 2].E0[r * P + j];
+}
+
+template <typename T, int P>
+__device__ void load_embedding(T* E, int dg) {
+  constexpr int K = P - 1;
+  const int M = dg ? 2 * P : 2 * K + 1;
+  for (int i = threadIdx.x; i < M * P; i += blockDim.x) {
+    const int r = i / P, j = i % P;
+    if (dg)
+      E[i] = r < P ? emb<T, P>(0, r, j) : emb<T, P>(1, r - P, j);
+    else
+      E[i] = r <= K ? emb<T, P>(0, r, j) : emb<T, P>(1, r - K, j);
+  }
+}
+
+__device__ __forceinline__ bool on_boundary(int X, int Y, int Z,
+                                            const int (&g)[3]) {
+  return X == 0 || Y == 0 || Z == 0 || X == g[0] - 1 || Y == g[1] - 1 ||
+         Z == g[2] - 1;
+}
+
+template <typename T, int P>
+__global__ void k_prolongate(XferArgs a, const T* __restrict__ xc,
+                             T* __restrict__ xf) {
+  constexpr int K = P - 1;
+  const int M = a.dg ? 2 * P : 2 * K + 1;
+  extern __shared__ __align__(16) unsigned char xsm[];
+  T* E = reinterpret_cast<T*>(xsm);
+  T* u = E + M * P;
+  T* t1 = u + P * P * P;
+  T* t2 = t1 + P * P * M;
+  const int C = blockIdx.x;
+  const int cx = C % a.nc[0], cy = (C / a.nc[0]) % a.nc[1],
+            cz = C / (a.nc[0] * a.nc[1]);
+  load_embedding<T, P>(E, a.dg);
+  for (int i = threadIdx.x; i < P * P * P; i += blockDim.x) {
+    const int ix = i % P, iy = (i / P) % P, iz = i / (P * P);
+    T v;
+    if (a.dg) {
+      v = xc[((size_t)C * P * P * P + i) * a.stride + a.col];
+    } else {
+      const int X = cx * K + ix, Y = cy * K + iy, Z = cz * K + iz;
+      v = on_boundary(X, Y, Z, a.gc)
+              ? T(0)
+              : xc[((size_t)X + (size_t)a.gc[0] * (Y + (size_t)a.gc[1] * Z)) *
+                       a.stride +
+                   a.col];
+    }
+    u[i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < P * P * M; i += blockDim.x) {  // x
+    const int fx = i % M, r = i / M;                            // r = iy + P iz
+    T s = T(0);
+    for (int j = 0; j < P; ++j) s += E[fx * P + j] * u[r * P + j];
+    t1[r * M + fx] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < P * M * M; i += blockDim.x) {  // y
+    const int fx = i % M, fy = (i / M) % M, iz = i / (M * M);
+    T s = T(0);
+    for (int j = 0; j < P; ++j) s += E[fy * P + j] * t1[(iz * P + j) * M + fx];
+    t2[i] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < M * M * M; i += blockDim.x) {  // z
+    const int fx = i % M, fy = (i / M) % M, fz = i / (M * M);
+    T s = T(0);
+    for (int j = 0; j < P; ++j) s += E[fz * P + j] * t2[(j * M + fy) * M + fx];
+    if (a.dg) {
+      const int ox = fx / P, oy = fy / P, oz = fz / P;
+      const int F = (2 * cx + ox) + a.nf[0] * ((2 * cy + oy) + a.nf[1] * (2 * cz + oz));
+      const int loc = (fx % P) + P * ((fy % P) + P * (fz % P));
+      xf[((size_t)F * P * P * P + loc) * a.stride + a.col] = s;
+    } else {
+      // each fine node is written by the coarse cell owning it
+      const bool own = (fx < 2 * K || cx == a.nc[0] - 1) &&
+                       (fy < 2 * K || cy == a.nc[1] - 1) &&
+                       (fz < 2 * K || cz == a.nc[2] - 1);
+      if (!own) continue;
+      const int X = 2 * K * cx + fx, Y = 2 * K * cy + fy, Z = 2 * K * cz + fz;
+      const size_t gi = (size_t)X + (size_t)a.gf[0] * (Y + (size_t)a.gf[1] * Z);
+      xf[gi * a.stride + a.col] = on_boundary(X, Y, Z, a.gf) ? T(0) : s;
+    }
+  }
+}
+
+template <typename T, int P>
+__global__ void k_restrict(XferArgs a, const T* __restrict__ xf,
+                           T* __restrict__ xc) {
+  constexpr int K = P - 1;
+  const int M = a.dg ? 2 * P : 2 * K + 1;
+  extern __shared__ __align__(16) unsigned char xsm[];
+  T* E = reinterpret_cast<T*>(xsm);
+  T* u = E + M * P;
+  T* t1 = u + M * M * M;
+  T* t2 = t1 + M * M * P;
+  const int C = blockIdx.x;
+  const int cx = C % a.nc[0], cy = (C / a.nc[0]) % a.nc[1],
+            cz = C / (a.nc[0] * a.nc[1]);
+  load_embedding<T, P>(E, a.dg);
+  for (int i = threadIdx.x; i < M * M * M; i += blockDim.x) {
+    const int fx = i % M, fy = (i / M) % M, fz = i / (M * M);
+    T v;
+    if (a.dg) {
+      const int ox = fx / P, oy = fy / P, oz = fz / P;
+      const int F = (2 * cx + ox) + a.nf[0] * ((2 * cy + oy) + a.nf[1] * (2 * cz + oz));
+      const int loc = (fx % P) + P * ((fy % P) + P * (fz % P));
+      v = xf[((size_t)F * P * P * P + loc) * a.stride + a.col];
+    } else {
+      // a fine node on a coarse-cell face is counted by its owner only
+      const bool own = (fx < 2 * K || cx == a.nc[0] - 1) &&
+                       (fy < 2 * K || cy == a.nc[1] - 1) &&
+                       (fz < 2 * K || cz == a.nc[2] - 1);
+      const int X = 2 * K * cx + fx, Y = 2 * K * cy + fy, Z = 2 * K * cz + fz;
+      v = (!own || on_boundary(X, Y, Z, a.gf))
+              ? T(0)
+              : xf[((size_t)X + (size_t)a.gf[0] * (Y + (size_t)a.gf[1] * Z)) *
+                       a.stride +
+                   a.col];
+    }
+    u[i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < M * M * P; i += blockDim.x) {  // x
+    const int ix = i % P, r = i / P;                            // r = fy + M fz
+    T s = T(0);
+    for (int f = 0; f < M; ++f) s += E[f * P + ix] * u[r * M + f];
+    t1[i] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < M * P * P; i += blockDim.x) {  // y
+    const int ix = i % P, iy = (i / P) % P, fz = i / (P * P);
+    T s = T(0);
+    for (int f = 0; f < M; ++f) s += E[f * P + iy] * t1[(f + M * fz) * P + ix];
+    t2[i] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < P * P * P; i += blockDim.x) {  // z
+    const int ix = i % P, iy = (i / P) % P, iz = i / (P * P);
+    T s = T(0);
+    for (int f = 0; f < M; ++f) s += E[f * P + iz] * t2[(f * P + iy) * P + ix];
+    if (a.dg) {
+      xc[((size_t)C * P * P * P + i) * a.stride + a.col] = s;
+    } else {
+      const int X = cx * K + ix, Y = cy * K + iy, Z = cz * K + iz;
+      if (!on_boundary(X, Y, Z, a.gc))
+        atomicAdd(xc + ((size_t)X + (size_t)a.gc[0] * (Y + (size_t)a.gc[1] * Z)) *
+                           a.stride +
+                      a.col,
+                  s);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions: per-column sums over interleaved [n][R] vectors.  Thread t of a
+// block handles column t % R; the block's per-column sums go to part[], and
+// the last block to finish adds them in block order (deterministic) and
+// applies the finishing operation on device scalars.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool last_block(unsigned* cnt) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return last;
+}
+
+__device__ void column_sums(double v, int R, double* part, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  const int groups = blockDim.x / R;
+  if (threadIdx.x < R) {
+    double s = 0;
+    for (int g = 0; g < groups; ++g) s += sh[threadIdx.x + g * R];
+    part[blockIdx.x * R + threadIdx.x] = s;
+  }
+}
+
+__device__ double finish_sum(int c, int R, const double* part) {
+  double s = 0;
+  for (int b = 0; b < gridDim.x; ++b) s += part[b * R + c];
+  return s;
+}
+
+// dot(a, b) per column and finishing operation on the slot-major scalars
+// st(slot) = scal[slot * R + column]:
+//   op 0: rz = rz0 = dot
+//   op 1: alpha = rz / dot while the column is active (else 0; dot <= 0 or
+//         a stopped column gives 0 and stops it); history records alpha
+//   op 2: beta = dot / rz, rz = dot; with history: record beta, count the
+//         iteration and stop on (r, z) <= 1e-30 (r0, z0)
+//   op 3: bn2 = dot
+__global__ void k_dot(const double* __restrict__ a,
+                      const double* __restrict__ b, int64_t n, int R,
+                      double* part, unsigned* cnt, double* scal, int op,
+                      double* hist, int hidx) {
+  __shared__ double sh[kVecThreads];
+  const int groups = blockDim.x / R;
+  const int c = threadIdx.x % R, g = threadIdx.x / R;
+  double v = 0;
+  if (g < groups)
+    for (int64_t row = (int64_t)blockIdx.x * groups + g; row < n;
+         row += (int64_t)gridDim.x * groups)
+      v += a[row * R + c] * b[row * R + c];
+  column_sums(g < groups ? v : 0.0, R, part, sh);
+  if (!last_block(cnt)) return;
+  if (threadIdx.x < R) {
+    const int cc = threadIdx.x;
+    const double s = finish_sum(cc, R, part);
+#define ST(slot) scal[(slot) * R + cc]
+    switch (op) {
+      case 0:
+        ST(S_RZ) = s;
+        ST(S_RZ0) = s;
+        break;
+      case 1: {
+        const bool go = ST(S_ACTIVE) != 0.0 && s > 0.0 && ST(S_STOP) == 0.0;
+        ST(S_ALPHA) = go ? ST(S_RZ) / s : 0.0;
+        if (!go && hist) ST(S_STOP) = 1.0;
+        if (hist && go) hist[2 * hidx] = ST(S_ALPHA);
+        break;
+      }
+      case 2: {
+        if (ST(S_STOP) != 0.0) break;
+        const double beta = ST(S_RZ) != 0.0 ? s / ST(S_RZ) : 0.0;
+        ST(S_BETA) = beta;
+        ST(S_RZ) = s;
+        if (hist) {
+          hist[2 * hidx + 1] = beta;
+          ST(S_COUNT_IT) = hidx + 1;
+          if (s <= 1e-30 * ST(S_RZ0)) ST(S_STOP) = 1.0;
+        }
+        break;
+      }
+      default:
+        ST(S_BN2) = s;
+    }
+#undef ST
+  }
+  if (threadIdx.x == 0) *cnt = 0u;
+}
+
+// x += alpha p; r -= alpha Ap; rn2 = |r|^2 per column.
+__global__ void k_cg_update(double* __restrict__ x, double* __restrict__ r,
+                            const double* __restrict__ p,
+                            const double* __restrict__ ap, int64_t n, int R,
+                            double* part, unsigned* cnt, double* scal) {
+  __shared__ double sh[kVecThreads];
+  const int groups = blockDim.x / R;
+  const int c = threadIdx.x % R, g = threadIdx.x / R;
+  double v = 0;
+  if (g < groups) {
+    const double al = scal[S_ALPHA * R + c];
+    for (int64_t row = (int64_t)blockIdx.x * groups + g; row < n;
+         row += (int64_t)gridDim.x * groups) {
+      const int64_t i = row * R + c;
+      if (x) x[i] += al * p[i];
+      const double ri = r[i] - al * ap[i];
+      r[i] = ri;
+      v += ri * ri;
+    }
+  }
+  column_sums(g < groups ? v : 0.0, R, part, sh);
+  if (!last_block(cnt)) return;
+  if (threadIdx.x < R)
+    scal[S_RN2 * R + threadIdx.x] = finish_sum(threadIdx.x, R, part);
+  if (threadIdx.x == 0) *cnt = 0u;
+}
+
+// p = z + beta p per column (beta = 0 for inactive columns keeps p = z).
+__global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z,
+                       int64_t n, int R, const double* scal) {
+  GRID_STRIDE(i, n * R) {
+    const int c = (int)(i % R);
+    p[i] = z[i] + scal[S_BETA * R + c] * p[i];
+  }
+}
+
+// Start vector of the eigenvalue estimate: 1 + 0.1 sin(i), 0 on constrained
+// dofs.
+__global__ void k_start_vector(double* v, int64_t n, int g0, int g1, int g2,
+                               int cg) {
+  GRID_STRIDE(i, n) {
+    bool con = false;
+    if (cg) {
+      const int64_t ix = i % g0, iy = (i / g0) % g1,
+                    iz = i / ((int64_t)g0 * g1);
+      con = ix == 0 || iy == 0 || iz == 0 || ix == g0 - 1 || iy == g1 - 1 ||
+            iz == g2 - 1;
+    }
+    v[i] = con ? 0.0 : 1.0 + 0.1 * sin((double)i);
+  }
+}
+
+__global__ void k_jacobi(const double* __restrict__ r,
+                         const double* __restrict__ dinv,
+                         double* __restrict__ z, int64_t n, int R) {
+  GRID_STRIDE(i, n * R) z[i] = dinv[i / R] * r[i];
+}
+
+// Extreme eigenvalues of the Lanczos tridiagonal built from CG coefficients
+// (diag_j = 1/alpha_j + beta_{j-1}/alpha_{j-1}, off_j = sqrt(beta_j)/alpha_j)
+// by Sturm-sequence bisection; single thread.
+__device__ int sturm_count(const double* dg, const double* of, int m,
+                           double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (int j = 0; j < m; ++j) {
+    q = dg[j] - x - (j ? of[j - 1] * of[j - 1] / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void k_lanczos(const double* hist, const double* scal,
+                          double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int m = (int)scal[S_COUNT_IT];
+  if (m > 64) m = 64;
+  if (m < 1) {  // no free dofs: any positive interval is harmless
+    out[0] = out[1] = 1.0;
+    return;
+  }
+  double dg[64], of[64];
+  for (int j = 0; j < m; ++j) {
+    const double al = hist[2 * j], be = hist[2 * j + 1];
+    dg[j] = 1.0 / al + (j ? hist[2 * j - 1] / hist[2 * j - 2] : 0.0);
+    of[j] = sqrt(be) / al;
+  }
+  double lo = 1e300, hi = -1e300;
+  for (int j = 0; j < m; ++j) {
+    double r = (j ? fabs(of[j - 1]) : 0.0) + (j < m - 1 ? fabs(of[j]) : 0.0);
+    lo = fmin(lo, dg[j] - r);
+    hi = fmax(hi, dg[j] + r);
+  }
+  for (int which = 0; which < 2; ++which) {
+    double a = lo, b = hi;
+    const int target = which == 0 ? m - 1 : 0;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (a + b);
+      if (sturm_count(dg, of, m, mid) > target)
+        b = mid;
+      else
+        a = mid;
+      if (b - a <= 1e-12 * fmax(fabs(a), fabs(b))) break;
+    }
+    out[which] = 0.5 * (a + b);  // 0: max, 1: min
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_fill(T* x, T v, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_fill<T><<<vec_grid(n), kVecThreads, 0, s>>>(x, v, n);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+template void launch_fill<double>(double*, double, int64_t, cudaStream_t);
+template void launch_fill<float>(float*, float, int64_t, cudaStream_t);
+
+void launch_invert_diag(const Level& L, double* diag, cudaStream_t s) {
+  k_invert_diag<<<vec_grid(L.ndofs), kVecThreads, 0, s>>>(
+      diag, L.ndofs, L.gdim[0], L.gdim[1], L.gdim[2], L.disc == MFP_CG);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+
+void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
+  k_to_float<<<vec_grid(n), kVecThreads, 0, s>>>(a, b, n);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+void launch_to_double(const float* a, double* b, int64_t n, cudaStream_t s) {
+  k_to_double<<<vec_grid(n), kVecThreads, 0, s>>>(a, b, n);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+
+template <typename T>
+void launch_cheb_first(const T* b, const T* dinv, T* d, T* x, const T* ax,
+                       double c, int64_t n, int nrhs, cudaStream_t s) {
+  k_cheb_first<T><<<vec_grid(n * nrhs), kVecThreads, 0, s>>>(b, dinv, d, x,
+                                                              ax, (T)c, n,
+                                                              nrhs);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+template <typename T>
+void launch_cheb_step(const T* b, const T* dinv, T* d, T* x, const T* ax,
+                      double cd, double cr, int64_t n, int nrhs,
+                      cudaStream_t s) {
+  k_cheb_step<T><<<vec_grid(n * nrhs), kVecThreads, 0, s>>>(
+      b, dinv, d, x, ax, (T)cd, (T)cr, n, nrhs);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+template <typename T>
+void launch_residual(const T* b, const T* ax, T* r, int64_t n,
+                     cudaStream_t s) {
+  k_residual<T><<<vec_grid(n), kVecThreads, 0, s>>>(b, ax, r, n);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+template <typename T>
+void launch_axpy(T* y, const T* x, double a, int64_t n, cudaStream_t s) {
+  k_axpy<T><<<vec_grid(n), kVecThreads, 0, s>>>(y, x, (T)a, n);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+#define INST_VEC(T)                                                           \
+  template void launch_cheb_first<T>(const T*, const T*, T*, T*, const T*,   \
+                                     double, int64_t, int, cudaStream_t);     \
+  template void launch_cheb_step<T>(const T*, const T*, T*, T*, const T*,    \
+                                    double, double, int64_t, int,            \
+                                    cudaStream_t);                            \
+  template void launch_residual<T>(const T*, const T*, T*, int64_t,          \
+                                   cudaStream_t);                             \
+  template void launch_axpy<T>(T*, const T*, double, int64_t, cudaStream_t);
+INST_VEC(double)
+INST_VEC(float)
+
+static XferArgs xfer_args(const Level& fine, const Level& coarse, int stride,
+                          int col) {
+  XferArgs a;
+  for (int d = 0; d < 3; ++d) {
+    a.nc[d] = coarse.n[d];
+    a.gc[d] = coarse.gdim[d];
+    a.gf[d] = fine.gdim[d];
+    a.nf[d] = fine.n[d];
+  }
+  a.dg = fine.disc == MFP_SIPG;
+  a.stride = stride;
+  a.col = col;
+  return a;
+}
+
+template <typename T>
+void launch_prolongate(const Level& fine, const Level& coarse, const T* xc,
+                       T* xf, int stride, int col, cudaStream_t s) {
+  ensure_tables();
+  XferArgs a = xfer_args(fine, coarse, stride, col);
+  dispatch_p(fine.p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
+    const int M = a.dg ? 2 * P : 2 * P - 1;
+    const size_t smem = (size_t)(M * P + P * P * P + P * P * M + P * M * M) *
+                        sizeof(T);
+    auto kern = k_prolongate<T, P>;
+    if (smem > 48 * 1024)
+      MFP_CHECK_CUDA(cudaFuncSetAttribute(
+          kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(int)coarse.ncells, 256, smem, s>>>(a, xc, xf);
+  });
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+template <typename T>
+void launch_restrict(const Level& fine, const Level& coarse, const T* xf,
+                     T* xc, int stride, int col, cudaStream_t s) {
+  ensure_tables();
+  XferArgs a = xfer_args(fine, coarse, stride, col);
+  if (fine.disc == MFP_CG && col == 0)
+    MFP_CHECK_CUDA(cudaMemsetAsync(
+        xc, 0, (size_t)coarse.ndofs * stride * sizeof(T), s));
+  dispatch_p(fine.p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
+    const int M = a.dg ? 2 * P : 2 * P - 1;
+    const size_t smem = (size_t)(M * P + M * M * M + M * M * P + M * P * P) *
+                        sizeof(T);
+    auto kern = k_restrict<T, P>;
+    if (smem > 48 * 1024)
+      MFP_CHECK_CUDA(cudaFuncSetAttribute(
+          kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(int)coarse.ncells, 256, smem, s>>>(a, xf, xc);
+  });
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+template void launch_prolongate<double>(const Level&, const Level&,
+                                        const double*, double*, int, int,
+                                        cudaStream_t);
+template void launch_prolongate<float>(const Level&, const Level&,
+                                       const float*, float*, int, int,
+                                       cudaStream_t);
+template void launch_restrict<double>(const Level&, const Level&,
+                                      const double*, double*, int, int,
+                                      cudaStream_t);
+template void launch_restrict<float>(const Level&, const Level&, const float*,
+                                     float*, int, int, cudaStream_t);
+
+// reductions
+static int red_grid(int64_t rows, int R) {
+  const int groups = kVecThreads / R;
+  int64_t b = (rows + groups - 1) / groups;
+  const int64_t cap = kMaxRedBlocks;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+void launch_dot(const double* a, const double* b, int64_t n, int R,
+                RedScratch& rs, double* scal, int op, double* hist, int hidx,
+                cudaStream_t s) {
+  k_dot<<<red_grid(n, R), kVecThreads, 0, s>>>(a, b, n, R, rs.part, rs.cnt,
+                                               scal, op, hist, hidx);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+void launch_cg_update(double* x, double* r, const double* p, const double* ap,
+                      int64_t n, int R, RedScratch& rs, double* scal,
+                      cudaStream_t s) {
+  k_cg_update<<<red_grid(n, R), kVecThreads, 0, s>>>(x, r, p, ap, n, R,
+                                                     rs.part, rs.cnt, scal);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+void launch_cg_p(double* p, const double* z, int64_t n, int R,
+                 const double* scal, cudaStream_t s) {
+  k_cg_p<<<vec_grid(n * R), kVecThreads, 0, s>>>(p, z, n, R, scal);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+void launch_start_vector(const Level& L, double* v, cudaStream_t s) {
+  k_start_vector<<<vec_grid(L.ndofs), kVecThreads, 0, s>>>(
+      v, L.ndofs, L.gdim[0], L.gdim[1], L.gdim[2], L.disc == MFP_CG);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+void launch_jacobi(const double* r, const double* dinv, double* z, int64_t n,
+                   int R, cudaStream_t s) {
+  k_jacobi<<<vec_grid(n * R), kVecThreads, 0, s>>>(r, dinv, z, n, R);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+void launch_lanczos(const double* hist, const double* scal, double* out,
+                    cudaStream_t s) {
+  k_lanczos<<<1, 32, 0, s>>>(hist, scal, out);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+
+}  // namespace mfp

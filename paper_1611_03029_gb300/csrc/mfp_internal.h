@@ -1,0 +1,232 @@
+// Internal declarations of the mfpoisson library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mfpoisson.h"
+
+namespace mfp {
+
+constexpr int kMaxP = 9;  // k <= 8
+
+// ---------------------------------------------------------------------------
+// 1D reference-element tables on [0, 1] (Sec. 2.1: Lagrange basis in the
+// k+1 Gauss-Lobatto points; Sec. 3: (k+1)-point Gauss quadrature).
+// Row-major p x p matrices, entry [q * p + j].
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DevTab {
+  T S[kMaxP * kMaxP];     // S[q][j]    = phi_j(g_q)       GLL basis at Gauss
+  T D[kMaxP * kMaxP];     // D[q][j]    = l_j'(g_q)        Gauss collocation
+  T Dphi[kMaxP * kMaxP];  // Dphi[q][j] = phi_j'(g_q)      GLL basis slope
+  T E0[kMaxP * kMaxP];    // E0[i][j]   = phi_j(x_i / 2)   left-child embed
+  T E1[kMaxP * kMaxP];    // E1[i][j]   = phi_j((1+x_i)/2) right-child embed
+  T dphi0[kMaxP];         // phi_j'(0)
+  T dphi1[kMaxP];         // phi_j'(1)
+  T w[kMaxP];             // Gauss weights on [0, 1]
+  T g[kMaxP];             // Gauss points on [0, 1]
+  T x[kMaxP];             // GLL points on [0, 1]
+};
+
+struct HostTables {
+  DevTab<double> d[8];  // index k-1
+  DevTab<float> f[8];
+};
+const HostTables& host_tables();
+
+// ---------------------------------------------------------------------------
+// Error state
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+void clear_error();
+// Count of kernels this library has launched (process-wide).
+void note_launch();
+
+struct Fail {
+  mfp_status st;
+};
+#define MFP_CHECK_CUDA(call)                                                  \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      ::mfp::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));   \
+      throw ::mfp::Fail{e_ == cudaErrorMemoryAllocation ? MFP_ERR_OOM         \
+                                                        : MFP_ERR_CUDA};      \
+    }                                                                         \
+  } while (0)
+#define MFP_REQUIRE(cond, msg)                  \
+  do {                                          \
+    if (!(cond)) {                              \
+      ::mfp::set_error(msg);                    \
+      throw ::mfp::Fail{MFP_ERR_ARG};           \
+    }                                           \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Device scalars of the CG iterations, slot-major: scal[slot * R + column]
+// ---------------------------------------------------------------------------
+enum ScalarSlot {
+  S_RZ = 0,      // (r, z)
+  S_RZ0,         // initial (r, z)
+  S_ALPHA,
+  S_BETA,
+  S_RN2,         // |r|^2 after the update
+  S_BN2,         // |b|^2
+  S_ACTIVE,      // 1 while the column iterates
+  S_STOP,        // set on breakdown / convergence of the eigenvalue CG
+  S_COUNT_IT,    // completed eigenvalue-CG iterations
+  S_COUNT
+};
+constexpr int kMaxRedBlocks = 1024;
+constexpr int kMaxRhs = 256;
+struct RedScratch {
+  double* part = nullptr;  // [kMaxRedBlocks][R]
+  unsigned* cnt = nullptr; // zero between launches
+};
+
+// ---------------------------------------------------------------------------
+// Level data
+// ---------------------------------------------------------------------------
+template <typename T>
+struct LevelData {
+  T* G = nullptr;      // curved: [ncells][6][p^3] w det J J^{-1} J^{-T}
+  T* kcell = nullptr;  // per-point coefficient [ncells][p^3] (or null)
+  T* kface = nullptr;  // per-point face coefficient [nfaces][p^2] (or null)
+  T* fdata = nullptr;  // curved SIPG: [nfaces][7][p^2] dA, nJ_L(3), nJ_R(3)
+  T* sigma = nullptr;  // curved SIPG: [nfaces] penalty
+  T* dinv = nullptr;   // [ndofs] inverse Jacobi diagonal
+  bool valid = false;
+};
+
+struct Level {
+  int n[3] = {0, 0, 0};
+  int k = 1, p = 2;
+  int disc = MFP_CG;
+  bool curved = false;
+  int64_t ncells = 0, ndofs = 0, nfaces = 0;
+  int gdim[3] = {0, 0, 0};    // CG node grid
+  int face_off[3] = {0, 0, 0};
+  double h[3] = {0, 0, 0};
+  double kappa = 1.0;
+  double penalty = 1.0;
+  double map_amp = 0.0;
+  double* vol = nullptr;      // curved: cell volumes [ncells]
+  LevelData<double> d64;
+  LevelData<float> d32;
+  // eigenvalue estimate and Chebyshev parameters (Sec. 4.1)
+  double lam_max = 0, lam_min = 0, cheb_lo = 0, cheb_hi = 0;
+  int cheb_degree = 0;
+  int64_t applies = 0;
+  // V-cycle scratch in the V-cycle precision, scratch_rhs columns
+  void* t_res = nullptr;  // operator output / residual / correction
+  void* t_d = nullptr;    // Chebyshev update
+  void* t_x = nullptr;    // iterate (levels below the finest)
+  void* t_b = nullptr;    // right-hand side (levels below the finest)
+  int scratch_rhs = 0;
+};
+
+template <typename T>
+inline LevelData<T>& level_data(Level& L);
+template <>
+inline LevelData<double>& level_data<double>(Level& L) { return L.d64; }
+template <>
+inline LevelData<float>& level_data<float>(Level& L) { return L.d32; }
+
+}  // namespace mfp
+
+struct mfp_ctx {
+  mfp_desc desc;
+  int device = 0;
+  bool has_coef = false;
+  std::vector<mfp::Level> levels;
+  int vprec = MFP_FP64;     // V-cycle arithmetic
+  // outer CG (float64), sized for cg_rhs columns
+  double* cg_r = nullptr;
+  double* cg_p = nullptr;
+  double* cg_ap = nullptr;
+  double* cg_z = nullptr;
+  double* scal = nullptr;   // [S_COUNT][cg_rhs]
+  double* hist = nullptr;   // eigenvalue CG coefficients [128]
+  double* eig_out = nullptr;
+  double* params = nullptr; // device copy of forcing parameters
+  int params_cap = 0;
+  mfp::RedScratch red;
+  double* host_scal = nullptr;  // pinned [S_COUNT][kMaxRhs]
+  float* mix_r = nullptr;       // float V-cycle input / output on the finest
+  float* mix_z = nullptr;
+  int cg_rhs = 0;
+  int64_t vcycles = 0;
+};
+
+namespace mfp {
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the kernel translation units)
+// ---------------------------------------------------------------------------
+void launch_apply_cg(const Level& L, const LevelData<double>& D,
+                     const double* src, double* dst, int stride, int col,
+                     int cpb, cudaStream_t s);
+void launch_apply_cg(const Level& L, const LevelData<float>& D,
+                     const float* src, float* dst, int stride, int col,
+                     int cpb, cudaStream_t s);
+void launch_apply_dg(const Level& L, const LevelData<double>& D,
+                     const double* src, double* dst, int stride, int col,
+                     int cpb, cudaStream_t s);
+void launch_apply_dg(const Level& L, const LevelData<float>& D,
+                     const float* src, float* dst, int stride, int col,
+                     int cpb, cudaStream_t s);
+
+void launch_curved_cell_geometry(Level& L, cudaStream_t s);
+void launch_curved_face_geometry(Level& L, cudaStream_t s);
+void launch_diagonal(const Level& L, double* diag, cudaStream_t s);
+void launch_rhs(const Level& L, int kind, const double* params_dev,
+                int nterms, double* b, int64_t stride, cudaStream_t s);
+void launch_coarsen_coefficient(const Level& fine, const Level& coarse,
+                                cudaStream_t s);
+void launch_start_vector(const Level& L, double* v, cudaStream_t s);
+void launch_gradient(const Level& L, const double* u, const double* lam,
+                     double* gc, double* gf, cudaStream_t s);
+
+template <typename T>
+void launch_prolongate(const Level& fine, const Level& coarse, const T* xc,
+                       T* xf, int stride, int col, cudaStream_t s);
+template <typename T>
+void launch_restrict(const Level& fine, const Level& coarse, const T* xf,
+                     T* xc, int stride, int col, cudaStream_t s);
+
+template <typename T>
+void launch_fill(T* x, T v, int64_t n, cudaStream_t s);
+void launch_invert_diag(const Level& L, double* diag, cudaStream_t s);
+void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t s);
+void launch_to_double(const float* a, double* b, int64_t n, cudaStream_t s);
+template <typename T>
+void launch_cheb_first(const T* b, const T* dinv, T* d, T* x, const T* ax,
+                       double c, int64_t n, int nrhs, cudaStream_t s);
+template <typename T>
+void launch_cheb_step(const T* b, const T* dinv, T* d, T* x, const T* ax,
+                      double cd, double cr, int64_t n, int nrhs,
+                      cudaStream_t s);
+template <typename T>
+void launch_residual(const T* b, const T* ax, T* r, int64_t n,
+                     cudaStream_t s);
+template <typename T>
+void launch_axpy(T* y, const T* x, double a, int64_t n, cudaStream_t s);
+
+void launch_dot(const double* a, const double* b, int64_t n, int R,
+                RedScratch& rs, double* scal, int op, double* hist, int hidx,
+                cudaStream_t s);
+void launch_cg_update(double* x, double* r, const double* p, const double* ap,
+                      int64_t n, int R, RedScratch& rs, double* scal,
+                      cudaStream_t s);
+void launch_cg_p(double* p, const double* z, int64_t n, int R,
+                 const double* scal, cudaStream_t s);
+void launch_jacobi(const double* r, const double* dinv, double* z, int64_t n,
+                   int R, cudaStream_t s);
+void launch_lanczos(const double* hist, const double* scal, double* out,
+                    cudaStream_t s);
+
+}  // namespace mfp

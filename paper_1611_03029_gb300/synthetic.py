@@ -1,0 +1,113 @@
+"""Seeded synthetic inputs shared by the tests, bench.py and the oracle
+legs.  Holds none of the method's arithmetic: random vectors, the
+Gaussian-sum forcing parameters and the log-coefficient Fourier field
+sampled at the physical positions of the Gauss points of a Cartesian mesh.
+"""
+import numpy as np
+
+
+def random_vector(n, seed, ncols=1):
+    """Standard normal float64 values, shape [n] or [n, ncols]."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((n, ncols) if ncols > 1 else n)
+    return v
+
+
+def gaussian_terms(seed, n_terms=8):
+    """Forcing f(x) = sum_j A_j exp(-|x - c_j|^2 / w_j^2): rows (c_x, c_y,
+    c_z, w, A); centres uniform in the unit cube, widths uniform in
+    [0.05, 0.2], amplitudes standard normal, drawn in that order."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0.0, 1.0, (n_terms, 3))
+    w = rng.uniform(0.05, 0.2, n_terms)
+    a = rng.standard_normal(n_terms)
+    return np.column_stack([c, w, a])
+
+
+def gaussian_forcing(params):
+    """The forcing of `gaussian_terms` as a function of points [..., 3]."""
+    params = np.asarray(params)
+
+    def f(x):
+        out = np.zeros(x.shape[:-1])
+        for cx, cy, cz, w, a in params:
+            d2 = ((x[..., 0] - cx) ** 2 + (x[..., 1] - cy) ** 2
+                  + (x[..., 2] - cz) ** 2)
+            out += a * np.exp(-d2 / w ** 2)
+        return out
+    return f
+
+
+def fourier_modes(seed, n_modes=32, kmax=4, amplitude=0.5):
+    """g(x) = sum_m c cos(pi k_m . x + phi_m): k_m uniform in {0..kmax}^3
+    without 0, phi_m uniform in [0, 2 pi), c = amplitude sqrt(2 / n_modes)
+    so that the RMS of g is about `amplitude`."""
+    rng = np.random.default_rng(seed)
+    ks = []
+    while len(ks) < n_modes:
+        k = rng.integers(0, kmax + 1, 3)
+        if k.any():
+            ks.append(k)
+    phi = rng.uniform(0.0, 2 * np.pi, n_modes)
+    c = amplitude * np.sqrt(2.0 / n_modes)
+    return np.array(ks, float), phi, c
+
+
+def fourier_field(modes, x):
+    ks, phi, c = modes
+    arg = np.pi * np.tensordot(x, ks.T, axes=([-1], [0])) + phi
+    return c * np.cos(arg).sum(-1)
+
+
+def _gauss01(p):
+    g, _ = np.polynomial.legendre.leggauss(p)
+    return 0.5 * (g + 1.0)
+
+
+def cell_points(n, p):
+    """Physical Gauss points of every cell of the Cartesian n[0] x n[1] x
+    n[2] mesh of the unit cube: [ncells, p^3, 3], local order x fastest."""
+    g = _gauss01(p)
+    h = [1.0 / m for m in n]
+    cz, cy, cx = np.meshgrid(np.arange(n[2]), np.arange(n[1]),
+                             np.arange(n[0]), indexing="ij")
+    qz, qy, qx = np.meshgrid(g, g, g, indexing="ij")
+    X = (cx.reshape(-1, 1) + qx.reshape(1, -1)) * h[0]
+    Y = (cy.reshape(-1, 1) + qy.reshape(1, -1)) * h[1]
+    Z = (cz.reshape(-1, 1) + qz.reshape(1, -1)) * h[2]
+    return np.stack([X, Y, Z], -1)
+
+
+def face_points(n, p):
+    """Physical Gauss points of every face (x-normal, then y-, then z-normal
+    faces; each direction lexicographic, x fastest; point qa + p qb over the
+    tangential axes a < b): [nfaces, p^2, 3]."""
+    g = _gauss01(p)
+    h = [1.0 / m for m in n]
+    out = []
+    for d in range(3):
+        m = list(n)
+        m[d] += 1
+        t = [e for e in range(3) if e != d]
+        fz, fy, fx = np.meshgrid(np.arange(m[2]), np.arange(m[1]),
+                                 np.arange(m[0]), indexing="ij")
+        fc = [fx.reshape(-1), fy.reshape(-1), fz.reshape(-1)]
+        qb, qa = np.meshgrid(g, g, indexing="ij")
+        q = {t[0]: qa.reshape(-1), t[1]: qb.reshape(-1)}
+        pts = np.empty((fc[0].size, p * p, 3))
+        for e in range(3):
+            if e == d:
+                pts[..., e] = (fc[e] * h[e])[:, None]
+            else:
+                pts[..., e] = (fc[e][:, None] + q[e][None, :]) * h[e]
+        out.append(pts)
+    return np.concatenate(out, 0)
+
+
+def log_coefficient(n, p, seed):
+    """a = exp(g) at all cell and face Gauss points of the Cartesian mesh,
+    g the Fourier field of `fourier_modes(seed)`."""
+    modes = fourier_modes(seed)
+    a_cell = np.exp(fourier_field(modes, cell_points(n, p)))
+    a_face = np.exp(fourier_field(modes, face_points(n, p)))
+    return a_cell, a_face

@@ -1,0 +1,58 @@
+"""Adjoint gradient (not in the paper): parity with the oracle's assembled
+coefficient derivative, and the finite-difference check of the loss
+through GPU solves."""
+import numpy as np
+import pytest
+import torch
+
+from conftest import rel_err
+from oracle import adjoint, fem
+from paper_1611_03029_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("disc,mapping", [("cg", "identity"), ("cg", "sine"),
+                                          ("dg", "identity"), ("dg", "sine")])
+def test_gradient_kernel_matches_oracle(mfp, disc, mapping):
+    n, k = (3, 2, 4), 3
+    amp = 0.1 if mapping == "sine" else 0.0
+    op = mfp.Poisson(*n, k, disc=disc, mapping=mapping, map_param=amp,
+                     n_levels=1)
+    P = fem.Problem(*n, k, disc=disc, mapping=mapping, amp=amp)
+    u = synthetic.random_vector(P.n_dofs, 1)
+    lam = synthetic.random_vector(P.n_dofs, 2)
+    gc, gf = op.gradient(torch.from_numpy(u).cuda(),
+                         torch.from_numpy(lam).cuda())
+    rc, rf = adjoint.gradient(P, u, lam)
+    assert rel_err(gc.cpu().numpy(), rc) <= 1e-12
+    if disc == "dg":
+        assert rel_err(gf.cpu().numpy(), rf) <= 1e-12
+
+
+def test_autograd_gradient_matches_finite_differences(mfp):
+    from paper_1611_03029_gb300.mfpoisson import MFPSolve
+    n, k = (4, 4, 4), 2
+    p = k + 1
+    a_c, a_f = synthetic.log_coefficient(n, p, seed=7)
+    op = mfp.Poisson(*n, k, disc="dg")
+    b = op.rhs(0)
+    ut = torch.from_numpy(synthetic.random_vector(op.n_dofs(), 8) * 0.01).cuda()
+    ac = torch.from_numpy(a_c).cuda().requires_grad_(True)
+    af = torch.from_numpy(a_f).cuda().requires_grad_(True)
+    u = MFPSolve.apply(ac, af, op, b, 1e-13, 300)
+    loss = 0.5 * ((u - ut) ** 2).sum()
+    loss.backward()
+    rng = np.random.default_rng(11)
+    eps = 1e-4 * float(np.abs(a_c).max())
+    for _ in range(3):
+        dc = torch.from_numpy(rng.standard_normal(a_c.shape)).cuda()
+        df = torch.from_numpy(rng.standard_normal(a_f.shape)).cuda()
+        with torch.no_grad():
+            lp = 0.5 * ((MFPSolve.apply(ac + eps * dc, af + eps * df, op, b,
+                                        1e-13, 300) - ut) ** 2).sum()
+            lm = 0.5 * ((MFPSolve.apply(ac - eps * dc, af - eps * df, op, b,
+                                        1e-13, 300) - ut) ** 2).sum()
+        fd = float((lp - lm) / (2 * eps))
+        an = float((ac.grad * dc).sum() + (af.grad * df).sum())
+        assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)

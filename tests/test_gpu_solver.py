@@ -1,0 +1,154 @@
+"""Parity of the multigrid pieces (Sec. 4.1) and of the solves with the
+oracle: Jacobi diagonal, transfer, eigenvalue estimates, Chebyshev
+smoother, coarse solve, V-cycle, and PCG solutions checked against the
+oracle's assembled matrix."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as sla
+import torch
+
+from conftest import rel_err
+from oracle import fem, mg
+from paper_1611_03029_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("cg", "identity", 2, (4, 4, 6)), ("cg", "sine", 3, (4, 2, 4)),
+         ("dg", "identity", 2, (4, 4, 2)), ("dg", "sine", 1, (4, 6, 4))]
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def pair(mfp, disc, mapping, k, n, prec="fp64"):
+    amp = 0.1 if mapping == "sine" else 0.0
+    op = mfp.Poisson(*n, k, disc=disc, mapping=mapping, map_param=amp,
+                     mg_precision=prec)
+    P = fem.Problem(*n, k, disc=disc, mapping=mapping, amp=amp)
+    return op, P
+
+
+@pytest.mark.parametrize("disc,mapping,k,n", CASES)
+def test_inverse_diagonal(mfp, disc, mapping, k, n):
+    op, P = pair(mfp, disc, mapping, k, n)
+    V = mg.VCycle(P)
+    for lv, L in enumerate(V.levels):
+        d = op.inverse_diagonal(lv).cpu().numpy()
+        assert rel_err(d, L.dinv) <= 1e-12
+
+
+@pytest.mark.parametrize("disc,mapping,k,n", CASES)
+def test_transfer(mfp, disc, mapping, k, n):
+    op, P = pair(mfp, disc, mapping, k, n)
+    probs = mg.hierarchy(P)
+    for lv in range(1, len(probs)):
+        Pm = mg.prolongation(probs[lv], probs[lv - 1])
+        xc = synthetic.random_vector(probs[lv - 1].n_dofs, seed=lv)
+        xf = synthetic.random_vector(probs[lv].n_dofs, seed=10 + lv)
+        assert rel_err(op.prolongate(cuda(xc), lv).cpu().numpy(),
+                       Pm @ xc) <= 1e-13
+        assert rel_err(op.restrict(cuda(xf), lv).cpu().numpy(),
+                       Pm.T @ xf) <= 1e-13
+
+
+@pytest.mark.parametrize("disc,mapping,k,n", CASES)
+def test_eigen_estimates_and_smoother(mfp, disc, mapping, k, n):
+    op, P = pair(mfp, disc, mapping, k, n)
+    V = mg.VCycle(P)
+    for lv, L in enumerate(V.levels):
+        info = op.level_info(lv)
+        assert abs(info["lam_max"] - L.lam_max) <= 1e-9 * L.lam_max
+        assert abs(info["lam_min"] - L.lam_min) <= 1e-8 * L.lam_max
+        assert info["degree"] == L.degree
+        b = synthetic.random_vector(L.prob.n_dofs, seed=lv)
+        b[L.prob.constrained()] = 0.0
+        x0 = synthetic.random_vector(L.prob.n_dofs, seed=50 + lv)
+        x0[L.prob.constrained()] = 0.0
+        # the oracle smoother on the GPU's interval isolates the recurrence
+        ref, _ = mg.chebyshev(L.A, L.dinv, b, None, info["lo"], info["hi"],
+                              info["degree"])
+        assert rel_err(op.smooth(cuda(b), level=lv).cpu().numpy(),
+                       ref) <= 1e-11
+        ref, _ = mg.chebyshev(L.A, L.dinv, b, x0, info["lo"], info["hi"],
+                              info["degree"])
+        got = op.smooth(cuda(b), cuda(x0.copy()), level=lv).cpu().numpy()
+        assert rel_err(got, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("disc,mapping,k,n", CASES)
+def test_vcycle(mfp, disc, mapping, k, n):
+    op, P = pair(mfp, disc, mapping, k, n)
+    V = mg.VCycle(P)
+    r = synthetic.random_vector(P.n_dofs, seed=3)
+    r[P.constrained()] = 0.0
+    z = op.vcycle(cuda(r)).cpu().numpy()
+    assert rel_err(z, V.apply(r)) <= 1e-9
+
+
+@pytest.mark.parametrize("disc,mapping,k,n,limit", [
+    ("cg", "identity", 2, (8, 8, 8), 8),      # 17^3 = 4913 dofs
+    ("dg", "identity", 2, (8, 8, 8), 16),
+    ("cg", "sine", 4, (4, 4, 4), 10),
+    ("dg", "sine", 3, (4, 4, 4), 20)])
+def test_solve_fp64(mfp, disc, mapping, k, n, limit):
+    op, P = pair(mfp, disc, mapping, k, n)
+    b = op.rhs(0)
+    x, its, rel = op.solve(b, rtol=1e-10, max_it=100)
+    A = fem.assemble(P)
+    bh, xh = b.cpu().numpy(), x.cpu().numpy()
+    # P10: the GPU solution solves the oracle's system to the tolerance
+    res = np.linalg.norm(bh - A @ xh) / np.linalg.norm(bh)
+    assert res <= 1.05e-10, res
+    assert its[0] <= limit
+    xd = sla.spsolve(A.tocsc(), fem.load_vector(P, fem.sine_forcing))
+    assert rel_err(xh, xd) <= 1e-7
+
+
+@pytest.mark.parametrize("disc", ["cg", "dg"])
+def test_solve_mixed_precision(mfp, disc):
+    n, k = (8, 8, 8), 3
+    op64, P = pair(mfp, disc, "sine", k, n)
+    op32, _ = pair(mfp, disc, "sine", k, n, prec="fp32")
+    b = op64.rhs(0)
+    x64, its64, _ = op64.solve(b, rtol=1e-10)
+    x32, its32, rel32 = op32.solve(b, rtol=1e-10)
+    A = fem.assemble(P)
+    bh = b.cpu().numpy()
+    res = np.linalg.norm(bh - A @ x32.cpu().numpy()) / np.linalg.norm(bh)
+    assert res <= 1.05e-10
+    assert its32[0] <= its64[0] + 3
+    assert rel_err(x32.cpu().numpy(), x64.cpu().numpy()) <= 1e-7
+
+
+def test_batched_solve_matches_single(mfp):
+    n, k, R = (8, 8, 8), 2, 4
+    op, P = pair(mfp, "cg", "identity", k, n)
+    N = op.n_dofs()
+    B = torch.empty(N * R, dtype=torch.float64, device="cuda")
+    params = [synthetic.gaussian_terms(1000 + r) for r in range(R)]
+    for r in range(R):
+        op.rhs(1, params[r], out=B[r:], stride=R)
+    X, its, rel = op.solve(B, n_rhs=R, rtol=1e-10)
+    Xh = X.reshape(N, R).cpu().numpy()
+    Bh = B.reshape(N, R).cpu().numpy()
+    A = fem.assemble(P)
+    for r in range(R):
+        x1, it1, _ = op.solve(torch.from_numpy(Bh[:, r].copy()).cuda())
+        assert its[r] == it1[0]
+        assert rel_err(Xh[:, r], x1.cpu().numpy()) <= 1e-12
+        res = np.linalg.norm(Bh[:, r] - A @ Xh[:, r]) / np.linalg.norm(Bh[:, r])
+        assert res <= 1.05e-10
+
+
+def test_apply_counts_per_iteration(mfp):
+    # C14 reading: 1 (A p) + 4 (pre, zero start) + 1 (residual) + 5 (post)
+    op, _ = pair(mfp, "cg", "identity", 2, (8, 8, 8))
+    b = op.rhs(0)
+    before, _, _ = op.counters()
+    x, its, _ = op.solve(b, rtol=1e-10)
+    after, vc, _ = op.counters()
+    fine = after[-1] - before[-1]
+    # its applies of A p, its V-cycles (the initial one included, the last
+    # iteration's is skipped after convergence)
+    assert fine == its[0] * 1 + its[0] * 10
