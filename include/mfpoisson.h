@@ -131,6 +131,28 @@ mfp_status mfp_set_coefficient(mfp_ctx* ctx, const double* a_cell_dev,
 mfp_status mfp_rhs(mfp_ctx* ctx, int f_kind, const double* params_host,
                    int n_terms, double* b_dev, int64_t stride, void* stream);
 
+/* Same load vector as mfp_rhs, for callers that must not allocate device
+ * memory once their set-up is done: for example applications that hand all
+ * device memory to their own pool up front (a library cudaMalloc would fail
+ * or fragment it), or latency-bound loops that cannot afford the implicit
+ * device synchronisation of cudaMalloc / cudaFree.  mfp_rhs stages the
+ * Gaussian parameters in a device buffer it allocates when n_terms grows;
+ * this entry point copies them into a fixed array compiled into the library
+ * instead (160 KiB, held on every device that loads the library until the
+ * process exits) and calls no allocating routine.
+ *  - n_terms <= 4096 for f_kind 1; larger counts return MFP_ERR_ARG.
+ *  - The first call on a device looks up the array's device address; make
+ *    that first call before any stream capture.
+ *  - All calls share the array, which keeps the last call's parameters.
+ *    Calls whose work overlaps on the GPU (different streams without
+ *    ordering) race on it; calls on one stream are safe.
+ *  - params_host may be pageable (copied before return) or page-locked (it
+ *    must then stay valid until the call's work on `stream` has run).
+ * The paper has no counterpart; arguments and output as in mfp_rhs. */
+mfp_status mfp_rhs_noalloc(mfp_ctx* ctx, int f_kind, const double* params_host,
+                           int n_terms, double* b_dev, int64_t stride,
+                           void* stream);
+
 /* dst = A src on `level` (Eq. 12, plus the SIPG face terms of Eq. 6/7 and
  * identity rows / columns for CG Dirichlet nodes).  prec MFP_FP64 takes
  * double vectors, MFP_FP32 float vectors (FP32 level data must exist, i.e.

@@ -62,6 +62,9 @@ def lib():
             "mfp_set_coefficient": (ctypes.c_int, [vp, vp, vp, vp]),
             "mfp_rhs": (ctypes.c_int, [vp, ctypes.c_int, dp, ctypes.c_int, vp,
                                        ctypes.c_int64, vp]),
+            "mfp_rhs_noalloc": (ctypes.c_int, [vp, ctypes.c_int, dp,
+                                               ctypes.c_int, vp,
+                                               ctypes.c_int64, vp]),
             "mfp_apply": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp,
                                          vp, ctypes.c_int, vp]),
             "mfp_inverse_diagonal": (ctypes.c_int, [vp, ctypes.c_int,

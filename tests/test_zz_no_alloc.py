@@ -1,0 +1,53 @@
+"""mfp_rhs_noalloc serves callers that must not allocate device memory after
+their set-up (memory handed to their own pool, or loops that cannot take
+cudaMalloc's implicit synchronisation).  It must give the same load vector
+as mfp_rhs, which stages the forcing parameters in a buffer the library
+allocates, within the 1e-12 relative tolerance of the other parity tests.
+Two calls in a row with different parameters check that the shared fixed
+parameter array is refreshed on every call."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from conftest import rel_err
+from paper_1611_03029_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+@pytest.mark.parametrize("disc,stride", [("cg", 1), ("dg", 2)])
+def test_rhs_noalloc_matches_rhs(mfp, disc, stride):
+    lib = mfp.lib()
+    op = mfp.Poisson(3, 4, 2, 3, disc=disc, mapping="sine", map_param=0.1,
+                     n_levels=1)
+    n = op.n_dofs()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for seed in (1000, 1001):
+        g = np.ascontiguousarray(synthetic.gaussian_terms(seed))
+        ref = op.rhs(1, g).cpu().numpy()
+        out = torch.full((n * stride,), float("nan"), dtype=torch.float64,
+                         device="cuda")
+        st = lib.mfp_rhs_noalloc(op._h, 1, _dp(g), g.shape[0],
+                                 ctypes.c_void_p(out.data_ptr()), stride, s)
+        assert st == mfp.MFP_OK, lib.mfp_last_error()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()[::stride]
+        assert rel_err(got, ref) <= 1e-12
+
+
+def test_rhs_noalloc_rejects_too_many_terms(mfp):
+    lib = mfp.lib()
+    op = mfp.Poisson(2, 2, 2, 1, n_levels=1)
+    out = torch.zeros(op.n_dofs(), dtype=torch.float64, device="cuda")
+    big = np.zeros((4097, 5))
+    big[:, 3] = 0.1
+    st = lib.mfp_rhs_noalloc(op._h, 1, _dp(big), 4097,
+                             ctypes.c_void_p(out.data_ptr()), 1, None)
+    assert st == mfp.MFP_ERR_ARG
+    assert b"4096" in lib.mfp_last_error()
