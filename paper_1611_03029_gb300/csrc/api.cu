@@ -52,12 +52,10 @@ void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
   if (L.disc == MFP_CG)
     MFP_CHECK_CUDA(
         cudaMemsetAsync(dst, 0, (size_t)L.ndofs * R * sizeof(T), s));
-  for (int r = 0; r < R; ++r) {
-    if (L.disc == MFP_CG)
-      launch_apply_cg(L, D, src, dst, R, r, cpb_override(), s);
-    else
-      launch_apply_dg(L, D, src, dst, R, r, cpb_override(), s);
-  }
+  if (L.disc == MFP_CG)
+    launch_apply_cg(L, D, src, dst, R, cpb_override(), s);
+  else
+    launch_apply_dg(L, D, src, dst, R, cpb_override(), s);
   L.applies += R;
   (void)c;
 }

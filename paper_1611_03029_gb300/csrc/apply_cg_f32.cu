@@ -4,19 +4,17 @@
 namespace mfp {
 
 void launch_apply_cg(const Level& L, const LevelData<float>& D,
-                       const float* src, float* dst, int stride, int col,
-                       int cpb, cudaStream_t s) {
+                       const float* src, float* dst, int nrhs, int cpb,
+                       cudaStream_t s) {
   ensure_tables();
   ApplyArgs<float> a = make_apply_args<float>(L, D, src, dst);
-  a.stride = stride;
-  a.col = col;
-  if (cpb <= 0) cpb = default_cpb(L.p);
+  a.stride = nrhs;
   dispatch_p(L.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;
     if (L.curved)
-      run_apply<P, float, false, true>(a, cpb, s);
+      run_apply_cols<P, float, false, true>(a, nrhs, cpb, s);
     else
-      run_apply<P, float, false, false>(a, cpb, s);
+      run_apply_cols<P, float, false, false>(a, nrhs, cpb, s);
   });
 }
 

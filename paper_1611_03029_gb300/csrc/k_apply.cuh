@@ -39,7 +39,9 @@ struct ApplyArgs {
   T fa[3];  // Cartesian: face area of a d-face
   T sg[3];  // Cartesian: penalty of a d-face
   int stride;  // batched layout: value i of column r at [i*stride + r]
-  int col;
+  int col;     // first column of this launch
+  int cpb;     // cells per block
+  int ncols;   // columns per block
 };
 
 template <int P>
@@ -236,22 +238,37 @@ __device__ __forceinline__ void face_contrib(
   __syncthreads();
 }
 
+// Work decomposition: a block owns `cpb` cells and `ncols` right-hand-side
+// columns; each (cell, column) pair is a virtual cell worked on by p*p
+// threads (thread = one line of each sweep).  The block is padded to whole
+// warps; padding threads work on a dummy virtual cell and write nothing to
+// global memory.  Columns of one cell are adjacent threads, so batched
+// vectors [N][R] are read coalesced and the geometry of a cell is loaded
+// once per point for all its columns (same address across the warp).
 template <int P, typename T, bool DG, bool CURVED>
 __global__ void k_apply(const ApplyArgs<T> a) {
   constexpr int P2 = P * P, P3 = P2 * P;
+  // float geometry is prefetched into registers during the gather (the float
+  // apply is latency-bound); float64 is bound by the FP64 pipe instead
+  constexpr bool PREFETCH = CURVED && sizeof(T) == 4 && P <= 7;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
-  const int cpb = blockDim.x / P2;
-  const int lc = threadIdx.x / P2;
-  const int t = threadIdx.x - lc * P2;
-  const int ta = t % P, tb = t / P;
-  T* base = sm + (size_t)lc * cell_smem_elems<T, P, DG>();
+  const int cpb = a.cpb, nc = a.ncols;
+  const int items = cpb * nc * P2;
+  const int tid = threadIdx.x;
+  const bool item_ok = tid < items;
+  const int rr = tid % nc;
+  const int rest = tid / nc;
+  const int ta = rest % P, tb = (rest / P) % P;
+  const int lc = item_ok ? rest / P2 : 0;
+  const int v = item_ok ? lc * nc + rr : cpb * nc;  // dummy slot for padding
+  T* base = sm + (size_t)v * cell_smem_elems<T, P, DG>();
   T* Aq = base;
   T* GX = base + P3;
   T* GY = base + 2 * P3;
   T* U = base + 3 * P3;   // DG: nodal input
   T* FS = base + 4 * P3;  // DG: face scratch [8][p^2]
-  T* tabs = sm + (size_t)cpb * cell_smem_elems<T, P, DG>();
+  T* tabs = sm + (size_t)(cpb * nc + 1) * cell_smem_elems<T, P, DG>();
   T* sS = tabs;
   T* sD = tabs + P2;
   T* sDphi = tabs + 2 * P2;
@@ -261,22 +278,34 @@ __global__ void k_apply(const ApplyArgs<T> a) {
   load_tables_shared<T, P>(sS, sD, sDphi, s0, s1, sw);
   __syncthreads();
   const int gx0 = a.g[0], gy0 = a.g[1], gz0 = a.g[2];
+  ApplyArgs<T> ac = a;
+  ac.col = a.col + rr;
 
   for (int cbase = blockIdx.x * cpb; cbase < a.ncells;
        cbase += gridDim.x * cpb) {
     const int cell = cbase + lc;
-    const bool active = cell < a.ncells;
+    const bool active = item_ok && cell < a.ncells;
     const int cc = active ? cell : 0;
     const int cx = cc % a.n[0];
     const int cy = (cc / a.n[0]) % a.n[1];
     const int cz = cc / (a.n[0] * a.n[1]);
+    const int col = ac.col;
     T r[P], o[P];
+    T gp[PREFETCH ? 6 : 1][PREFETCH ? P : 1];
+    if constexpr (PREFETCH) {
+#pragma unroll
+      for (int qz = 0; qz < P; ++qz) {
+        const T* Gp = a.G + (size_t)cc * 6 * P3 + idx3<P>(ta, tb, qz);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) gp[c][qz] = Gp[c * P3];
+      }
+    }
     // ---- gather the z-line (x = ta, y = tb)
     if constexpr (DG) {
 #pragma unroll
       for (int z = 0; z < P; ++z) {
         const size_t gi = (size_t)cc * P3 + idx3<P>(ta, tb, z);
-        r[z] = active ? a.src[gi * a.stride + a.col] : T(0);
+        r[z] = active ? a.src[gi * a.stride + col] : T(0);
         U[idx3<P>(ta, tb, z)] = r[z];
       }
     } else {
@@ -287,7 +316,7 @@ __global__ void k_apply(const ApplyArgs<T> a) {
         const int Z = cz * (P - 1) + z;
         const bool con = bxy || Z == 0 || Z == gz0 - 1;
         const size_t gi = (size_t)X + (size_t)gx0 * (Y + (size_t)gy0 * Z);
-        r[z] = (active && !con) ? a.src[gi * a.stride + a.col] : T(0);
+        r[z] = (active && !con) ? a.src[gi * a.stride + col] : T(0);
       }
     }
     // ---- values at Gauss points: z (registers), y, x
@@ -331,9 +360,15 @@ __global__ void k_apply(const ApplyArgs<T> a) {
         const T kap = a.kcell ? a.kcell[(size_t)cc * P3 + q] : a.kappa;
         T tx, ty, tz;
         if constexpr (CURVED) {
-          const T* Gp = a.G + (size_t)cc * 6 * P3 + q;
-          const T g0 = Gp[0], g1 = Gp[P3], g2 = Gp[2 * P3], g3 = Gp[3 * P3],
-                  g4 = Gp[4 * P3], g5 = Gp[5 * P3];
+          T g0, g1, g2, g3, g4, g5;
+          if constexpr (PREFETCH) {
+            g0 = gp[0][qz]; g1 = gp[1][qz]; g2 = gp[2][qz];
+            g3 = gp[3][qz]; g4 = gp[4][qz]; g5 = gp[5][qz];
+          } else {
+            const T* Gp = a.G + (size_t)cc * 6 * P3 + q;
+            g0 = Gp[0]; g1 = Gp[P3]; g2 = Gp[2 * P3];
+            g3 = Gp[3 * P3]; g4 = Gp[4 * P3]; g5 = Gp[5 * P3];
+          }
           tx = kap * (g0 * ux + g1 * uy + g2 * uz);
           ty = kap * (g1 * ux + g3 * uy + g4 * uz);
           tz = kap * (g2 * ux + g4 * uy + g5 * uz);
@@ -388,7 +423,7 @@ __global__ void k_apply(const ApplyArgs<T> a) {
           const bool con = bxy || Z == 0 || Z == gz0 - 1;
           const size_t gi =
               ((size_t)X + (size_t)gx0 * (Y + (size_t)gy0 * Z)) * a.stride +
-              a.col;
+              col;
           if (con)
             a.dst[gi] = a.src[gi];  // identity row (same value from all cells)
           else
@@ -400,23 +435,23 @@ __global__ void k_apply(const ApplyArgs<T> a) {
 #pragma unroll
       for (int z = 0; z < P; ++z) Aq[idx3<P>(ta, tb, z)] = o[z];
       __syncthreads();
-      face_contrib<P, T, CURVED, 0, 0>(a, active, cx, cy, cz, U, Aq, FS, sS,
+      face_contrib<P, T, CURVED, 0, 0>(ac, active, cx, cy, cz, U, Aq, FS, sS,
                                        sD, s0, s1, sw, ta, tb);
-      face_contrib<P, T, CURVED, 0, 1>(a, active, cx, cy, cz, U, Aq, FS, sS,
+      face_contrib<P, T, CURVED, 0, 1>(ac, active, cx, cy, cz, U, Aq, FS, sS,
                                        sD, s0, s1, sw, ta, tb);
-      face_contrib<P, T, CURVED, 1, 0>(a, active, cx, cy, cz, U, Aq, FS, sS,
+      face_contrib<P, T, CURVED, 1, 0>(ac, active, cx, cy, cz, U, Aq, FS, sS,
                                        sD, s0, s1, sw, ta, tb);
-      face_contrib<P, T, CURVED, 1, 1>(a, active, cx, cy, cz, U, Aq, FS, sS,
+      face_contrib<P, T, CURVED, 1, 1>(ac, active, cx, cy, cz, U, Aq, FS, sS,
                                        sD, s0, s1, sw, ta, tb);
-      face_contrib<P, T, CURVED, 2, 0>(a, active, cx, cy, cz, U, Aq, FS, sS,
+      face_contrib<P, T, CURVED, 2, 0>(ac, active, cx, cy, cz, U, Aq, FS, sS,
                                        sD, s0, s1, sw, ta, tb);
-      face_contrib<P, T, CURVED, 2, 1>(a, active, cx, cy, cz, U, Aq, FS, sS,
+      face_contrib<P, T, CURVED, 2, 1>(ac, active, cx, cy, cz, U, Aq, FS, sS,
                                        sD, s0, s1, sw, ta, tb);
       if (active) {
 #pragma unroll
         for (int z = 0; z < P; ++z) {
           const size_t gi = (size_t)cc * P3 + idx3<P>(ta, tb, z);
-          a.dst[gi * a.stride + a.col] = Aq[idx3<P>(ta, tb, z)];
+          a.dst[gi * a.stride + col] = Aq[idx3<P>(ta, tb, z)];
         }
       }
       __syncthreads();
@@ -424,40 +459,65 @@ __global__ void k_apply(const ApplyArgs<T> a) {
   }
 }
 
+// Cells per block for one column: the block (padded to whole warps) keeps
+// at least 97 % of its lanes busy: p^2 * cpb close to 128 or 256.
 inline int default_cpb(int p) {
   switch (p) {
     case 2: return 32;
-    case 3: return 12;
+    case 3: return 14;
     case 4: return 8;
-    case 5: return 4;
-    case 6: return 3;
-    case 7: return 2;
-    case 8: return 2;
-    default: return 1;
+    case 5: return 5;
+    case 6: return 7;
+    case 7: return 5;
+    case 8: return 4;
+    default: return 3;
   }
 }
 
 template <int P, typename T, bool DG, bool CURVED>
-void run_apply(const ApplyArgs<T>& a, int cpb, cudaStream_t s) {
+void run_apply(ApplyArgs<T> a, int cpb, int ncols, cudaStream_t s) {
   constexpr int P2 = P * P;
-  const size_t smem =
-      ((size_t)cpb * cell_smem_elems<T, P, DG>() + table_smem_elems<P>()) *
-      sizeof(T);
+  a.cpb = cpb;
+  a.ncols = ncols;
+  const int threads = ((cpb * ncols * P2 + 31) / 32) * 32;
+  const size_t smem = ((size_t)(cpb * ncols + 1) * cell_smem_elems<T, P, DG>() +
+                       table_smem_elems<P>()) *
+                      sizeof(T);
   auto kern = k_apply<P, T, DG, CURVED>;
   if (smem > 48 * 1024)
     MFP_CHECK_CUDA(cudaFuncSetAttribute(
         kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   MFP_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, kern, cpb * P2, smem));
+      &per_sm, kern, threads, smem));
   if (per_sm < 1) per_sm = 1;
   const int64_t need = (a.ncells + cpb - 1) / cpb;
   const int64_t cap = (int64_t)per_sm * sm_count();
   const int grid = (int)(need < cap ? need : cap);
   if (grid <= 0) return;
-  kern<<<grid, cpb * P2, smem, s>>>(a);
+  kern<<<grid, threads, smem, s>>>(a);
   MFP_CHECK_CUDA(cudaGetLastError());
   note_launch();
+}
+
+// Launch plan for R columns: columns per launch limited by 1024 threads per
+// block; cells per block from `cpb` (0 = default) for one column, divided
+// among the columns.
+template <int P, typename T, bool DG, bool CURVED>
+void run_apply_cols(const ApplyArgs<T>& a0, int R, int cpb,
+                    cudaStream_t s) {
+  constexpr int P2 = P * P;
+  const int maxcols = 1024 / P2 > 0 ? 1024 / P2 : 1;
+  if (cpb <= 0) cpb = default_cpb(P);
+  for (int c0 = 0; c0 < R; c0 += maxcols) {
+    const int nc = R - c0 < maxcols ? R - c0 : maxcols;
+    int cells = cpb / nc;
+    if (cells < 1) cells = 1;
+    while (cells > 1 && cells * nc * P2 > 1024) --cells;
+    ApplyArgs<T> a = a0;
+    a.col = c0;
+    run_apply<P, T, DG, CURVED>(a, cells, nc, s);
+  }
 }
 
 template <typename T>
@@ -488,6 +548,8 @@ ApplyArgs<T> make_apply_args(const Level& L, const LevelData<T>& D,
   }
   a.stride = 1;
   a.col = 0;
+  a.cpb = 1;
+  a.ncols = 1;
   return a;
 }
 

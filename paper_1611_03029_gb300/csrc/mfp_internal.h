@@ -167,18 +167,20 @@ namespace mfp {
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the kernel translation units)
 // ---------------------------------------------------------------------------
+// dst = A src for nrhs interleaved columns ([N][nrhs]); cpb = cells per
+// block for one column (0: default).
 void launch_apply_cg(const Level& L, const LevelData<double>& D,
-                     const double* src, double* dst, int stride, int col,
-                     int cpb, cudaStream_t s);
+                     const double* src, double* dst, int nrhs, int cpb,
+                     cudaStream_t s);
 void launch_apply_cg(const Level& L, const LevelData<float>& D,
-                     const float* src, float* dst, int stride, int col,
-                     int cpb, cudaStream_t s);
+                     const float* src, float* dst, int nrhs, int cpb,
+                     cudaStream_t s);
 void launch_apply_dg(const Level& L, const LevelData<double>& D,
-                     const double* src, double* dst, int stride, int col,
-                     int cpb, cudaStream_t s);
+                     const double* src, double* dst, int nrhs, int cpb,
+                     cudaStream_t s);
 void launch_apply_dg(const Level& L, const LevelData<float>& D,
-                     const float* src, float* dst, int stride, int col,
-                     int cpb, cudaStream_t s);
+                     const float* src, float* dst, int nrhs, int cpb,
+                     cudaStream_t s);
 
 void launch_curved_cell_geometry(Level& L, cudaStream_t s);
 void launch_curved_face_geometry(Level& L, cudaStream_t s);
