@@ -218,6 +218,17 @@ mfp_status mfp_gradient(mfp_ctx* ctx, const double* u_dev,
                         const double* lambda_dev, double* g_cell_dev,
                         double* g_face_dev, void* stream);
 
+/* Autotuner (not in the paper): times the operator apply of `level` in
+ * precision `prec` for n_rhs columns with every admissible number of cells
+ * per thread block (1..32, at most 1024 threads per block), on scratch
+ * vectors it allocates and frees itself, and keeps the fastest choice in the
+ * context for later applies with the same (level, prec, n_rhs); captured
+ * V-cycles are re-captured.  Synchronises `stream`.  cells_out / ms_out
+ * receive the choice and its time per apply (may be NULL).  The environment
+ * variable MFP_CELLS_PER_BLOCK overrides every choice. */
+mfp_status mfp_autotune(mfp_ctx* ctx, int level, int prec, int n_rhs,
+                        int* cells_out, double* ms_out, void* stream);
+
 /* Counters: operator applications per level since creation (array of
  * mfp_n_levels entries), V-cycles since creation, and the number of CUDA
  * kernels this library has launched in the process.  NULL outputs are

@@ -16,6 +16,8 @@ void set_error(const std::string& msg) { g_err = msg; }
 void clear_error() { g_err.clear(); }
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launches_total() { return g_launches.load(); }
+void add_launches(int64_t n) { g_launches.fetch_add(n); }
 
 namespace {
 
@@ -43,6 +45,25 @@ int cpb_override() {
   return e ? std::atoi(e) : 0;
 }
 
+int64_t tune_key(int level, int prec, int R) {
+  return ((int64_t)level * 4 + prec) * 4096 + R;
+}
+
+// Cells per block for an apply: environment override, else the autotuned
+// value of this (level, precision, columns), else 0 (kernel default).
+int cells_for(const mfp_ctx* c, int level, int prec, int R) {
+  const int o = cpb_override();
+  if (o > 0) return o;
+  const int64_t k = tune_key(level, prec, R);
+  for (const auto& kv : c->tuned)
+    if (kv.first == k) return kv.second;
+  return 0;
+}
+
+int level_index(const mfp_ctx* c, const Level& L) {
+  return (int)(&L - c->levels.data());
+}
+
 template <typename T>
 void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
                  cudaStream_t s) {
@@ -52,12 +73,13 @@ void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
   if (L.disc == MFP_CG)
     MFP_CHECK_CUDA(
         cudaMemsetAsync(dst, 0, (size_t)L.ndofs * R * sizeof(T), s));
+  const int prec = sizeof(T) == 8 ? MFP_FP64 : MFP_FP32;
+  const int cells = cells_for(c, level_index(c, L), prec, R);
   if (L.disc == MFP_CG)
-    launch_apply_cg(L, D, src, dst, R, cpb_override(), s);
+    launch_apply_cg(L, D, src, dst, R, cells, s);
   else
-    launch_apply_dg(L, D, src, dst, R, cpb_override(), s);
+    launch_apply_dg(L, D, src, dst, R, cells, s);
   L.applies += R;
-  (void)c;
 }
 
 void cheb_coeffs_first(const Level& L, double& c) {
@@ -96,13 +118,11 @@ void smooth(mfp_ctx* c, int l, const T* b, T* x, bool zero, int R,
 template <typename T>
 void prolongate(mfp_ctx* c, int l, const T* xc, T* xf, int R,
                 cudaStream_t s) {
-  for (int r = 0; r < R; ++r)
-    launch_prolongate<T>(c->levels[l], c->levels[l - 1], xc, xf, R, r, s);
+  launch_prolongate<T>(c->levels[l], c->levels[l - 1], xc, xf, R, 0, s);
 }
 template <typename T>
 void restrict_(mfp_ctx* c, int l, const T* xf, T* xc, int R, cudaStream_t s) {
-  for (int r = 0; r < R; ++r)
-    launch_restrict<T>(c->levels[l], c->levels[l - 1], xf, xc, R, r, s);
+  launch_restrict<T>(c->levels[l], c->levels[l - 1], xf, xc, R, 0, s);
 }
 
 // V-cycle on level l for A x = b, x overwritten (zero initial guess).
@@ -127,8 +147,13 @@ void vcycle_level(mfp_ctx* c, int l, const T* b, T* x, int R,
   smooth<T>(c, l, b, x, false, R, s);
 }
 
+void drop_graphs(mfp_ctx* c);
+
 void ensure_scratch(mfp_ctx* c, int R) {
   MFP_REQUIRE(R >= 1 && R <= kMaxRhs, "n_rhs must be in 1..256");
+  bool grow = c->cg_rhs < R;
+  for (auto& L : c->levels) grow = grow || L.scratch_rhs < R;
+  if (grow) drop_graphs(c);
   const size_t vb = c->vprec == MFP_FP32 ? sizeof(float) : sizeof(double);
   for (size_t l = 0; l < c->levels.size(); ++l) {
     Level& L = c->levels[l];
@@ -177,6 +202,70 @@ void vcycle_top(mfp_ctx* c, const double* r, double* z, int R,
     vcycle_level<double>(c, top, r, z, R, s);
   }
   c->vcycles += R;
+}
+
+void drop_graphs(mfp_ctx* c) {
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+bool graphs_enabled() {
+  const char* e = std::getenv("MFP_CUDA_GRAPHS");
+  return !(e && e[0] == '0');
+}
+
+// The solve's V-cycle (internal buffers cg_r -> cg_z) replayed from a CUDA
+// graph captured on its first use for this column count.  The capture does
+// not execute work, so the counter increments it made are taken back and
+// re-added on every replay.
+void vcycle_solve(mfp_ctx* c, int R, cudaStream_t s) {
+  if (!graphs_enabled()) {
+    vcycle_top(c, c->cg_r, c->cg_z, R, s);
+    return;
+  }
+  if ((int)c->graphs.size() <= R) c->graphs.resize(R + 1);
+  mfp_ctx::VGraph& g = c->graphs[R];
+  if (!g.exec) {
+    std::vector<int64_t> a0;
+    for (auto& L : c->levels) a0.push_back(L.applies);
+    const int64_t l0 = launches_total(), v0 = c->vcycles;
+    // capture on the context's own stream (the legacy default stream cannot
+    // be captured); the graph is then launched on the caller's stream
+    if (!c->cap_stream)
+      MFP_CHECK_CUDA(
+          cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = c->cap_stream;
+    MFP_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t graph = nullptr;
+    try {
+      vcycle_top(c, c->cg_r, c->cg_z, R, cs);
+    } catch (...) {
+      cudaStreamEndCapture(cs, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      for (size_t l = 0; l < c->levels.size(); ++l) c->levels[l].applies = a0[l];
+      throw;
+    }
+    MFP_CHECK_CUDA(cudaStreamEndCapture(cs, &graph));
+    cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    MFP_CHECK_CUDA(e);
+    g.applies.resize(c->levels.size());
+    for (size_t l = 0; l < c->levels.size(); ++l) {
+      g.applies[l] = c->levels[l].applies - a0[l];
+      c->levels[l].applies = a0[l];
+    }
+    g.launches = launches_total() - l0;
+    add_launches(-g.launches);
+    g.vcycles = c->vcycles - v0;
+    c->vcycles = v0;
+  }
+  MFP_CHECK_CUDA(cudaGraphLaunch(g.exec, s));
+  for (size_t l = 0; l < c->levels.size(); ++l)
+    c->levels[l].applies += g.applies[l];
+  add_launches(g.launches);
+  c->vcycles += g.vcycles;
 }
 
 // Eigenvalue estimate of D^{-1} A on level l (Sec. 4.1): Jacobi-PCG from the
@@ -254,6 +343,9 @@ void free_level(Level& L) {
 }
 
 void free_ctx(mfp_ctx* c) {
+  drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
   for (auto& L : c->levels) free_level(L);
   dfree(c->cg_r);
   dfree(c->cg_p);
@@ -279,6 +371,7 @@ void to_float_array(const double* a, float*& b, int64_t n, cudaStream_t s) {
 
 // Geometry, diagonal and eigenvalue estimate of every level.
 void build_levels(mfp_ctx* c, cudaStream_t s) {
+  drop_graphs(c);  // Chebyshev parameters are baked into captured V-cycles
   const bool f32 = c->vprec == MFP_FP32;
   for (size_t l = 0; l < c->levels.size(); ++l) {
     Level& L = c->levels[l];
@@ -731,7 +824,7 @@ mfp_status mfp_solve(mfp_ctx* c, const double* b, double* x, int R,
     }
     if (n_active == 0) break;
     if (changed) upload_active();
-    vcycle_top(c, c->cg_r, c->cg_z, R, s);
+    vcycle_solve(c, R, s);
     launch_dot(c->cg_r, c->cg_z, n, R, c->red, c->scal, 2, nullptr, 0, s);
     launch_cg_p(c->cg_p, c->cg_z, n, R, c->scal, s);
   }
@@ -753,6 +846,87 @@ mfp_status mfp_gradient(mfp_ctx* c, const double* u, const double* lam,
   MFP_REQUIRE(c && u && lam && gc, "null argument");
   MFP_REQUIRE(c->desc.disc == MFP_CG || gf, "SIPG needs g_face");
   launch_gradient(c->levels.back(), u, lam, gc, gf, st(stream));
+  API_END
+}
+
+mfp_status mfp_autotune(mfp_ctx* c, int level, int prec, int n_rhs,
+                        int* cells_out, double* ms_out, void* stream) {
+  API_BEGIN
+  Level& L = get_level(c, level);
+  MFP_REQUIRE(n_rhs >= 1 && n_rhs <= kMaxRhs, "n_rhs must be in 1..256");
+  const int pr = prec_of(prec);
+  cudaStream_t s = st(stream);
+  const size_t esz = pr == MFP_FP64 ? sizeof(double) : sizeof(float);
+  const size_t bytes = (size_t)L.ndofs * n_rhs * esz;
+  void *src = nullptr, *dst = nullptr;
+  MFP_CHECK_CUDA(cudaMalloc(&src, bytes));
+  cudaError_t e = cudaMalloc(&dst, bytes);
+  if (e != cudaSuccess) {
+    cudaFree(src);
+    MFP_CHECK_CUDA(e);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int64_t key = tune_key(level, pr, n_rhs);
+  // drop a previous choice so the candidates below are what gets timed
+  for (size_t i = 0; i < c->tuned.size(); ++i)
+    if (c->tuned[i].first == key) {
+      c->tuned.erase(c->tuned.begin() + i);
+      break;
+    }
+  int best = 0;
+  float best_ms = 1e30f;
+  const int64_t a0 = L.applies;
+  try {
+    MFP_CHECK_CUDA(cudaEventCreate(&e0));
+    MFP_CHECK_CUDA(cudaEventCreate(&e1));
+    if (pr == MFP_FP64)
+      launch_fill<double>(static_cast<double*>(src), 1.0, L.ndofs * n_rhs, s);
+    else
+      launch_fill<float>(static_cast<float*>(src), 1.0f, L.ndofs * n_rhs, s);
+    const int p2 = L.p * L.p;
+    const int cand[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32};
+    for (int cells : cand) {
+      if ((int64_t)cells * n_rhs * p2 > 1024 && cells > 1) break;
+      if (cells > L.ncells) break;
+      c->tuned.push_back({key, cells});
+      auto run = [&]() {
+        if (pr == MFP_FP64)
+          apply_level<double>(c, L, static_cast<const double*>(src),
+                              static_cast<double*>(dst), n_rhs, s);
+        else
+          apply_level<float>(c, L, static_cast<const float*>(src),
+                             static_cast<float*>(dst), n_rhs, s);
+      };
+      run();
+      MFP_CHECK_CUDA(cudaEventRecord(e0, s));
+      for (int it = 0; it < 3; ++it) run();
+      MFP_CHECK_CUDA(cudaEventRecord(e1, s));
+      MFP_CHECK_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      MFP_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= 3;
+      c->tuned.pop_back();
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cells;
+      }
+    }
+  } catch (...) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(src);
+    cudaFree(dst);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(src);
+  cudaFree(dst);
+  L.applies = a0;
+  c->tuned.push_back({key, best});
+  drop_graphs(c);  // captured V-cycles used the previous launch shapes
+  if (cells_out) *cells_out = best;
+  if (ms_out) *ms_out = best_ms;
   API_END
 }
 

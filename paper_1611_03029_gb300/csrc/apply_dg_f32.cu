@@ -4,7 +4,7 @@
 namespace mfp {
 
 void launch_apply_dg(const Level& L, const LevelData<float>& D,
-                       const float* src, float* dst, int nrhs, int cpb,
+                       const float* src, float* dst, int nrhs, int cells,
                        cudaStream_t s) {
   ensure_tables();
   ApplyArgs<float> a = make_apply_args<float>(L, D, src, dst);
@@ -12,9 +12,9 @@ void launch_apply_dg(const Level& L, const LevelData<float>& D,
   dispatch_p(L.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;
     if (L.curved)
-      run_apply_cols<P, float, true, true>(a, nrhs, cpb, s);
+      run_apply_cols<P, float, true, true>(a, nrhs, cells, s);
     else
-      run_apply_cols<P, float, true, false>(a, nrhs, cpb, s);
+      run_apply_cols<P, float, true, false>(a, nrhs, cells, s);
   });
 }
 

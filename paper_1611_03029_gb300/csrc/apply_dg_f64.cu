@@ -4,7 +4,7 @@
 namespace mfp {
 
 void launch_apply_dg(const Level& L, const LevelData<double>& D,
-                       const double* src, double* dst, int nrhs, int cpb,
+                       const double* src, double* dst, int nrhs, int cells,
                        cudaStream_t s) {
   ensure_tables();
   ApplyArgs<double> a = make_apply_args<double>(L, D, src, dst);
@@ -12,9 +12,9 @@ void launch_apply_dg(const Level& L, const LevelData<double>& D,
   dispatch_p(L.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;
     if (L.curved)
-      run_apply_cols<P, double, true, true>(a, nrhs, cpb, s);
+      run_apply_cols<P, double, true, true>(a, nrhs, cells, s);
     else
-      run_apply_cols<P, double, true, false>(a, nrhs, cpb, s);
+      run_apply_cols<P, double, true, false>(a, nrhs, cells, s);
   });
 }
 

@@ -501,17 +501,16 @@ void run_apply(ApplyArgs<T> a, int cpb, int ncols, cudaStream_t s) {
 }
 
 // Launch plan for R columns: columns per launch limited by 1024 threads per
-// block; cells per block from `cpb` (0 = default) for one column, divided
-// among the columns.
+// block; cells per block `cells_req` (0: the one-column default divided
+// among the columns).
 template <int P, typename T, bool DG, bool CURVED>
-void run_apply_cols(const ApplyArgs<T>& a0, int R, int cpb,
+void run_apply_cols(const ApplyArgs<T>& a0, int R, int cells_req,
                     cudaStream_t s) {
   constexpr int P2 = P * P;
   const int maxcols = 1024 / P2 > 0 ? 1024 / P2 : 1;
-  if (cpb <= 0) cpb = default_cpb(P);
   for (int c0 = 0; c0 < R; c0 += maxcols) {
     const int nc = R - c0 < maxcols ? R - c0 : maxcols;
-    int cells = cpb / nc;
+    int cells = cells_req > 0 ? cells_req : default_cpb(P) / nc;
     if (cells < 1) cells = 1;
     while (cells > 1 && cells * nc * P2 > 1024) --cells;
     ApplyArgs<T> a = a0;

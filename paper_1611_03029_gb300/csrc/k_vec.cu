@@ -143,6 +143,7 @@ __global__ void k_prolongate(XferArgs a, const T* __restrict__ xc,
   T* t1 = u + P * P * P;
   T* t2 = t1 + P * P * M;
   const int C = blockIdx.x;
+  a.col = blockIdx.y;  // one column of the batch per grid row
   const int cx = C % a.nc[0], cy = (C / a.nc[0]) % a.nc[1],
             cz = C / (a.nc[0] * a.nc[1]);
   load_embedding<T, P>(E, a.dg);
@@ -209,6 +210,7 @@ __global__ void k_restrict(XferArgs a, const T* __restrict__ xf,
   T* t1 = u + M * M * M;
   T* t2 = t1 + M * M * P;
   const int C = blockIdx.x;
+  a.col = blockIdx.y;  // one column of the batch per grid row
   const int cx = C % a.nc[0], cy = (C / a.nc[0]) % a.nc[1],
             cz = C / (a.nc[0] * a.nc[1]);
   load_embedding<T, P>(E, a.dg);
@@ -570,7 +572,7 @@ void launch_prolongate(const Level& fine, const Level& coarse, const T* xc,
     if (smem > 48 * 1024)
       MFP_CHECK_CUDA(cudaFuncSetAttribute(
           kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(int)coarse.ncells, 256, smem, s>>>(a, xc, xf);
+    kern<<<dim3((unsigned)coarse.ncells, (unsigned)stride), 256, smem, s>>>(a, xc, xf);
   });
   MFP_CHECK_CUDA(cudaGetLastError());
   note_launch();
@@ -580,7 +582,7 @@ void launch_restrict(const Level& fine, const Level& coarse, const T* xf,
                      T* xc, int stride, int col, cudaStream_t s) {
   ensure_tables();
   XferArgs a = xfer_args(fine, coarse, stride, col);
-  if (fine.disc == MFP_CG && col == 0)
+  if (fine.disc == MFP_CG)
     MFP_CHECK_CUDA(cudaMemsetAsync(
         xc, 0, (size_t)coarse.ndofs * stride * sizeof(T), s));
   dispatch_p(fine.p, [&](auto pc) {
@@ -592,7 +594,7 @@ void launch_restrict(const Level& fine, const Level& coarse, const T* xf,
     if (smem > 48 * 1024)
       MFP_CHECK_CUDA(cudaFuncSetAttribute(
           kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(int)coarse.ncells, 256, smem, s>>>(a, xf, xc);
+    kern<<<dim3((unsigned)coarse.ncells, (unsigned)stride), 256, smem, s>>>(a, xf, xc);
   });
   MFP_CHECK_CUDA(cudaGetLastError());
   note_launch();

@@ -45,6 +45,8 @@ void set_error(const std::string& msg);
 void clear_error();
 // Count of kernels this library has launched (process-wide).
 void note_launch();
+int64_t launches_total();
+void add_launches(int64_t n);
 
 struct Fail {
   mfp_status st;
@@ -160,6 +162,18 @@ struct mfp_ctx {
   float* mix_z = nullptr;
   int cg_rhs = 0;
   int64_t vcycles = 0;
+  // V-cycles of mfp_solve captured as CUDA graphs, one per column count;
+  // replays add the captured counter increments
+  struct VGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> applies;
+    int64_t launches = 0;
+    int64_t vcycles = 0;
+  };
+  std::vector<VGraph> graphs;  // index: column count
+  cudaStream_t cap_stream = nullptr;  // capture stream (legacy stream can't)
+  // tuned cells per block: key (level, precision, columns) -> cells
+  std::vector<std::pair<int64_t, int>> tuned;
 };
 
 namespace mfp {
@@ -167,19 +181,19 @@ namespace mfp {
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the kernel translation units)
 // ---------------------------------------------------------------------------
-// dst = A src for nrhs interleaved columns ([N][nrhs]); cpb = cells per
-// block for one column (0: default).
+// dst = A src for nrhs interleaved columns ([N][nrhs]); cells = cells per
+// block for this column count (0: default choice).
 void launch_apply_cg(const Level& L, const LevelData<double>& D,
-                     const double* src, double* dst, int nrhs, int cpb,
+                     const double* src, double* dst, int nrhs, int cells,
                      cudaStream_t s);
 void launch_apply_cg(const Level& L, const LevelData<float>& D,
-                     const float* src, float* dst, int nrhs, int cpb,
+                     const float* src, float* dst, int nrhs, int cells,
                      cudaStream_t s);
 void launch_apply_dg(const Level& L, const LevelData<double>& D,
-                     const double* src, double* dst, int nrhs, int cpb,
+                     const double* src, double* dst, int nrhs, int cells,
                      cudaStream_t s);
 void launch_apply_dg(const Level& L, const LevelData<float>& D,
-                     const float* src, float* dst, int nrhs, int cpb,
+                     const float* src, float* dst, int nrhs, int cells,
                      cudaStream_t s);
 
 void launch_curved_cell_geometry(Level& L, cudaStream_t s);

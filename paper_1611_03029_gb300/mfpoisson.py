@@ -83,6 +83,8 @@ def lib():
                                          dp, vp]),
             "mfp_gradient": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
             "mfp_counters": (ctypes.c_int, [vp, i64p, i64p, i64p]),
+            "mfp_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ip, dp, vp]),
             "mfp_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -273,6 +275,16 @@ class Poisson:
         _check(lib().mfp_gradient(self._h, _ptr(u), _ptr(lam), _ptr(gc),
                                   _ptr(gf), _stream(stream)))
         return gc, gf
+
+    def autotune(self, level=None, prec="fp64", n_rhs=1, stream=None):
+        """Pick the fastest cells-per-block for this apply; returns
+        (cells, ms per apply)."""
+        cells, ms = ctypes.c_int(), ctypes.c_double()
+        p = MFP_FP64 if prec in ("fp64", torch.float64) else MFP_FP32
+        _check(lib().mfp_autotune(self._h, self._lvl(level), p, n_rhs,
+                                  ctypes.byref(cells), ctypes.byref(ms),
+                                  _stream(stream)))
+        return cells.value, ms.value
 
     def counters(self):
         arr = (ctypes.c_int64 * self.n_levels)()

@@ -152,3 +152,50 @@ def test_apply_counts_per_iteration(mfp):
     # its applies of A p, its V-cycles (the initial one included, the last
     # iteration's is skipped after convergence)
     assert fine == its[0] * 1 + its[0] * 10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_vcycle_matches_eager(mfp, prec, monkeypatch):
+    # The solve replays its V-cycle from a captured CUDA graph; the result,
+    # the iteration count and the operator counters equal the eager run.
+    op, P = pair(mfp, "dg", "sine", 2, (4, 4, 4), prec=prec)
+    b = op.rhs(0)
+    monkeypatch.setenv("MFP_CUDA_GRAPHS", "0")
+    a0, v0, _ = op.counters()
+    x0, it0, r0 = op.solve(b, rtol=1e-10)
+    a1, v1, _ = op.counters()
+    monkeypatch.setenv("MFP_CUDA_GRAPHS", "1")
+    x1, it1, r1 = op.solve(b, rtol=1e-10)
+    a2, v2, _ = op.counters()
+    assert it0 == it1
+    assert rel_err(x1.cpu().numpy(), x0.cpu().numpy()) <= 1e-13
+    assert [q - p for p, q in zip(a0, a1)] == [q - p for p, q in zip(a1, a2)]
+    assert v1 - v0 == v2 - v1
+
+
+def test_autotune_keeps_results(mfp):
+    op, P = pair(mfp, "dg", "sine", 3, (4, 4, 2))
+    u = synthetic.random_vector(P.n_dofs, seed=4)
+    y0 = op.apply(cuda(u)).cpu().numpy()
+    cells, ms = op.autotune()
+    assert 1 <= cells <= 32 and ms > 0
+    y1 = op.apply(cuda(u)).cpu().numpy()
+    assert np.array_equal(y0, y1)  # SIPG: same arithmetic per cell
+    A = fem.assemble(P)
+    assert rel_err(y1, A @ u) <= 1e-12
+    b = op.rhs(0)
+    x, its, rel = op.solve(b, rtol=1e-10)
+    res = np.linalg.norm(b.cpu().numpy() - A @ x.cpu().numpy())
+    assert res <= 1.05e-10 * np.linalg.norm(b.cpu().numpy())
+
+
+def test_batched_apply_is_one_launch(mfp):
+    op, P = pair(mfp, "cg", "identity", 3, (4, 4, 4))
+    R = 16
+    N = op.n_dofs()
+    X = torch.randn(N * R, dtype=torch.float64, device="cuda")
+    _, _, l0 = op.counters()
+    op.apply(X, n_rhs=R)
+    torch.cuda.synchronize()
+    _, _, l1 = op.counters()
+    assert l1 - l0 == 1
