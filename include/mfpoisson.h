@@ -63,6 +63,7 @@ typedef enum {
 enum { MFP_CG = 0, MFP_SIPG = 1 };
 enum { MFP_FP64 = 0, MFP_FP32 = 1, MFP_MIXED = 2 };
 enum { MFP_MAP_IDENTITY = 0, MFP_MAP_SINE = 1 };
+enum { MFP_ARITH_DF = 0, MFP_ARITH_NATIVE = 1 };
 
 typedef struct {
   int nx, ny, nz;        /* fine-level cells per axis (>= 1)                */
@@ -87,10 +88,19 @@ typedef struct {
                             always float64 (MFP_MIXED is a synonym of FP32) */
   int cheb_degree;       /* Chebyshev smoother degree (Sec. 4.1: 5)         */
   int eig_cg_iters;      /* CG iterations of the eigenvalue estimate (15)   */
+  int fp64_arith;        /* float64 operator applies: MFP_ARITH_DF (default)
+                            carries every intermediate as a pair of floats
+                            (about 48 bits, error-free TwoSum / FMA TwoProd)
+                            on the FP32 pipes, about 58x wider than the FP64
+                            pipe on GB300; vector entries must lie in
+                            [2^-80, 2^127] in magnitude (smaller ones lose
+                            their low part).  MFP_ARITH_NATIVE uses DFMA.
+                            Float64 vectors in HBM either way.             */
 } mfp_desc;
 
 /* Fill `desc` with the defaults (1 cell, k=1, CG, identity map, kappa 1,
- * penalty_factor 1, FP64 V-cycle, Chebyshev degree 5, 15 CG iterations). */
+ * penalty_factor 1, FP64 V-cycle, Chebyshev degree 5, 15 CG iterations,
+ * double-float arithmetic for float64 applies). */
 void mfp_desc_default(mfp_desc* desc);
 
 /* Create a context on the current CUDA device: builds every multigrid level

@@ -75,6 +75,22 @@ void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
         cudaMemsetAsync(dst, 0, (size_t)L.ndofs * R * sizeof(T), s));
   const int prec = sizeof(T) == 8 ? MFP_FP64 : MFP_FP32;
   const int cells = cells_for(c, level_index(c, L), prec, R);
+  if constexpr (sizeof(T) == 8) {
+    if (c->desc.fp64_arith == MFP_ARITH_DF) {
+      const double* sd = reinterpret_cast<const double*>(src);
+      double* dd = reinterpret_cast<double*>(dst);
+      bool ok;
+      if (L.disc == MFP_CG)
+        ok = apply_cg_df_lo(L, sd, dd, R, cells, s) ||
+             apply_cg_df_hi(L, sd, dd, R, cells, s);
+      else
+        ok = apply_dg_df_lo(L, sd, dd, R, cells, s) ||
+             apply_dg_df_hi(L, sd, dd, R, cells, s);
+      MFP_REQUIRE(ok, "degree out of range");
+      L.applies += R;
+      return;
+    }
+  }
   if (L.disc == MFP_CG)
     launch_apply_cg(L, D, src, dst, R, cells, s);
   else
@@ -335,6 +351,10 @@ void free_level(Level& L) {
   dfree(L.d32.fdata);
   dfree(L.d32.sigma);
   dfree(L.d32.dinv);
+  for (float** p : {&L.ddf.Gh, &L.ddf.Gl, &L.ddf.kch, &L.ddf.kcl, &L.ddf.kfh,
+                    &L.ddf.kfl, &L.ddf.fdh, &L.ddf.fdl, &L.ddf.sgh,
+                    &L.ddf.sgl})
+    dfree(*p);
   dfree(L.vol);
   dfree(L.t_res);
   dfree(L.t_d);
@@ -369,6 +389,27 @@ void to_float_array(const double* a, float*& b, int64_t n, cudaStream_t s) {
   launch_to_float(a, b, n, s);
 }
 
+void split_array(const double* a, float*& hi, float*& lo, int64_t n,
+                 cudaStream_t s) {
+  if (!a) return;
+  if (!hi) hi = dalloc<float>(n);
+  if (!lo) lo = dalloc<float>(n);
+  launch_split(a, hi, lo, n, s);
+}
+
+// Double-float copies of the float64 level data for the FP64-accurate
+// applies on the FP32 pipes.
+void build_df(Level& L, cudaStream_t s) {
+  const int64_t P3 = (int64_t)L.p * L.p * L.p, P2 = (int64_t)L.p * L.p;
+  LevelDF& F = L.ddf;
+  split_array(L.d64.G, F.Gh, F.Gl, L.ncells * 6 * P3, s);
+  split_array(L.d64.kcell, F.kch, F.kcl, L.ncells * P3, s);
+  split_array(L.d64.kface, F.kfh, F.kfl, L.nfaces * P2, s);
+  split_array(L.d64.fdata, F.fdh, F.fdl, L.nfaces * 7 * P2, s);
+  split_array(L.d64.sigma, F.sgh, F.sgl, L.nfaces, s);
+  F.valid = true;
+}
+
 // Geometry, diagonal and eigenvalue estimate of every level.
 void build_levels(mfp_ctx* c, cudaStream_t s) {
   drop_graphs(c);  // Chebyshev parameters are baked into captured V-cycles
@@ -393,6 +434,7 @@ void build_levels(mfp_ctx* c, cudaStream_t s) {
       to_float_array(L.d64.kcell, L.d32.kcell, L.ncells * P3, s);
       to_float_array(L.d64.kface, L.d32.kface, L.nfaces * P2, s);
     }
+    if (c->desc.fp64_arith == MFP_ARITH_DF) build_df(L, s);
     if (!L.d64.dinv) L.d64.dinv = dalloc<double>(L.ndofs);
     launch_diagonal(L, L.d64.dinv, s);
     launch_invert_diag(L, L.d64.dinv, s);
@@ -460,6 +502,7 @@ void mfp_desc_default(mfp_desc* d) {
   d->mg_precision = MFP_FP64;
   d->cheb_degree = 5;
   d->eig_cg_iters = 15;
+  d->fp64_arith = MFP_ARITH_DF;
 }
 
 const char* mfp_last_error(void) { return g_err.c_str(); }
@@ -485,6 +528,8 @@ mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out) {
                 "cheb_degree must be in 1..64");
     MFP_REQUIRE(d.eig_cg_iters >= 1 && d.eig_cg_iters <= 64,
                 "eig_cg_iters must be in 1..64");
+    MFP_REQUIRE(d.fp64_arith == MFP_ARITH_DF || d.fp64_arith == MFP_ARITH_NATIVE,
+                "unknown fp64_arith");
     MFP_REQUIRE(d.mg_precision == MFP_FP64 || d.mg_precision == MFP_FP32 ||
                     d.mg_precision == MFP_MIXED,
                 "unknown mg_precision");
@@ -897,7 +942,13 @@ mfp_status mfp_autotune(mfp_ctx* c, int level, int prec, int n_rhs,
           apply_level<float>(c, L, static_cast<const float*>(src),
                              static_cast<float*>(dst), n_rhs, s);
       };
-      run();
+      try {
+        run();  // shapes that do not fit on an SM are skipped
+      } catch (const Fail&) {
+        cudaGetLastError();
+        c->tuned.pop_back();
+        continue;
+      }
       MFP_CHECK_CUDA(cudaEventRecord(e0, s));
       for (int it = 0; it < 3; ++it) run();
       MFP_CHECK_CUDA(cudaEventRecord(e1, s));
@@ -923,6 +974,8 @@ mfp_status mfp_autotune(mfp_ctx* c, int level, int prec, int n_rhs,
   cudaFree(src);
   cudaFree(dst);
   L.applies = a0;
+  MFP_REQUIRE(best > 0, "no admissible launch shape");
+  clear_error();
   c->tuned.push_back({key, best});
   drop_graphs(c);  // captured V-cycles used the previous launch shapes
   if (cells_out) *cells_out = best;

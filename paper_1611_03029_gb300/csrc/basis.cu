@@ -128,6 +128,21 @@ const HostTables& host_tables() {
     for (int k = 1; k <= 8; ++k) {
       fill(tabs.d[k - 1], k);
       fill(tabs.f[k - 1], k);
+      const DevTab<double>& d = tabs.d[k - 1];
+      DevTabDF& t = tabs.df[k - 1];
+      auto split = [](double v, float& h, float& l) {
+        h = (float)v;
+        l = (float)(v - (double)h);
+      };
+      for (int i = 0; i < kMaxP * kMaxP; ++i) {
+        split(d.S[i], t.Sh[i], t.Sl[i]);
+        split(d.D[i], t.Dh[i], t.Dl[i]);
+      }
+      for (int i = 0; i < kMaxP; ++i) {
+        split(d.dphi0[i], t.d0h[i], t.d0l[i]);
+        split(d.dphi1[i], t.d1h[i], t.d1l[i]);
+        split(d.w[i], t.wh[i], t.wl[i]);
+      }
     }
   });
   return tabs;

@@ -12,6 +12,7 @@ namespace {
 
 __constant__ DevTab<double> c_tab64[8];
 __constant__ DevTab<float> c_tab32[8];
+__constant__ DevTabDF c_tabdf[8];
 
 // Uploads the tables to the current device once per device per TU.
 inline void ensure_tables() {
@@ -24,6 +25,7 @@ inline void ensure_tables() {
   const HostTables& h = host_tables();
   MFP_CHECK_CUDA(cudaMemcpyToSymbol(c_tab64, h.d, sizeof(h.d)));
   MFP_CHECK_CUDA(cudaMemcpyToSymbol(c_tab32, h.f, sizeof(h.f)));
+  MFP_CHECK_CUDA(cudaMemcpyToSymbol(c_tabdf, h.df, sizeof(h.df)));
   if (dev < 64) done[dev] = true;
 }
 

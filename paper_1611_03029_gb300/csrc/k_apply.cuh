@@ -490,7 +490,9 @@ void run_apply(ApplyArgs<T> a, int cpb, int ncols, cudaStream_t s) {
   int per_sm = 0;
   MFP_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &per_sm, kern, threads, smem));
-  if (per_sm < 1) per_sm = 1;
+  MFP_REQUIRE(per_sm >= 1,
+              "apply launch shape does not fit on an SM (cells per block too "
+              "large for the registers or shared memory)");
   const int64_t need = (a.ncells + cpb - 1) / cpb;
   const int64_t cap = (int64_t)per_sm * sm_count();
   const int grid = (int)(need < cap ? need : cap);

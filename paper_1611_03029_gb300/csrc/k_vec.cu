@@ -44,6 +44,15 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b,
                            int64_t n) {
   GRID_STRIDE(i, n) b[i] = (float)a[i];
 }
+__global__ void k_split(const double* __restrict__ a, float* __restrict__ hi,
+                        float* __restrict__ lo, int64_t n) {
+  GRID_STRIDE(i, n) {
+    const float h = __double2float_rn(a[i]);
+    hi[i] = h;
+    lo[i] = __double2float_rn(a[i] - (double)h);
+  }
+}
+
 __global__ void k_to_double(const float* __restrict__ a,
                             double* __restrict__ b, int64_t n) {
   GRID_STRIDE(i, n) b[i] = (double)a[i];
@@ -491,6 +500,13 @@ void launch_invert_diag(const Level& L, double* diag, cudaStream_t s) {
 
 void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
   k_to_float<<<vec_grid(n), kVecThreads, 0, s>>>(a, b, n);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+void launch_split(const double* a, float* hi, float* lo, int64_t n,
+                  cudaStream_t s) {
+  if (n <= 0) return;
+  k_split<<<vec_grid(n), kVecThreads, 0, s>>>(a, hi, lo, n);
   MFP_CHECK_CUDA(cudaGetLastError());
   note_launch();
 }

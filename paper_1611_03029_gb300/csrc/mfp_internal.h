@@ -32,9 +32,19 @@ struct DevTab {
   T x[kMaxP];             // GLL points on [0, 1]
 };
 
+// The same tables as double-float pairs (value = hi + lo, |lo| <= ulp(hi)/2)
+// for the FP64-accurate kernels that run on the FP32 pipes.
+struct DevTabDF {
+  float Sh[kMaxP * kMaxP], Sl[kMaxP * kMaxP];
+  float Dh[kMaxP * kMaxP], Dl[kMaxP * kMaxP];
+  float d0h[kMaxP], d0l[kMaxP], d1h[kMaxP], d1l[kMaxP];
+  float wh[kMaxP], wl[kMaxP];
+};
+
 struct HostTables {
   DevTab<double> d[8];  // index k-1
   DevTab<float> f[8];
+  DevTabDF df[8];
 };
 const HostTables& host_tables();
 
@@ -104,6 +114,16 @@ struct LevelData {
   bool valid = false;
 };
 
+// Double-float copies of the float64 level data (hi / lo float arrays)
+struct LevelDF {
+  float *Gh = nullptr, *Gl = nullptr;    // [ncells][6][p^3]
+  float *kch = nullptr, *kcl = nullptr;  // [ncells][p^3]
+  float *kfh = nullptr, *kfl = nullptr;  // [nfaces][p^2]
+  float *fdh = nullptr, *fdl = nullptr;  // [nfaces][7][p^2]
+  float *sgh = nullptr, *sgl = nullptr;  // [nfaces]
+  bool valid = false;
+};
+
 struct Level {
   int n[3] = {0, 0, 0};
   int k = 1, p = 2;
@@ -119,6 +139,7 @@ struct Level {
   double* vol = nullptr;      // curved: cell volumes [ncells]
   LevelData<double> d64;
   LevelData<float> d32;
+  LevelDF ddf;
   // eigenvalue estimate and Chebyshev parameters (Sec. 4.1)
   double lam_max = 0, lam_min = 0, cheb_lo = 0, cheb_hi = 0;
   int cheb_degree = 0;
@@ -195,6 +216,20 @@ void launch_apply_dg(const Level& L, const LevelData<double>& D,
 void launch_apply_dg(const Level& L, const LevelData<float>& D,
                      const float* src, float* dst, int nrhs, int cells,
                      cudaStream_t s);
+
+// dst = A src in float64 I/O with double-float arithmetic on the FP32 pipes
+// (one translation unit per degree range; false if p is not in its range)
+bool apply_cg_df_lo(const Level& L, const double* src, double* dst, int nrhs,
+                    int cells, cudaStream_t s);
+bool apply_cg_df_hi(const Level& L, const double* src, double* dst, int nrhs,
+                    int cells, cudaStream_t s);
+bool apply_dg_df_lo(const Level& L, const double* src, double* dst, int nrhs,
+                    int cells, cudaStream_t s);
+bool apply_dg_df_hi(const Level& L, const double* src, double* dst, int nrhs,
+                    int cells, cudaStream_t s);
+// hi / lo split of a float64 array
+void launch_split(const double* a, float* hi, float* lo, int64_t n,
+                  cudaStream_t s);
 
 void launch_curved_cell_geometry(Level& L, cudaStream_t s);
 void launch_curved_face_geometry(Level& L, cudaStream_t s);

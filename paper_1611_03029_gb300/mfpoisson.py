@@ -18,6 +18,7 @@ MFP_ERR_NOT_CONVERGED, MFP_ERR_STATE = -4, -6
 MFP_CG, MFP_SIPG = 0, 1
 MFP_FP64, MFP_FP32, MFP_MIXED = 0, 1, 2
 MFP_MAP_IDENTITY, MFP_MAP_SINE = 0, 1
+MFP_ARITH_DF, MFP_ARITH_NATIVE = 0, 1
 
 
 class MfpDesc(ctypes.Structure):
@@ -29,7 +30,8 @@ class MfpDesc(ctypes.Structure):
                 ("penalty_factor", ctypes.c_double),
                 ("mg_precision", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int),
-                ("eig_cg_iters", ctypes.c_int)]
+                ("eig_cg_iters", ctypes.c_int),
+                ("fp64_arith", ctypes.c_int)]
 
 
 class MfpError(RuntimeError):
@@ -124,7 +126,7 @@ class Poisson:
     def __init__(self, nx, ny, nz, degree, disc="cg", n_levels=0,
                  mapping="identity", map_param=0.0, kappa=1.0,
                  penalty_factor=1.0, mg_precision="fp64", cheb_degree=5,
-                 eig_cg_iters=15, stream=None):
+                 eig_cg_iters=15, fp64_arith="df", stream=None):
         L = lib()
         d = MfpDesc()
         L.mfp_desc_default(ctypes.byref(d))
@@ -138,6 +140,8 @@ class Poisson:
         d.mg_precision = _PREC[mg_precision]
         d.cheb_degree = cheb_degree
         d.eig_cg_iters = eig_cg_iters
+        d.fp64_arith = {"df": MFP_ARITH_DF, "native": MFP_ARITH_NATIVE}[
+            fp64_arith]
         self.desc = d
         self.disc = disc
         self.degree = degree

@@ -22,6 +22,8 @@ def main(argv=None):
     ap.add_argument("--degree", type=int, default=4)
     ap.add_argument("--curved", action="store_true")
     ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--arith", default="df", choices=["df", "native"],
+                    help="float64 arithmetic: double-float or DFMA")
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--reps", type=int, default=20)
@@ -36,7 +38,8 @@ def main(argv=None):
     op = M.Poisson(n, n, n, a.degree, disc=a.disc,
                    mapping="sine" if a.curved else "identity",
                    map_param=0.1 if a.curved else 0.0, n_levels=1,
-                   mg_precision="fp64" if a.prec == "f64" else "fp32")
+                   mg_precision="fp64" if a.prec == "f64" else "fp32",
+                   fp64_arith=a.arith)
     dt = torch.float64 if a.prec == "f64" else torch.float32
     N = op.n_dofs()
     src = torch.randn(N * a.nrhs, dtype=dt, device="cuda")
@@ -54,6 +57,7 @@ def main(argv=None):
     t = e0.elapsed_time(e1) / a.reps * 1e-3
     print(json.dumps({"disc": a.disc, "cells": n, "degree": a.degree,
                       "curved": a.curved, "prec": a.prec, "nrhs": a.nrhs,
+                      "arith": a.arith if a.prec == "f64" else "f32",
                       "dofs": N, "ms": t * 1e3,
                       "MDoF_s": N * a.nrhs / t / 1e6,
                       "cells_per_block": os.environ.get(

@@ -31,15 +31,18 @@ def cases():
 
 @pytest.mark.parametrize("disc,mapping,k,n", cases())
 def test_apply_matches_oracle_fp64(mfp, disc, mapping, k, n):
+    # both float64 arithmetics: double-float on the FP32 pipes (default) and
+    # native DFMA
     amp = 0.1 if mapping == "sine" else 0.0
-    op = mfp.Poisson(*n, k, disc=disc, mapping=mapping, map_param=amp,
-                     n_levels=1)
     P = fem.Problem(*n, k, disc=disc, mapping=mapping, amp=amp)
     A = fem.assemble(P)
     u = synthetic.random_vector(P.n_dofs, seed=100 + k)
-    y = op.apply(torch.from_numpy(u).cuda()).cpu().numpy()
     ref = A @ u
-    assert rel_err(y, ref) <= TOL64
+    for arith in ("df", "native"):
+        op = mfp.Poisson(*n, k, disc=disc, mapping=mapping, map_param=amp,
+                         n_levels=1, fp64_arith=arith)
+        y = op.apply(torch.from_numpy(u).cuda()).cpu().numpy()
+        assert rel_err(y, ref) <= TOL64, arith
     # anisotropic penalty / normals: same with the paper's penalty factor
     if disc == "dg" and k == 2:
         op3 = mfp.Poisson(*n, k, disc=disc, mapping=mapping, map_param=amp,
@@ -67,11 +70,12 @@ def test_apply_matches_oracle_fp32(mfp, disc, mapping, k):
 
 
 @pytest.mark.parametrize("disc", ["cg", "dg"])
-def test_variable_coefficient_apply(mfp, disc):
+@pytest.mark.parametrize("arith", ["df", "native"])
+def test_variable_coefficient_apply(mfp, disc, arith):
     n, k = (4, 2, 3), 3
     p = k + 1
     a_cell, a_face = synthetic.log_coefficient(n, p, seed=7)
-    op = mfp.Poisson(*n, k, disc=disc, n_levels=1)
+    op = mfp.Poisson(*n, k, disc=disc, n_levels=1, fp64_arith=arith)
     op.set_coefficient(torch.from_numpy(a_cell).cuda().contiguous(),
                        torch.from_numpy(a_face).cuda().contiguous())
     P = fem.Problem(*n, k, disc=disc, a_cell=a_cell, a_face=a_face)
@@ -94,12 +98,13 @@ def test_batched_apply_equals_columns(mfp, disc):
 
 
 @pytest.mark.parametrize("disc", ["cg", "dg"])
-def test_full_size_curved_q4_sampled_rows(mfp, disc):
+@pytest.mark.parametrize("arith", ["df", "native"])
+def test_full_size_curved_q4_sampled_rows(mfp, disc, arith):
     # 32^3 cells, Q4, curved: the apply-throughput workload; the oracle
     # evaluates sampled rows one by one.
     n, k = (32, 32, 32), 4
     op = mfp.Poisson(*n, k, disc=disc, mapping="sine", map_param=0.1,
-                     n_levels=1)
+                     n_levels=1, fp64_arith=arith)
     N = op.n_dofs()
     u = synthetic.random_vector(N, seed=21)
     y = op.apply(torch.from_numpy(u).cuda()).cpu().numpy()
