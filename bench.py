@@ -37,6 +37,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=N_CELLS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="solve",
+                    choices=["solve", "latency", "sweep", "batched",
+                             "gradient"],
+                    help="solve: the default contract line; the others print "
+                         "their own lines for the remaining configurations")
+    ap.add_argument("--degrees", default="1,2,3,4,5,6,7,8")
     return ap.parse_args()
 
 
@@ -122,6 +128,35 @@ def apply_flops(disc, k, ncells, curved):
     return float(cell) * ncells
 
 
+def df_dot(n):
+    """FP32-pipe flops of one double-float dot product of length n: first
+    product 7 (FMUL + 3 FFMA), each further term 14 (FMUL, 3 FFMA, 7 FADD),
+    final TwoSum 6."""
+    return 14 * n - 1
+
+
+def apply_flops_df(disc, k, ncells, curved):
+    """FP32-pipe flops (FFMA = 2) of one double-float apply, counted from the
+    kernel's double-float operations: 12 sweeps of p^2 lines x p dots of
+    length p per cell, the quadrature-point operation, the two transposed
+    accumulations and, for SIPG, per face point 18 dots of length p (both
+    sides' normal slopes, interpolation of four traces, tangential slopes
+    when curved, two transposed interpolations), the flux arithmetic, the
+    curved fold and the distribution onto the own nodes."""
+    p = k + 1
+    dadd, dmul = 11, 10
+    cell = 12 * p ** 3 * df_dot(p) + 2 * p ** 3 * dadd
+    cell += p ** 3 * (3 * df_dot(3) if curved else 6 * dmul)
+    if disc == "dg":
+        dots = (18 if curved else 14) * df_dot(p)
+        flux = 6 * dmul + 3 * dadd + 4 + (3 * dmul + 2 * df_dot(3) if curved
+                                          else 5 * dmul)
+        fold = 28 * p if curved else 0
+        dist = dadd + p * (dmul + dadd)
+        cell += 6 * p * p * (dots + flux + fold + dist)
+    return float(cell) * ncells
+
+
 def apply_bytes(disc, k, n, curved, word=8):
     """Compulsory DRAM bytes of one apply: source read, destination written
     (CG: plus the zero fill), stored geometry (6 words per cell point) and,
@@ -136,6 +171,28 @@ def apply_bytes(disc, k, n, curved, word=8):
             nf = 3 * n * n * (n + 1)
             b += (7 * p * p + 1) * nf * word
     return float(b)
+
+
+# FP64 pipe peak of the GB300 from its unit counts: 152 SMs x 2 DFMA per
+# clock per SM x 2 flop x 2.07 GHz = 1258.6 GFLOP/s (a DFMA-chain probe on
+# this pool measured 1254.6).  FP32: 152 x 128 FFMA x 2 x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # probe measured 73.2
+
+# DRAM traffic (read + write) per launch of the dominant kernel from one ncu
+# capture, keyed by a hash of the sources it was compiled from; a kernel
+# changed since its capture reports null.
+TRAFFIC = {}
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("k_apply_df.cuh", "df.cuh", "dev_tables.cuh",
+              "apply_dg_df_lo.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1611_03029_gb300", "csrc",
+                                   f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def load_peaks():
@@ -245,6 +302,10 @@ def run_ours(args):
     mixed = {disc: M.Poisson(n, n, n, DEGREE, disc=disc, mapping="sine",
                              map_param=AMP, mg_precision="fp32")
              for disc in ("cg", "dg")}
+    tuned = {}
+    for d in ("cg", "dg"):
+        tuned["f64_" + d] = ops[d].autotune(prec="fp64")[0]
+        tuned["f32_" + d] = mixed[d].autotune(prec="fp32")[0]
     b = {d: ops[d].rhs(0) for d in ops}
     x = {d: torch.empty_like(b[d]) for d in ops}
     N = {d: ops[d].n_dofs() for d in ops}
@@ -323,6 +384,8 @@ def run_ours(args):
                 "ms": t * 1e3, "MDoF_s": N[d] / t / 1e6,
                 "equiv_MDoF_s": equiv / t / 1e6,
                 "GFLOP_s": apply_flops(d, DEGREE, n ** 3, True) / t / 1e9,
+                "fp32_pipe_GFLOP_s": (apply_flops_df(d, DEGREE, n ** 3, True)
+                                      / t / 1e9 if prec == "f64" else None),
                 "GB_s": apply_bytes(d, DEGREE, n, True,
                                     8 if prec == "f64" else 4) / t / 1e9}
 
@@ -345,17 +408,22 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     peaks = load_peaks()
-    # dominant kernel: the float64 SIPG apply (largest share of the step);
-    # float64 sum factorization is bound by the FP64 pipe ("alu").
-    fp64_peak = float(os.environ.get("MFP_FP64_PEAK_GFLOPS", "0")) or None
+    # dominant kernel: the float64 SIPG apply (largest share of the step in
+    # the launch list), double-float arithmetic, bound by the FP32 pipe.
     dom = apply["f64_dg"]
-    roof = {"kernel": "k_apply<P=5,double,DG,curved>", "bound": "alu",
-            "achieved": dom["GFLOP_s"] / 1e3, "peak": None,
-            "unit": "TFLOP/s", "frac": None, "traffic": None,
-            "peak_source": "FP64 pipe peak from the unit-count derivation"}
-    if fp64_peak:
-        roof["peak"] = fp64_peak / 1e3
-        roof["frac"] = roof["achieved"] / roof["peak"]
+    ach = dom["fp32_pipe_GFLOP_s"] / 1e3
+    roof = {"kernel": "k_apply_df<P=5,DG,curved>", "bound": "alu",
+            "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP32_PEAK_TFLOPS,
+            "traffic": TRAFFIC.get(kernel_hash()),
+            "algorithmic_bytes": apply_bytes("dg", DEGREE, n, True),
+            "work": "FP32-pipe flops of the double-float operations "
+                    "(bench.apply_flops_df)",
+            "fp64_equivalent_TFLOP_s": dom["GFLOP_s"] / 1e3,
+            "fp64_pipe_peak": FP64_PEAK_TFLOPS,
+            "peak_source": "FP32 pipe from unit counts (152 SMs x 128 FFMA/clk "
+                           "x 2 x 2.07 GHz); FFMA probe measured 73.2 TFLOP/s",
+            "kernel_source_hash": kernel_hash()}
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -374,6 +442,7 @@ def run_ours(args):
                   "iterations": {d: its_mixed[d][0] for d in its_mixed},
                   "speedup_vs_fp64": ms / mixed_ms},
         "apply": apply,
+        "cells_per_block": tuned,
         "roofline": roof,
         "e2e": {"value": dofs_step / (e2e_ms * 1e-3), "unit": "DoF/s",
                 "h2d_bytes_per_step": 8 * dofs_step,
@@ -390,12 +459,203 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Further configurations (one JSON line each, not the contract line)
+# ---------------------------------------------------------------------------
+def _timed(fn, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def run_latency(args):
+    """8^3 cells, continuous Q2 (17^3 = 4913 dofs), Cartesian, FP64: time to
+    1e-10 with the V-cycle replayed from a CUDA graph and eagerly, and the
+    latency of one operator apply."""
+    import torch
+    from paper_1611_03029_gb300 import build
+    build.build()
+    from paper_1611_03029_gb300 import mfpoisson as M
+    st = torch.cuda.current_stream()
+    op = M.Poisson(8, 8, 8, 2, disc="cg")
+    b = op.rhs(0)
+    x = torch.empty_like(b)
+    res = {}
+    for mode in ("graph", "eager"):
+        os.environ["MFP_CUDA_GRAPHS"] = "1" if mode == "graph" else "0"
+        for _ in range(args.warmup):
+            op.solve(b, x, rtol=RTOL)
+        ts = []
+        for _ in range(args.steps):
+            t, (_, it, rel) = _timed(lambda: op.solve(b, x, rtol=RTOL), st)
+            ts.append(t)
+        res[mode] = {"ms": min(ts), "median_ms": sorted(ts)[len(ts) // 2],
+                     "iterations": it[0], "relres": rel[0]}
+    os.environ["MFP_CUDA_GRAPHS"] = "1"
+    src = torch.randn(op.n_dofs(), dtype=torch.float64, device="cuda")
+    dst = torch.empty_like(src)
+    t, _ = _timed(lambda: [op.apply(src, dst) for _ in range(200)], st)
+    print(json.dumps({"workload": "latency: CG Q2 8^3 cells (4913 dofs), "
+                      "Cartesian, FP64, 3 levels", "solve": res,
+                      "apply_us": t / 200 * 1e3,
+                      "dofs": op.n_dofs()}), flush=True)
+
+
+SWEEP = {  # degree: (cells per axis CG, cells per axis SIPG)
+    1: (256, 128), 2: (128, 96), 3: (96, 64), 4: (64, 64),
+    5: (56, 48), 6: (48, 40), 7: (40, 32), 8: (32, 32)}
+
+
+def run_sweep(args):
+    """Degree sweep on Cartesian meshes of 16-33M dofs: FP64 V-cycle versus
+    FP32 V-cycle inside the float64 CG, time to 1e-10, iterations and the
+    difference of the two solutions."""
+    import torch
+    from paper_1611_03029_gb300 import build
+    build.build()
+    from paper_1611_03029_gb300 import mfpoisson as M
+    st = torch.cuda.current_stream()
+    for k in [int(v) for v in args.degrees.split(",")]:
+        for disc, n in (("cg", SWEEP[k][0]), ("dg", SWEEP[k][1])):
+            out = {"workload": "sweep", "disc": disc, "degree": k,
+                   "cells": n}
+            xs = {}
+            for prec in ("fp64", "fp32"):
+                op = M.Poisson(n, n, n, k, disc=disc, mg_precision=prec)
+                b = op.rhs(0)
+                x = torch.empty_like(b)
+                op.solve(b, x, rtol=RTOL, max_it=200)
+                t, (_, it, rel) = _timed(
+                    lambda: op.solve(b, x, rtol=RTOL, max_it=200), st)
+                out["dofs"] = op.n_dofs()
+                out[prec] = {"ms": t, "iterations": it[0], "relres": rel[0],
+                             "dofs_per_s": op.n_dofs() / (t * 1e-3)}
+                xs[prec] = x.clone()
+                del op
+                torch.cuda.empty_cache()
+            out["mixed_vs_fp64_rel_diff"] = float(
+                (xs["fp32"] - xs["fp64"]).norm() / xs["fp64"].norm())
+            out["mixed_speedup"] = out["fp64"]["ms"] / out["fp32"]["ms"]
+            print(json.dumps(out), flush=True)
+
+
+def run_batched(args):
+    """16 right-hand sides (sums of 8 Gaussians), continuous Q3 on 48^3
+    Cartesian cells (3,048,625 dofs each): one batched mixed-precision solve
+    (one launch per operator apply, graph-captured V-cycle) versus 16
+    sequential float64 solves."""
+    import torch
+    from paper_1611_03029_gb300 import build, synthetic
+    build.build()
+    from paper_1611_03029_gb300 import mfpoisson as M
+    st = torch.cuda.current_stream()
+    R, n, k = 16, 48, 3
+    mixed = M.Poisson(n, n, n, k, disc="cg", mg_precision="fp32")
+    fp64 = M.Poisson(n, n, n, k, disc="cg")
+    N = mixed.n_dofs()
+    B = torch.empty(N * R, dtype=torch.float64, device="cuda")
+    for r in range(R):
+        mixed.rhs(1, synthetic.gaussian_terms(1000 + r), out=B[r:], stride=R)
+    X = torch.empty_like(B)
+    tuned = mixed.autotune(prec="fp64", n_rhs=R)[0]
+    mixed.solve(B, X, n_rhs=R, rtol=RTOL)
+    t_b, (_, its_b, rel_b) = _timed(
+        lambda: mixed.solve(B, X, n_rhs=R, rtol=RTOL), st)
+    cols = [B[r::R].contiguous() for r in range(R)]
+    x1 = torch.empty(N, dtype=torch.float64, device="cuda")
+    fp64.solve(cols[0], x1, rtol=RTOL)
+
+    def seq():
+        its = []
+        for r in range(R):
+            _, it, _ = fp64.solve(cols[r], x1, rtol=RTOL)
+            its.append(it[0])
+        return its
+    t_s, its_s = _timed(seq, st)
+    print(json.dumps({"workload": "batched: 16 RHS, CG Q3 48^3 Cartesian",
+                      "dofs_per_rhs": N, "batched_mixed_ms": t_b,
+                      "batched_iterations": its_b,
+                      "batched_max_relres": max(rel_b),
+                      "sequential_fp64_ms": t_s,
+                      "sequential_iterations": its_s,
+                      "speedup": t_s / t_b,
+                      "cells_per_block_fp64_R16": tuned,
+                      "dofs_per_s_batched": N * R / (t_b * 1e-3)}),
+          flush=True)
+
+
+def run_gradient(args):
+    """-div(a grad u) = f, a = exp(g) at every quadrature point, SIPG Q3 on
+    32^3 Cartesian cells: forward solve, adjoint solve and the dL/da kernel,
+    with the directional finite-difference check of the gradient."""
+    import numpy as np
+    import torch
+    from paper_1611_03029_gb300 import build, synthetic
+    build.build()
+    from paper_1611_03029_gb300 import mfpoisson as M
+    st = torch.cuda.current_stream()
+    n, k = 32, 3
+    op = M.Poisson(n, n, n, k, disc="dg")
+    a_c, a_f = synthetic.log_coefficient((n, n, n), k + 1, seed=7)
+    ac = torch.from_numpy(a_c).cuda()
+    af = torch.from_numpy(a_f).cuda()
+    t_set, _ = _timed(lambda: op.set_coefficient(ac, af), st)
+    b = op.rhs(0)
+    u, _, _ = op.solve(b, rtol=1e-13, max_it=300)
+    ut = torch.from_numpy(
+        synthetic.random_vector(op.n_dofs(), 8)).cuda() * u.norm() / \
+        np.sqrt(op.n_dofs())
+
+    def fwd_adj_grad():
+        u, itf, _ = op.solve(b, rtol=1e-13, max_it=300)
+        lam, ita, _ = op.solve((u - ut).contiguous(), rtol=1e-13, max_it=300)
+        gc, gf = op.gradient(u, lam)
+        return u, lam, gc, gf, itf[0], ita[0]
+    t, (u, lam, gc, gf, itf, ita) = _timed(fwd_adj_grad, st)
+    t_g, _ = _timed(lambda: op.gradient(u, lam), st)
+
+    def loss(dc, df, eps):
+        op.set_coefficient((ac + eps * dc).contiguous(),
+                           (af + eps * df).contiguous())
+        uu, _, _ = op.solve(b, rtol=1e-13, max_it=300)
+        return 0.5 * float(((uu - ut) ** 2).sum())
+    rng = np.random.default_rng(11)
+    eps = 1e-4 * float(ac.abs().max())
+    checks = []
+    for _ in range(3):
+        dc = torch.from_numpy(rng.standard_normal(a_c.shape)).cuda()
+        df = torch.from_numpy(rng.standard_normal(a_f.shape)).cuda()
+        dc /= dc.norm()
+        df /= df.norm()
+        fd = (loss(dc, df, eps) - loss(dc, df, -eps)) / (2 * eps)
+        an = float((gc * dc).sum() + (gf * df).sum())
+        checks.append(abs(fd - an) / abs(an))
+    op.set_coefficient(ac, af)
+    print(json.dumps({"workload": "gradient: SIPG Q3 32^3, a = exp(g)",
+                      "dofs": op.n_dofs(), "cell_points": a_c.size,
+                      "face_points": a_f.size,
+                      "forward_adjoint_gradient_ms": t,
+                      "gradient_kernel_ms": t_g,
+                      "set_coefficient_ms": t_set,
+                      "iterations": {"forward": itf, "adjoint": ita},
+                      "fd_rel_errors": checks}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "solve":
         run_ours(args)
+    else:
+        {"latency": run_latency, "sweep": run_sweep, "batched": run_batched,
+         "gradient": run_gradient}[args.workload](args)
 
 
 if __name__ == "__main__":
