@@ -633,7 +633,9 @@ def run_gradient(args):
         df = torch.from_numpy(rng.standard_normal(a_f.shape)).cuda()
         dc /= dc.norm()
         df /= df.norm()
-        fd = (loss(dc, df, eps) - loss(dc, df, -eps)) / (2 * eps)
+        # fourth-order central difference
+        fd = (8 * (loss(dc, df, eps) - loss(dc, df, -eps))
+              - (loss(dc, df, 2 * eps) - loss(dc, df, -2 * eps))) / (12 * eps)
         an = float((gc * dc).sum() + (gf * df).sum())
         checks.append(abs(fd - an) / abs(an))
     op.set_coefficient(ac, af)

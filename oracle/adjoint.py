@@ -68,3 +68,33 @@ def loss(u, u_target):
     """L = 0.5 ||u - u_t||_2^2 on the dof vector."""
     d = np.asarray(u) - np.asarray(u_target)
     return 0.5 * float(d @ d)
+
+
+def gradient_sampled(prob, u, lam, cells, faces):
+    """dL/da at the points of selected cells and faces only (the same
+    assembled derivative as `gradient`), for checking large meshes."""
+    u = np.array(u, float)
+    lam = np.array(lam, float)
+    cmask = prob.constrained()
+    u[cmask] = 0.0
+    lam[cmask] = 0.0
+    cells = np.asarray(cells)
+    dK = cell_qp_matrices(prob, cells)
+    dm = prob.dof_map(cells)
+    g_cell = -np.einsum("ci,cmij,cj->cm", lam[dm], dK, u[dm])
+    g_face = {}
+    if prob.disc == "dg":
+        for d in range(3):
+            for g in fem.face_operators(prob, d, faces):
+                dmf = prob.dof_map(g["cells"].ravel()).reshape(
+                    len(g["fid"]), -1)
+                ul, ll = u[dmf], lam[dmf]
+                ju = np.einsum("fmj,fj->fm", g["jump_u"], ul)
+                au = np.einsum("fmj,fj->fm", g["avg_u"], ul)
+                jv = np.einsum("fmi,fi->fm", g["jump_v"], ll)
+                av = np.einsum("fmi,fi->fm", g["avg_v"], ll)
+                val = g["c"] * (-jv * au - av * ju
+                                + g["sigma"][:, None] * jv * ju)
+                for t, f in enumerate(g["fid"]):
+                    g_face[int(f)] = -val[t]
+    return g_cell, g_face

@@ -57,9 +57,11 @@ __device__ __forceinline__ int fnode(int l, int a, int b) {
   return a + P * (b + P * l);
 }
 
+// Shared-memory stride of one virtual cell, odd so that the columns of a
+// batch (adjacent threads, one virtual cell each) fall into distinct banks.
 template <typename T, int P, bool DG>
 __host__ __device__ constexpr int cell_smem_elems() {
-  return (DG ? 4 : 3) * P * P * P + (DG ? 8 * P * P : 0);
+  return ((DG ? 4 : 3) * P * P * P + (DG ? 8 * P * P : 0)) | 1;
 }
 template <int P>
 __host__ __device__ constexpr int table_smem_elems() {

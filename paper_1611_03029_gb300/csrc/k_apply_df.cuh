@@ -90,9 +90,10 @@ __device__ __forceinline__ int dfnode(int l, int a, int b) {
   return a + P * (b + P * l);
 }
 
+// odd stride: the columns of a batch fall into distinct shared-memory banks
 template <int P, bool DG>
 __host__ __device__ constexpr int df_cell_floats() {
-  return (DG ? 8 : 6) * P * P * P + (DG ? 16 * P * P : 0);
+  return ((DG ? 8 : 6) * P * P * P + (DG ? 16 * P * P : 0)) | 1;
 }
 template <int P>
 __host__ __device__ constexpr int df_table_floats() {

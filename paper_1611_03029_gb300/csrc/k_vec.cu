@@ -69,7 +69,7 @@ __global__ void k_cheb_first(const T* __restrict__ b,
                              int64_t n, int nrhs) {
   GRID_STRIDE(i, n * nrhs) {
     const T r = ax ? b[i] - ax[i] : b[i];
-    const T di = c * dinv[i / nrhs] * r;
+    const T di = c * dinv[nrhs == 1 ? i : i / nrhs] * r;
     d[i] = di;
     x[i] = ax ? x[i] + di : di;
   }
@@ -81,7 +81,7 @@ __global__ void k_cheb_step(const T* __restrict__ b,
                             T* __restrict__ x, const T* __restrict__ ax, T cd,
                             T cr, int64_t n, int nrhs) {
   GRID_STRIDE(i, n * nrhs) {
-    const T di = cd * d[i] + cr * dinv[i / nrhs] * (b[i] - ax[i]);
+    const T di = cd * d[i] + cr * dinv[nrhs == 1 ? i : i / nrhs] * (b[i] - ax[i]);
     d[i] = di;
     x[i] += di;
   }

@@ -48,11 +48,41 @@ def test_autograd_gradient_matches_finite_differences(mfp):
     for _ in range(3):
         dc = torch.from_numpy(rng.standard_normal(a_c.shape)).cuda()
         df = torch.from_numpy(rng.standard_normal(a_f.shape)).cuda()
-        with torch.no_grad():
-            lp = 0.5 * ((MFPSolve.apply(ac + eps * dc, af + eps * df, op, b,
-                                        1e-13, 300) - ut) ** 2).sum()
-            lm = 0.5 * ((MFPSolve.apply(ac - eps * dc, af - eps * df, op, b,
-                                        1e-13, 300) - ut) ** 2).sum()
-        fd = float((lp - lm) / (2 * eps))
+        def L(e):
+            with torch.no_grad():
+                return float(0.5 * ((MFPSolve.apply(
+                    ac + e * dc, af + e * df, op, b, 1e-13, 300) - ut) ** 2
+                ).sum())
+        # fourth-order central difference
+        fd = (8 * (L(eps) - L(-eps)) - (L(2 * eps) - L(-2 * eps))) / (12 * eps)
         an = float((ac.grad * dc).sum() + (af.grad * df).sum())
         assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+
+
+def test_gradient_full_size_sampled(mfp):
+    # 32^3 cells SIPG Q3 with a = exp(g) at every cell and face point (the
+    # gradient workload); the oracle evaluates the gradient at sampled cells
+    # and faces one by one.
+    n, k = (32, 32, 32), 3
+    a_c, a_f = synthetic.log_coefficient(n, k + 1, seed=7)
+    op = mfp.Poisson(*n, k, disc="dg", n_levels=1)
+    op.set_coefficient(torch.from_numpy(a_c).cuda(),
+                       torch.from_numpy(a_f).cuda())
+    N = op.n_dofs()
+    u = synthetic.random_vector(N, 1)
+    lam = synthetic.random_vector(N, 2)
+    gc, gf = op.gradient(torch.from_numpy(u).cuda(),
+                         torch.from_numpy(lam).cuda())
+    gc, gf = gc.cpu().numpy(), gf.cpu().numpy()
+    P = fem.Problem(*n, k, disc="dg", a_cell=a_c, a_face=a_f)
+    rng = np.random.default_rng(4)
+    cells = np.concatenate([rng.choice(P.ncells, 12, replace=False),
+                            [0, P.ncells - 1]])
+    faces = np.concatenate([rng.choice(P.n_faces, 12, replace=False),
+                            [0, P.n_faces - 1]])
+    rc, rf = adjoint.gradient_sampled(P, u, lam, cells, faces)
+    scale = np.abs(gc).max()
+    assert np.abs(gc[cells] - rc).max() <= 1e-12 * scale
+    fscale = np.abs(gf).max()
+    for f, v in rf.items():
+        assert np.abs(gf[f] - v).max() <= 1e-12 * fscale
