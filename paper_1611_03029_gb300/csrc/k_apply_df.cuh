@@ -12,6 +12,17 @@
 #include "dev_tables.cuh"
 #include "df.cuh"
 
+// Resident 128-thread blocks per SM the register allocation must allow:
+// CG gains from more warps (latency of the gather and geometry loads), SIPG
+// from more registers (its face code spills below 128 per thread); measured
+// on 32^3 Q3/Q4 Cartesian and curved meshes.
+#ifndef MFP_DF_MIN_BLOCKS_CG
+#define MFP_DF_MIN_BLOCKS_CG 8
+#endif
+#ifndef MFP_DF_MIN_BLOCKS_DG
+#define MFP_DF_MIN_BLOCKS_DG 4
+#endif
+
 namespace mfp {
 namespace {
 
@@ -351,8 +362,19 @@ __device__ __forceinline__ void df_face(const ApplyArgsDF& a, bool active,
   __syncthreads();
 }
 
+// Register budget: enough resident warps to hide the load latency
+// (blocks of at most 128 threads for p <= 5, 256 above).
+template <int P>
+constexpr int df_max_threads() { return P <= 5 ? 128 : 256; }
+template <int P, bool DG>
+constexpr int df_min_blocks() {
+  // p >= 6: no cap (the larger line arrays would spill kilobytes)
+  return P <= 5 ? (DG ? MFP_DF_MIN_BLOCKS_DG : MFP_DF_MIN_BLOCKS_CG) : 1;
+}
+
 template <int P, bool DG, bool CURVED>
-__global__ void k_apply_df(const ApplyArgsDF a) {
+__global__ void __launch_bounds__(df_max_threads<P>(), df_min_blocks<P, DG>())
+    k_apply_df(const ApplyArgsDF a) {
   constexpr int P2 = P * P, P3 = P2 * P;
   extern __shared__ __align__(16) unsigned char smraw[];
   float* sm = reinterpret_cast<float*>(smraw);
