@@ -68,10 +68,210 @@ __host__ __device__ constexpr int table_smem_elems() {
   return 3 * P * P + 3 * P;
 }
 
-// One face of the own cell (axis D, side S: 0 lower, 1 upper).  Adds the
-// face integrals tested with the own cell's basis into Aq (nodal values).
+// One line of a p x p face array: Y[line] = M X[line] (or M^T) along the
+// first (DIR 0, index q + p c) or second (DIR 1, index c + p q) tangential
+// axis; the 1D matrix is a constant-bank operand.
+template <int P, typename T, int W, bool TRANS, int DIR>
+__device__ __forceinline__ void face_line(const T* X, T* Y, int c) {
+  T in[P], out[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) in[j] = X[DIR == 0 ? j + P * c : c + P * j];
+  if constexpr (TRANS)
+    mtv<T, P, W>(in, out);
+  else
+    mv<T, P, W>(in, out);
+#pragma unroll
+  for (int q = 0; q < P; ++q) Y[DIR == 0 ? q + P * c : c + P * q] = out[q];
+}
+
+// Face terms of SIPG (Eq. 6, mirror states Eq. 7) for one face of the own
+// cell, in three parts: the trace gather and the final scatter depend on the
+// face (axis D, side S: 0 lower, 1 upper) and are instantiated for each; the
+// interpolation to the face Gauss points, the flux and the transposed
+// interpolation are face-independent and exist once (the six faces run in a
+// loop, which keeps the kernel's code within the instruction cache).
+// Per-point parts use thread (ta, tb) for face point / node line (ta, tb);
+// interpolations are line sweeps, one line per thread.  FS: 8 p^2 arrays.
+template <int P, typename T, int D, int S>
+__device__ __forceinline__ void face_gather(const ApplyArgs<T>& a, bool active,
+                                            int nb, bool bnd, const T* U,
+                                            T* FS, int ta, int tb) {
+  constexpr int P2 = P * P, P3 = P2 * P;
+  constexpr int SLO = S ? T_DPHI1 : T_DPHI0;  // own slope table
+  constexpr int SLN = S ? T_DPHI0 : T_DPHI1;  // neighbour slope table
+  constexpr int lo = S ? P - 1 : 0;
+  constexpr int ln = S ? 0 : P - 1;
+  const int t = ta + P * tb;
+  T vo = U[fnode<P, D>(lo, ta, tb)];
+  T dno = T(0);
+#pragma unroll
+  for (int l = 0; l < P; ++l)
+    dno = fma(tv<T, P, SLO>(l), U[fnode<P, D>(l, ta, tb)], dno);
+  T vn = T(0), dnn = T(0);
+  if (!bnd && active) {
+    const size_t cb = (size_t)nb * P3;
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+      const T u = a.src[(cb + fnode<P, D>(l, ta, tb)) * a.stride + a.col];
+      dnn = fma(tv<T, P, SLN>(l), u, dnn);
+      if (l == ln) vn = u;
+    }
+  }
+  FS[0 * P2 + t] = vo;
+  FS[1 * P2 + t] = dno;
+  FS[2 * P2 + t] = vn;
+  FS[3 * P2 + t] = dnn;
+}
+
+template <int P, typename T, int D, int S>
+__device__ __forceinline__ void face_scatter(T* Aq, const T* FS, int ta,
+                                             int tb) {
+  constexpr int P2 = P * P;
+  constexpr int SLO = S ? T_DPHI1 : T_DPHI0;
+  constexpr int lo = S ? P - 1 : 0;
+  const int t = ta + P * tb;
+  const T vf = FS[0 * P2 + t], nf = FS[1 * P2 + t];
+  Aq[fnode<P, D>(lo, ta, tb)] += vf;
+#pragma unroll
+  for (int l = 0; l < P; ++l)
+    Aq[fnode<P, D>(l, ta, tb)] += tv<T, P, SLO>(l) * nf;
+}
+
+// FS[0..3] = own value, own reference normal slope, neighbour value,
+// neighbour slope at the face nodes  ->  FS[0] = value part, FS[1] =
+// normal-slope part of the own test functions at the face nodes.
+template <int P, typename T, bool CURVED>
+__device__ __forceinline__ void face_core(const ApplyArgs<T>& a, int D, int S,
+                                          int f, bool bnd, T* FS, const T* sw,
+                                          int ta, int tb) {
+  constexpr int P2 = P * P;
+  const int t = ta + P * tb;
+  for (int it = t; it < 4 * P; it += P2)
+    face_line<P, T, T_S, false, 0>(FS + (it / P) * P2, FS + (4 + it / P) * P2,
+                                   it % P);
+  __syncthreads();
+  for (int it = t; it < 4 * P; it += P2)
+    face_line<P, T, T_S, false, 1>(FS + (4 + it / P) * P2, FS + (it / P) * P2,
+                                   it % P);
+  __syncthreads();
+  if constexpr (CURVED) {  // tangential slopes of both traces
+    for (int it = t; it < 4 * P; it += P2) {
+      const int k = it / P;  // 0: d_a u-, 1: d_b u-, 2: d_a u+, 3: d_b u+
+      const T* src = FS + (k < 2 ? 0 : 2) * P2;
+      if (k & 1)
+        face_line<P, T, T_D, false, 1>(src, FS + (4 + k) * P2, it % P);
+      else
+        face_line<P, T, T_D, false, 0>(src, FS + (4 + k) * P2, it % P);
+    }
+    __syncthreads();
+  }
+  // flux at face quadrature point (ta, tb)
+  T cv, c0, c1 = T(0), c2 = T(0);
+  {
+    const T kap = a.kface ? a.kface[(size_t)f * P2 + t] : a.kappa;
+    T uo = FS[0 * P2 + t], un = FS[2 * P2 + t], dno, dnn, dA, sig;
+    if constexpr (!CURVED) {
+      const T nsc = (S ? T(1) : T(-1)) * a.ns[D];
+      dA = sw[ta] * sw[tb] * a.fa[D];
+      sig = a.sg[D];
+      dno = nsc * FS[1 * P2 + t];
+      dnn = bnd ? dno : nsc * FS[3 * P2 + t];
+      if (bnd) un = -uo;  // mirror state u+ = -u-, grad u+ = grad u- (Eq. 7)
+      const T kdA = kap * dA;
+      const T jump = uo - un;
+      cv = kdA * (sig * jump - T(0.5) * (dno + dnn));
+      c0 = T(-0.5) * kdA * jump * nsc;
+    } else {
+      const T* fd = a.fdata + (size_t)f * 7 * P2;
+      dA = fd[t];
+      sig = a.sigma[f];
+      // reference gradients in (x, y, z) from (normal, first, second
+      // tangential) components
+      const T on = FS[1 * P2 + t], o1 = FS[4 * P2 + t], o2 = FS[5 * P2 + t];
+      const T nn = FS[3 * P2 + t], n1 = FS[6 * P2 + t], n2 = FS[7 * P2 + t];
+      const T gox = D == 0 ? on : o1, goy = D == 1 ? on : (D == 0 ? o1 : o2),
+              goz = D == 2 ? on : o2;
+      const T gnx = D == 0 ? nn : n1, gny = D == 1 ? nn : (D == 0 ? n1 : n2),
+              gnz = D == 2 ? nn : n2;
+      const int oo = S ? 1 : 4, on_ = S ? 4 : 1;  // own / neighbour J^{-1} n
+      const T sgn = S ? T(1) : T(-1);  // own outward normal is sgn * n
+      const T ox = fd[oo * P2 + t], oy = fd[(oo + 1) * P2 + t],
+              oz = fd[(oo + 2) * P2 + t];
+      const T mx = fd[on_ * P2 + t], my = fd[(on_ + 1) * P2 + t],
+              mz = fd[(on_ + 2) * P2 + t];
+      dno = sgn * (ox * gox + oy * goy + oz * goz);
+      dnn = bnd ? dno : sgn * (mx * gnx + my * gny + mz * gnz);
+      if (bnd) un = -uo;
+      const T kdA = kap * dA;
+      const T jump = uo - un;
+      cv = kdA * (sig * jump - T(0.5) * (dno + dnn));
+      const T cg = T(-0.5) * kdA * jump * sgn;
+      const T gD = D == 0 ? ox : (D == 1 ? oy : oz);
+      const T g1 = D == 0 ? oy : ox;
+      const T g2 = D == 2 ? oy : oz;
+      c0 = cg * gD;
+      c1 = cg * g1;
+      c2 = cg * g2;
+    }
+  }
+  __syncthreads();
+  FS[0 * P2 + t] = cv;
+  FS[1 * P2 + t] = c0;
+  if constexpr (CURVED) {
+    FS[2 * P2 + t] = c1;
+    FS[3 * P2 + t] = c2;
+    __syncthreads();
+    // tangential test slopes fold into the face-layer values
+    for (int it = t; it < 2 * P; it += P2) {
+      if (it < P)
+        face_line<P, T, T_D, true, 0>(FS + 2 * P2, FS + 4 * P2, it);
+      else
+        face_line<P, T, T_D, true, 1>(FS + 3 * P2, FS + 5 * P2, it - P);
+    }
+    __syncthreads();
+    FS[0 * P2 + t] += FS[4 * P2 + t] + FS[5 * P2 + t];
+  }
+  __syncthreads();
+  // S^T along a, then along b, for the value and normal-slope parts
+  for (int it = t; it < 2 * P; it += P2)
+    face_line<P, T, T_S, true, 0>(FS + (it / P) * P2, FS + (2 + it / P) * P2,
+                                  it % P);
+  __syncthreads();
+  for (int it = t; it < 2 * P; it += P2)
+    face_line<P, T, T_S, true, 1>(FS + (2 + it / P) * P2, FS + (it / P) * P2,
+                                  it % P);
+  __syncthreads();
+}
+
+// One face of the own cell with line sweeps (the float variant: per-point
+// table reads would saturate the load/store unit).
 template <int P, typename T, bool CURVED, int D, int S>
-__device__ __forceinline__ void face_contrib(
+__device__ __forceinline__ void face_contrib_ln(
+    const ApplyArgs<T>& a, bool active, int cx, int cy, int cz, const T* U,
+    T* Aq, T* FS, const T* sw, int ta, int tb) {
+  int m[3] = {a.n[0], a.n[1], a.n[2]};
+  m[D] += 1;
+  int fc[3] = {cx, cy, cz};
+  fc[D] += S;
+  const int f = a.face_off[D] + fc[0] + m[0] * (fc[1] + m[1] * fc[2]);
+  int nbc[3] = {cx, cy, cz};
+  nbc[D] += S ? 1 : -1;
+  const bool bnd = nbc[D] < 0 || nbc[D] >= a.n[D];
+  const int nb = bnd ? 0 : nbc[0] + a.n[0] * (nbc[1] + a.n[1] * nbc[2]);
+  face_gather<P, T, D, S>(a, active, nb, bnd, U, FS, ta, tb);
+  __syncthreads();
+  face_core<P, T, CURVED>(a, D, S, f, bnd, FS, sw, ta, tb);
+  face_scatter<P, T, D, S>(Aq, FS, ta, tb);
+  __syncthreads();
+}
+
+// One face of the own cell (axis D, side S: 0 lower, 1 upper), per face
+// point: thread (ta, tb) interpolates all four traces to its own Gauss point
+// with table rows from shared memory (the float64 variant: its FP64 pipe,
+// not the load/store unit, is the limit).  Adds the face integrals tested
+// with the own cell's basis into Aq (nodal values).
+template <int P, typename T, bool CURVED, int D, int S>
+__device__ __forceinline__ void face_contrib_pt(
     const ApplyArgs<T>& a, bool active, int cx, int cy, int cz, const T* U,
     T* Aq, T* FS, const T* sS, const T* sD, const T* s0, const T* s1,
     const T* sw, int ta, int tb) {
@@ -437,18 +637,19 @@ __global__ void k_apply(const ApplyArgs<T> a) {
 #pragma unroll
       for (int z = 0; z < P; ++z) Aq[idx3<P>(ta, tb, z)] = o[z];
       __syncthreads();
-      face_contrib<P, T, CURVED, 0, 0>(ac, active, cx, cy, cz, U, Aq, FS, sS,
-                                       sD, s0, s1, sw, ta, tb);
-      face_contrib<P, T, CURVED, 0, 1>(ac, active, cx, cy, cz, U, Aq, FS, sS,
-                                       sD, s0, s1, sw, ta, tb);
-      face_contrib<P, T, CURVED, 1, 0>(ac, active, cx, cy, cz, U, Aq, FS, sS,
-                                       sD, s0, s1, sw, ta, tb);
-      face_contrib<P, T, CURVED, 1, 1>(ac, active, cx, cy, cz, U, Aq, FS, sS,
-                                       sD, s0, s1, sw, ta, tb);
-      face_contrib<P, T, CURVED, 2, 0>(ac, active, cx, cy, cz, U, Aq, FS, sS,
-                                       sD, s0, s1, sw, ta, tb);
-      face_contrib<P, T, CURVED, 2, 1>(ac, active, cx, cy, cz, U, Aq, FS, sS,
-                                       sD, s0, s1, sw, ta, tb);
+      if constexpr (sizeof(T) == 4) {
+#define FACE(DD, SS)                                                          \
+  face_contrib_ln<P, T, CURVED, DD, SS>(ac, active, cx, cy, cz, U, Aq, FS, sw, \
+                                        ta, tb)
+        FACE(0, 0); FACE(0, 1); FACE(1, 0); FACE(1, 1); FACE(2, 0); FACE(2, 1);
+#undef FACE
+      } else {
+#define FACE(DD, SS)                                                          \
+  face_contrib_pt<P, T, CURVED, DD, SS>(ac, active, cx, cy, cz, U, Aq, FS, sS, \
+                                        sD, s0, s1, sw, ta, tb)
+        FACE(0, 0); FACE(0, 1); FACE(1, 0); FACE(1, 1); FACE(2, 0); FACE(2, 1);
+#undef FACE
+      }
       if (active) {
 #pragma unroll
         for (int z = 0; z < P; ++z) {

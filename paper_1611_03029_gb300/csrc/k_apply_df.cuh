@@ -372,8 +372,16 @@ constexpr int df_min_blocks() {
   return P <= 5 ? (DG ? MFP_DF_MIN_BLOCKS_DG : MFP_DF_MIN_BLOCKS_CG) : 1;
 }
 
+template <int P, bool DG>
+constexpr int df_max_regs() {
+  return 65536 / (df_min_blocks<P, DG>() * df_max_threads<P>());
+}
+
+// __maxnreg__ caps the registers without capping the block size (batched
+// launches use up to 1024 threads; shapes that do not fit are rejected).
 template <int P, bool DG, bool CURVED>
-__global__ void __launch_bounds__(df_max_threads<P>(), df_min_blocks<P, DG>())
+__global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
+                                                       : df_max_regs<P, DG>()))
     k_apply_df(const ApplyArgsDF a) {
   constexpr int P2 = P * P, P3 = P2 * P;
   extern __shared__ __align__(16) unsigned char smraw[];
