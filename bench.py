@@ -46,6 +46,21 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate(ms_local, dofs_local, dist=None):
+    """Whole-job figures of one timed region: the step time is the maximum
+    over ranks, the dofs the sum over ranks (independent replicas)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms_local, dofs_local, dofs_local / (ms_local * 1e-3)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+    d = torch.tensor([float(dofs_local)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(d, op=dist.ReduceOp.SUM)
+    ms, dofs = float(t.item()), float(d.item())
+    return ms, dofs, dofs / (ms * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -340,13 +355,8 @@ def run_ours(args):
             dist.barrier()
     _, _, l1 = ops["cg"].counters()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     dofs_step = N["cg"] + N["dg"]
-    value = dofs_step * world / (ms * 1e-3)
+    ms, _, value = aggregate(sum(step_ms) / len(step_ms), dofs_step, dist)
 
     # --- mixed-precision solve rate (same workload, float32 V-cycle) -----
     for _ in range(2):
