@@ -712,12 +712,16 @@ template <int P, typename T, bool DG, bool CURVED>
 void run_apply_cols(const ApplyArgs<T>& a0, int R, int cells_req,
                     cudaStream_t s) {
   constexpr int P2 = P * P;
-  const int maxcols = 1024 / P2 > 0 ? 1024 / P2 : 1;
+  // block size limit of this kernel given its registers
+  cudaFuncAttributes fa;
+  MFP_CHECK_CUDA(cudaFuncGetAttributes(&fa, k_apply<P, T, DG, CURVED>));
+  const int maxthr = fa.maxThreadsPerBlock > 0 ? fa.maxThreadsPerBlock : 1024;
+  const int maxcols = maxthr / P2 > 0 ? maxthr / P2 : 1;
   for (int c0 = 0; c0 < R; c0 += maxcols) {
     const int nc = R - c0 < maxcols ? R - c0 : maxcols;
     int cells = cells_req > 0 ? cells_req : default_cpb(P) / nc;
     if (cells < 1) cells = 1;
-    while (cells > 1 && cells * nc * P2 > 1024) --cells;
+    while (cells > 1 && cells * nc * P2 > maxthr) --cells;
     ApplyArgs<T> a = a0;
     a.col = c0;
     run_apply<P, T, DG, CURVED>(a, cells, nc, s);
