@@ -64,6 +64,26 @@ int level_index(const mfp_ctx* c, const Level& L) {
   return (int)(&L - c->levels.data());
 }
 
+void drop_graphs(mfp_ctx* c);
+
+// Face buffer of the float64 SIPG apply in double-float arithmetic, grown
+// to R columns (never while a stream is being captured: the V-cycle's
+// levels are grown by ensure_scratch before the capture).
+void ensure_fbuf(mfp_ctx* c, Level& L, int R, cudaStream_t s) {
+  if (L.disc != MFP_SIPG || c->desc.fp64_arith != MFP_ARITH_DF ||
+      L.fbuf_rhs >= R)
+    return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (s) MFP_CHECK_CUDA(cudaStreamIsCapturing(s, &cs));
+  MFP_REQUIRE(cs == cudaStreamCaptureStatusNone,
+              "SIPG face buffer would grow inside a stream capture");
+  drop_graphs(c);  // captured applies hold the previous buffer
+  dfree(L.fbuf);
+  MFP_CHECK_CUDA(cudaMalloc(&L.fbuf, (size_t)L.ncells * 6 * L.p * L.p * R *
+                                         sizeof(float2)));
+  L.fbuf_rhs = R;
+}
+
 template <typename T>
 void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
                  cudaStream_t s) {
@@ -80,6 +100,7 @@ void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
       const double* sd = reinterpret_cast<const double*>(src);
       double* dd = reinterpret_cast<double*>(dst);
       bool ok;
+      ensure_fbuf(c, L, R, s);
       if (L.disc == MFP_CG)
         ok = apply_cg_df_lo(L, sd, dd, R, cells, s) ||
              apply_cg_df_hi(L, sd, dd, R, cells, s);
@@ -163,8 +184,6 @@ void vcycle_level(mfp_ctx* c, int l, const T* b, T* x, int R,
   smooth<T>(c, l, b, x, false, R, s);
 }
 
-void drop_graphs(mfp_ctx* c);
-
 void ensure_scratch(mfp_ctx* c, int R) {
   MFP_REQUIRE(R >= 1 && R <= kMaxRhs, "n_rhs must be in 1..256");
   bool grow = c->cg_rhs < R;
@@ -185,6 +204,11 @@ void ensure_scratch(mfp_ctx* c, int R) {
     MFP_CHECK_CUDA(cudaMalloc(&L.t_b, bytes));
     L.scratch_rhs = R;
   }
+  // float64 applies: the outer CG's on the finest level, every level's in a
+  // float64 V-cycle
+  for (size_t l = 0; l < c->levels.size(); ++l)
+    if (c->vprec == MFP_FP64 || l + 1 == c->levels.size())
+      ensure_fbuf(c, c->levels[l], R, nullptr);
   if (c->cg_rhs < R) {
     const int64_t n = c->levels.back().ndofs * (int64_t)R;
     dfree(c->cg_r);
@@ -360,6 +384,7 @@ void free_level(Level& L) {
   dfree(L.t_d);
   dfree(L.t_x);
   dfree(L.t_b);
+  dfree(L.fbuf);
 }
 
 void free_ctx(mfp_ctx* c) {

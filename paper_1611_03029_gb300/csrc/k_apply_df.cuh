@@ -38,6 +38,7 @@ struct ApplyArgsDF {
   const float *kfh, *kfl;    // [face][p^2] or null
   const float *fdh, *fdl;    // curved SIPG: [face][7][p^2]
   const float *sgh, *sgl;    // curved SIPG: [face]
+  float2* fb;                // SIPG: [cell][6][p^2] x columns, see below
   df kappa;
   bool kappa_one;            // constant coefficient exactly 1
   df gs[3], ns[3], fa[3], sg[3];
@@ -90,6 +91,55 @@ __device__ __forceinline__ void dmtv(const float (&ih)[P],
   }
 }
 
+// Rolled sum-factorization sweeps (MFP_DF_ROLL, p >= 4): a loop over the
+// output index with the table entries read by index keeps the double-float
+// code P times shorter than the unrolled matrix-vector product; unrolled,
+// the sweeps and faces of a cell overflow the instruction caches and
+// instruction fetch limits the issue rate (p <= 3 stays unrolled, its code
+// is short and the indexed table reads would cost more than they save).
+#ifndef MFP_DF_ROLL
+#define MFP_DF_ROLL 1
+#endif
+#if MFP_DF_ROLL
+#define MFP_DF_LOOP _Pragma("unroll (P >= 4 ? 1 : P)")
+#else
+#define MFP_DF_LOOP _Pragma("unroll")
+#endif
+
+// o[base + q * st] (+)= sum_j M[q][j] in[j]  (TR: M[j][q]), q = 0..P-1
+template <int P, int W, bool TR, bool ADD>
+__device__ __forceinline__ void dsweep(const float (&ih)[P],
+                                       const float (&il)[P], float* oh,
+                                       float* ol, int base, int st) {
+  MFP_DF_LOOP
+  for (int q = 0; q < P; ++q) {
+    const int i0 = TR ? q : q * P;
+    constexpr int js = TR ? P : 1;
+    dacc s = acc_first(tdh<P, W>(i0), tdl<P, W>(i0), ih[0], il[0]);
+#pragma unroll
+    for (int j = 1; j < P; ++j)
+      acc_mac(s, tdh<P, W>(i0 + j * js), tdl<P, W>(i0 + j * js), ih[j],
+              il[j]);
+    df r = acc_get(s);
+    const int o = base + q * st;
+    if constexpr (ADD) r = df_make(oh[o], ol[o]) + r;
+    oh[o] = r.h;
+    ol[o] = r.l;
+  }
+}
+
+// load the line base + j * st of a shared array into registers
+template <int P>
+__device__ __forceinline__ void dline(const float* h, const float* l,
+                                      int base, int st, float (&oh)[P],
+                                      float (&ol)[P]) {
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    oh[j] = h[base + j * st];
+    ol[j] = l[base + j * st];
+  }
+}
+
 template <int P>
 __device__ __forceinline__ int dx3(int x, int y, int z) {
   return x + P * (y + P * z);
@@ -124,60 +174,88 @@ __device__ __forceinline__ void stv(float* h, float* l, int i, df v) {
   l[i] = v.l;
 }
 
-// One face of the own cell (axis D, side S), double-float version of
-// face_contrib in k_apply.cuh.  FS holds 8 hi arrays then 8 lo arrays.
-template <int P, bool CURVED, int D, int S>
-__device__ __forceinline__ void df_face(const ApplyArgsDF& a, bool active,
-                                        int cx, int cy, int cz,
-                                        const float* Uh, const float* Ul,
-                                        float* Ah, float* Al, float* FSh,
-                                        float* FSl, const ShDF& t, int ta,
-                                        int tb) {
+template <int P>
+__device__ __forceinline__ ShDF make_shdf(const float* tabs) {
+  constexpr int P2 = P * P;
+  ShDF t;
+  t.Sh = tabs;
+  t.Sl = tabs + P2;
+  t.Dh = tabs + 2 * P2;
+  t.Dl = tabs + 3 * P2;
+  const float* p = tabs + 4 * P2;
+  t.d0h = p;
+  t.d0l = p + P;
+  t.d1h = p + 2 * P;
+  t.d1l = p + 3 * P;
+  t.wh = p + 4 * P;
+  t.wl = p + 5 * P;
+  return t;
+}
+
+// One face of the own cell with the axis D a runtime value: the hot loop
+// holds one copy of the face code instead of one per axis, which keeps the
+// double-float kernel's instruction stream short enough for the
+// instruction caches.  Each interior face is evaluated once, by the cell
+// below it (S = 1): it adds both sides' terms, the upper neighbour's into
+// the face buffer fb (slot 2D: value part, 2D + 1: normal-slope part at the
+// neighbour's face nodes) for k_dg_face_add.  A boundary face is one-sided
+// with the mirror state of Eq. 7; an interior lower face (S = 0) adds
+// nothing here.  FS holds 8 hi arrays then 8 lo arrays.
+template <int P, bool CURVED, int S>
+__device__ __forceinline__ void df_face_rt(const ApplyArgsDF& a, int col,
+                                           int D, bool active, int cx, int cy,
+                                           int cz, const float* Uh,
+                                           const float* Ul, float* Ah,
+                                           float* Al, float* FSh, float* FSl,
+                                           const ShDF& t, int ta, int tb) {
   constexpr int P2 = P * P, P3 = P2 * P;
-  constexpr int T1 = D == 0 ? 1 : 0;
-  constexpr int T2 = D == 2 ? 1 : 2;
+  constexpr int NA = S ? 4 : 2;  // arrays carried through S^T
+  constexpr int lo = S ? P - 1 : 0;
   const int ti = ta + P * tb;
-  int m[3] = {a.n[0], a.n[1], a.n[2]};
-  m[D] += 1;
-  int fc[3] = {cx, cy, cz};
-  fc[D] += S;
-  const int f = a.face_off[D] + fc[0] + m[0] * (fc[1] + m[1] * fc[2]);
-  int nbc[3] = {cx, cy, cz};
-  nbc[D] += S ? 1 : -1;
-  const bool bnd = nbc[D] < 0 || nbc[D] >= a.n[D];
-  const int nb = bnd ? 0 : nbc[0] + a.n[0] * (nbc[1] + a.n[1] * nbc[2]);
+  // node (l, ta, tb) of the own line normal to D is n0 + l * ls
+  const int ls = D == 0 ? 1 : (D == 1 ? P : P2);
+  const int n0 = D == 0 ? P * ti : (D == 1 ? ta + P2 * tb : ti);
+  const int cD = D == 0 ? cx : (D == 1 ? cy : cz);
+  const int f = a.face_off[D] + cx + (D == 0 ? S : 0) +
+                (a.n[0] + (D == 0)) *
+                    (cy + (D == 1 ? S : 0) +
+                     (a.n[1] + (D == 1)) * (cz + (D == 2 ? S : 0)));
+  const bool bnd = S ? cD + 1 >= a.n[D] : cD == 0;
+  const bool own = S == 1 || bnd;
+  const bool pair = S == 1 && !bnd && active;
+  const int nb = pair ? cx + a.n[0] * (cy + a.n[1] * cz) +
+                            (D == 0 ? 1 : (D == 1 ? a.n[0] : a.n[0] * a.n[1]))
+                      : 0;
   const float* dSh = S ? t.d1h : t.d0h;
   const float* dSl = S ? t.d1l : t.d0l;
-  const float* dNh = S ? t.d0h : t.d1h;
-  const float* dNl = S ? t.d0l : t.d1l;
-  constexpr int lo = S ? P - 1 : 0;
-  constexpr int ln = S ? 0 : P - 1;
-  // F1: nodal face values and reference normal slopes of both sides
+  // F1: nodal face values and reference normal slopes of both sides (the
+  // upper neighbour's layer 0 and slope from float64 in HBM)
   {
-    const df vo = ld(Uh, Ul, dfnode<P, D>(lo, ta, tb));
-    dacc so = acc_first(dSh[0], dSl[0], Uh[dfnode<P, D>(0, ta, tb)],
-                        Ul[dfnode<P, D>(0, ta, tb)]);
+    const df vo = ld(Uh, Ul, n0 + lo * ls);
+    dacc so = acc_first(dSh[0], dSl[0], Uh[n0], Ul[n0]);
 #pragma unroll
     for (int l = 1; l < P; ++l)
-      acc_mac(so, dSh[l], dSl[l], Uh[dfnode<P, D>(l, ta, tb)],
-              Ul[dfnode<P, D>(l, ta, tb)]);
+      acc_mac(so, dSh[l], dSl[l], Uh[n0 + l * ls], Ul[n0 + l * ls]);
     df vn = df_make(0.f), dnn = df_make(0.f);
-    if (!bnd && active) {
-      const size_t cb = (size_t)nb * P3;
-      dacc sn;
-      sn.h = 0.f;
-      sn.l = 0.f;
+    if constexpr (S == 1) {
+      if (pair) {
+        const double* u0 = a.src + ((size_t)nb * P3 + n0) * a.stride + col;
+        const size_t lstr = (size_t)ls * a.stride;
+        dacc sn;
+        sn.h = 0.f;
+        sn.l = 0.f;
 #pragma unroll
-      for (int l = 0; l < P; ++l) {
-        const df u = df_from_double(
-            a.src[(cb + dfnode<P, D>(l, ta, tb)) * a.stride + a.col]);
-        if (l == 0)
-          sn = acc_first(dNh[0], dNl[0], u.h, u.l);
-        else
-          acc_mac(sn, dNh[l], dNl[l], u.h, u.l);
-        if (l == ln) vn = u;
+        for (int l = 0; l < P; ++l) {
+          const df u = df_from_double(u0[l * lstr]);
+          if (l == 0) {
+            sn = acc_first(t.d0h[0], t.d0l[0], u.h, u.l);
+            vn = u;
+          } else {
+            acc_mac(sn, t.d0h[l], t.d0l[l], u.h, u.l);
+          }
+        }
+        dnn = acc_get(sn);
       }
-      dnn = acc_get(sn);
     }
     stv(FSh, FSl, 0 * P2 + ti, vo);
     stv(FSh, FSl, 1 * P2 + ti, acc_get(so));
@@ -185,59 +263,61 @@ __device__ __forceinline__ void df_face(const ApplyArgsDF& a, bool active,
     stv(FSh, FSl, 3 * P2 + ti, dnn);
   }
   __syncthreads();
-  // F2: interpolate along the first tangential axis
-#pragma unroll
+  // F2: interpolate along the first tangential axis (FS[arr] -> FS[4+arr])
+#pragma unroll 1
   for (int arr = 0; arr < 4; ++arr) {
-    dacc s = acc_first(t.Sh[ta * P], t.Sl[ta * P], FSh[arr * P2 + P * tb],
-                       FSl[arr * P2 + P * tb]);
+    const float* ih = FSh + arr * P2 + P * tb;
+    const float* il = FSl + arr * P2 + P * tb;
+    dacc s = acc_first(t.Sh[ta * P], t.Sl[ta * P], ih[0], il[0]);
 #pragma unroll
     for (int j = 1; j < P; ++j)
-      acc_mac(s, t.Sh[ta * P + j], t.Sl[ta * P + j],
-              FSh[arr * P2 + j + P * tb], FSl[arr * P2 + j + P * tb]);
+      acc_mac(s, t.Sh[ta * P + j], t.Sl[ta * P + j], ih[j], il[j]);
     stv(FSh, FSl, (4 + arr) * P2 + ti, acc_get(s));
   }
   __syncthreads();
-  // F3: along the second tangential axis
-  df q[4];
-#pragma unroll
+  // F3: along the second tangential axis (FS[4+arr] -> FS[arr])
+#pragma unroll 1
   for (int arr = 0; arr < 4; ++arr) {
-    dacc s = acc_first(t.Sh[tb * P], t.Sl[tb * P], FSh[(4 + arr) * P2 + ta],
-                       FSl[(4 + arr) * P2 + ta]);
+    const float* ih = FSh + (4 + arr) * P2 + ta;
+    const float* il = FSl + (4 + arr) * P2 + ta;
+    dacc s = acc_first(t.Sh[tb * P], t.Sl[tb * P], ih[0], il[0]);
 #pragma unroll
     for (int j = 1; j < P; ++j)
-      acc_mac(s, t.Sh[tb * P + j], t.Sl[tb * P + j],
-              FSh[(4 + arr) * P2 + ta + P * j],
-              FSl[(4 + arr) * P2 + ta + P * j]);
-    q[arr] = acc_get(s);
+      acc_mac(s, t.Sh[tb * P + j], t.Sl[tb * P + j], ih[P * j], il[P * j]);
+    stv(FSh, FSl, arr * P2 + ti, acc_get(s));
   }
-  __syncthreads();
-  if constexpr (CURVED) {
-    stv(FSh, FSl, 0 * P2 + ti, q[0]);
-    stv(FSh, FSl, 2 * P2 + ti, q[2]);
-    __syncthreads();
-  }
+  if constexpr (CURVED) __syncthreads();
+  // flux at the face quadrature points: value coefficient cv of the own
+  // side (-cv on the neighbour) and test-slope coefficients cg J^-1 n of
+  // each side, in face-local components (normal, tangential 1, 2)
+  df cv, c0o, c0n;
   {
     const df kap = a.kfh ? df_make(a.kfh[(size_t)f * P2 + ti],
                                    a.kfl[(size_t)f * P2 + ti])
                          : a.kappa;
-    df uo = q[0], un = q[2], dno, dnn, dA, sig;
-    df gvec[3] = {df_make(0.f), df_make(0.f), df_make(0.f)};
+    const df uo = ld(FSh, FSl, ti), q1 = ld(FSh, FSl, P2 + ti);
+    df un = ld(FSh, FSl, 2 * P2 + ti);
+    const df q3 = ld(FSh, FSl, 3 * P2 + ti);
+    df dno, dnn, dA, sig;
+    df go1, go2, gn1, gn2;  // tangential test-slope factors, both sides
+    df gvD, gnD;            // normal ones
     if constexpr (!CURVED) {
       const float sgn = S ? 1.f : -1.f;
       const df w2 = df_make(t.wh[ta], t.wl[ta]) * df_make(t.wh[tb], t.wl[tb]);
       dA = w2 * a.fa[D];
       sig = a.sg[D];
       const df nsc = df_make(sgn * a.ns[D].h, sgn * a.ns[D].l);
-      dno = nsc * q[1];
-      dnn = bnd ? dno : nsc * q[3];
-      gvec[D] = nsc;
+      dno = nsc * q1;
+      dnn = bnd ? dno : nsc * q3;
+      gvD = nsc;
+      gnD = nsc;
     } else {
-      const size_t fb = (size_t)f * 7 * P2;
-      dA = ld(a.fdh, a.fdl, fb + ti);
+      const int T1 = D == 0 ? 1 : 0;
+      const int T2 = D == 2 ? 1 : 2;
+      const size_t fb = (size_t)f * 7 * P2 + ti;
+      dA = ld(a.fdh, a.fdl, fb);
       sig = df_make(a.sgh[f], a.sgl[f]);
-      df go[3], gn[3];
-      go[D] = q[1];
-      gn[D] = q[3];
+      // reference tangential slopes of both traces
       dacc s1o = acc_first(t.Dh[ta * P], t.Dl[ta * P], FSh[P * tb],
                            FSl[P * tb]);
       dacc s2o = acc_first(t.Dh[tb * P], t.Dl[tb * P], FSh[ta], FSl[ta]);
@@ -256,109 +336,148 @@ __device__ __forceinline__ void df_face(const ApplyArgsDF& a, bool active,
         acc_mac(s2n, t.Dh[tb * P + j], t.Dl[tb * P + j],
                 FSh[2 * P2 + ta + P * j], FSl[2 * P2 + ta + P * j]);
       }
-      go[T1] = acc_get(s1o);
-      go[T2] = acc_get(s2o);
-      gn[T1] = acc_get(s1n);
-      gn[T2] = acc_get(s2n);
-      df nL[3], nR[3];
-#pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        nL[e] = ld(a.fdh, a.fdl, fb + (1 + e) * P2 + ti);
-        nR[e] = ld(a.fdh, a.fdl, fb + (4 + e) * P2 + ti);
-      }
-      if constexpr (S == 1) {  // own cell is the left one: outward = +n
-        dacc so = acc_first(nL[0].h, nL[0].l, go[0].h, go[0].l);
-        acc_mac(so, nL[1].h, nL[1].l, go[1].h, go[1].l);
-        acc_mac(so, nL[2].h, nL[2].l, go[2].h, go[2].l);
-        dacc sn = acc_first(nR[0].h, nR[0].l, gn[0].h, gn[0].l);
-        acc_mac(sn, nR[1].h, nR[1].l, gn[1].h, gn[1].l);
-        acc_mac(sn, nR[2].h, nR[2].l, gn[2].h, gn[2].l);
+      const df t1o = acc_get(s1o), t2o = acc_get(s2o);
+      // J^-1 n of the lower (L) and upper (R) cell, face-local components
+      const df LD = ld(a.fdh, a.fdl, fb + (1 + D) * P2),
+               L1 = ld(a.fdh, a.fdl, fb + (1 + T1) * P2),
+               L2 = ld(a.fdh, a.fdl, fb + (1 + T2) * P2);
+      const df RD = ld(a.fdh, a.fdl, fb + (4 + D) * P2),
+               R1 = ld(a.fdh, a.fdl, fb + (4 + T1) * P2),
+               R2 = ld(a.fdh, a.fdl, fb + (4 + T2) * P2);
+      if constexpr (S == 1) {  // own cell is the lower one: outward = +n
+        dacc so = acc_first(LD.h, LD.l, q1.h, q1.l);
+        acc_mac(so, L1.h, L1.l, t1o.h, t1o.l);
+        acc_mac(so, L2.h, L2.l, t2o.h, t2o.l);
+        const df t1n = acc_get(s1n), t2n = acc_get(s2n);
+        dacc sn = acc_first(RD.h, RD.l, q3.h, q3.l);
+        acc_mac(sn, R1.h, R1.l, t1n.h, t1n.l);
+        acc_mac(sn, R2.h, R2.l, t2n.h, t2n.l);
         dno = acc_get(so);
-        dnn = acc_get(sn);
-#pragma unroll
-        for (int e = 0; e < 3; ++e) gvec[e] = nL[e];
-      } else {  // own cell is the right one: outward = -n
-        dacc so = acc_first(nR[0].h, nR[0].l, go[0].h, go[0].l);
-        acc_mac(so, nR[1].h, nR[1].l, go[1].h, go[1].l);
-        acc_mac(so, nR[2].h, nR[2].l, go[2].h, go[2].l);
-        dacc sn = acc_first(nL[0].h, nL[0].l, gn[0].h, gn[0].l);
-        acc_mac(sn, nL[1].h, nL[1].l, gn[1].h, gn[1].l);
-        acc_mac(sn, nL[2].h, nL[2].l, gn[2].h, gn[2].l);
+        dnn = bnd ? dno : acc_get(sn);
+        gvD = LD;
+        go1 = L1;
+        go2 = L2;
+        gnD = RD;
+        gn1 = R1;
+        gn2 = R2;
+      } else {  // own cell is the upper one (boundary only): outward = -n
+        dacc so = acc_first(RD.h, RD.l, q1.h, q1.l);
+        acc_mac(so, R1.h, R1.l, t1o.h, t1o.l);
+        acc_mac(so, R2.h, R2.l, t2o.h, t2o.l);
         dno = -acc_get(so);
-        dnn = -acc_get(sn);
-#pragma unroll
-        for (int e = 0; e < 3; ++e) gvec[e] = -nR[e];
+        dnn = dno;
+        gvD = -RD;
+        go1 = -R1;
+        go2 = -R2;
+        gnD = gvD;
       }
-      if (bnd) dnn = dno;
     }
     if (bnd) un = -uo;  // mirror state (Eq. 7)
     const df kdA = kap * dA;
     const df jump = uo - un;
     const df avg = df_scale2(dno + dnn, 0.5f);
-    const df cv = kdA * (sig * jump - avg);
+    cv = kdA * (sig * jump - avg);
     const df cg = df_scale2(kdA * jump, -0.5f);
-    stv(FSh, FSl, 4 * P2 + ti, cv);
-    stv(FSh, FSl, 5 * P2 + ti, cg * gvec[D]);
+    c0o = cg * gvD;
+    c0n = cg * gnD;
     if constexpr (CURVED) {
-      stv(FSh, FSl, 6 * P2 + ti, cg * gvec[T1]);
-      stv(FSh, FSl, 7 * P2 + ti, cg * gvec[T2]);
-    }
-  }
-  __syncthreads();
-  {
-    dacc vq;
-    vq.h = FSh[4 * P2 + ti];
-    vq.l = FSl[4 * P2 + ti];
-    if constexpr (CURVED) {
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        acc_mac(vq, t.Dh[j * P + ta], t.Dl[j * P + ta], FSh[6 * P2 + j + P * tb],
-                FSl[6 * P2 + j + P * tb]);
-        acc_mac(vq, t.Dh[j * P + tb], t.Dl[j * P + tb],
-                FSh[7 * P2 + ta + P * j], FSl[7 * P2 + ta + P * j]);
+      stv(FSh, FSl, 4 * P2 + ti, cg * go1);
+      stv(FSh, FSl, 5 * P2 + ti, cg * go2);
+      if constexpr (S == 1) {
+        stv(FSh, FSl, 6 * P2 + ti, cg * gn1);
+        stv(FSh, FSl, 7 * P2 + ti, cg * gn2);
       }
     }
-    const df v = acc_get(vq);
-    const df g5 = ld(FSh, FSl, 5 * P2 + ti);
-    __syncthreads();
-    stv(FSh, FSl, 0 * P2 + ti, v);
-    stv(FSh, FSl, 1 * P2 + ti, g5);
+  }
+  // fold the tangential test slopes into the value parts (D^T at the face
+  // points)
+  {
+    df vo = cv, vn = -cv;
+    if constexpr (CURVED) {
+      __syncthreads();
+      dacc so, sn;
+      so.h = cv.h;
+      so.l = cv.l;
+      sn.h = vn.h;
+      sn.l = vn.l;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        acc_mac(so, t.Dh[j * P + ta], t.Dl[j * P + ta],
+                FSh[4 * P2 + j + P * tb], FSl[4 * P2 + j + P * tb]);
+        acc_mac(so, t.Dh[j * P + tb], t.Dl[j * P + tb],
+                FSh[5 * P2 + ta + P * j], FSl[5 * P2 + ta + P * j]);
+        if constexpr (S == 1) {
+          acc_mac(sn, t.Dh[j * P + ta], t.Dl[j * P + ta],
+                  FSh[6 * P2 + j + P * tb], FSl[6 * P2 + j + P * tb]);
+          acc_mac(sn, t.Dh[j * P + tb], t.Dl[j * P + tb],
+                  FSh[7 * P2 + ta + P * j], FSl[7 * P2 + ta + P * j]);
+        }
+      }
+      vo = acc_get(so);
+      vn = acc_get(sn);
+    }
+    stv(FSh, FSl, 0 * P2 + ti, vo);
+    stv(FSh, FSl, 1 * P2 + ti, c0o);
+    if constexpr (S == 1) {
+      stv(FSh, FSl, 2 * P2 + ti, vn);
+      stv(FSh, FSl, 3 * P2 + ti, c0n);
+    }
   }
   __syncthreads();
-  // S^T along a
-#pragma unroll
-  for (int arr = 0; arr < 2; ++arr) {
-    dacc s = acc_first(t.Sh[ta], t.Sl[ta], FSh[arr * P2 + P * tb],
-                       FSl[arr * P2 + P * tb]);
+  // S^T along a (FS[arr] -> FS[4+arr]), then along b (-> FS[arr])
+#pragma unroll 1
+  for (int arr = 0; arr < NA; ++arr) {
+    const float* ih = FSh + arr * P2 + P * tb;
+    const float* il = FSl + arr * P2 + P * tb;
+    dacc s = acc_first(t.Sh[ta], t.Sl[ta], ih[0], il[0]);
 #pragma unroll
     for (int j = 1; j < P; ++j)
-      acc_mac(s, t.Sh[j * P + ta], t.Sl[j * P + ta], FSh[arr * P2 + j + P * tb],
-              FSl[arr * P2 + j + P * tb]);
-    stv(FSh, FSl, (2 + arr) * P2 + ti, acc_get(s));
+      acc_mac(s, t.Sh[j * P + ta], t.Sl[j * P + ta], ih[j], il[j]);
+    stv(FSh, FSl, (4 + arr) * P2 + ti, acc_get(s));
   }
   __syncthreads();
-  // S^T along b and distribution onto the own nodes of line (ta, tb)
-  {
-    dacc sv = acc_first(t.Sh[tb], t.Sl[tb], FSh[2 * P2 + ta], FSl[2 * P2 + ta]);
-    dacc sn = acc_first(t.Sh[tb], t.Sl[tb], FSh[3 * P2 + ta], FSl[3 * P2 + ta]);
+#pragma unroll 1
+  for (int arr = 0; arr < NA; ++arr) {
+    const float* ih = FSh + (4 + arr) * P2 + ta;
+    const float* il = FSl + (4 + arr) * P2 + ta;
+    dacc s = acc_first(t.Sh[tb], t.Sl[tb], ih[0], il[0]);
 #pragma unroll
-    for (int j = 1; j < P; ++j) {
-      acc_mac(sv, t.Sh[j * P + tb], t.Sl[j * P + tb], FSh[2 * P2 + ta + P * j],
-              FSl[2 * P2 + ta + P * j]);
-      acc_mac(sn, t.Sh[j * P + tb], t.Sl[j * P + tb], FSh[3 * P2 + ta + P * j],
-              FSl[3 * P2 + ta + P * j]);
-    }
-    const df vf = acc_get(sv), nf = acc_get(sn);
-    {
-      const int i = dfnode<P, D>(lo, ta, tb);
-      stv(Ah, Al, i, ld(Ah, Al, i) + vf);
-    }
+    for (int j = 1; j < P; ++j)
+      acc_mac(s, t.Sh[j * P + tb], t.Sl[j * P + tb], ih[P * j], il[P * j]);
+    stv(FSh, FSl, arr * P2 + ti, acc_get(s));
+  }
+  // distribution onto the nodes of line (ta, tb): own thread's values only
+  if (own) {
+    const int i = n0 + lo * ls;
+    stv(Ah, Al, i, ld(Ah, Al, i) + ld(FSh, FSl, ti));
+    const df nf = ld(FSh, FSl, P2 + ti);
 #pragma unroll
     for (int l = 0; l < P; ++l) {
-      const int i = dfnode<P, D>(l, ta, tb);
-      stv(Ah, Al, i, ld(Ah, Al, i) + df_make(dSh[l], dSl[l]) * nf);
+      const int j = n0 + l * ls;
+      stv(Ah, Al, j, ld(Ah, Al, j) + df_make(dSh[l], dSl[l]) * nf);
     }
   }
+  if constexpr (S == 1) {
+    if (pair) {
+      float2* fbn = a.fb + ((size_t)nb * 6 + 2 * D) * P2 * a.stride + col;
+      fbn[(size_t)ti * a.stride] =
+          make_float2(FSh[2 * P2 + ti], FSl[2 * P2 + ti]);
+      fbn[(size_t)(P2 + ti) * a.stride] =
+          make_float2(FSh[3 * P2 + ti], FSl[3 * P2 + ti]);
+    }
+  }
+}
+
+template <int P, bool CURVED>
+__device__ __noinline__ void df_face_lower_rt(const ApplyArgsDF& a, int col,
+                                              int D, bool active, int cx,
+                                              int cy, int cz, const float* Uh,
+                                              const float* Ul, float* Ah,
+                                              float* Al, float* FSh,
+                                              float* FSl, const float* tabs,
+                                              int ta, int tb) {
+  df_face_rt<P, CURVED, 0>(a, col, D, active, cx, cy, cz, Uh, Ul, Ah, Al, FSh,
+                           FSl, make_shdf<P>(tabs), ta, tb);
   __syncthreads();
 }
 
@@ -382,7 +501,7 @@ constexpr int df_max_regs() {
 template <int P, bool DG, bool CURVED>
 __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
                                                        : df_max_regs<P, DG>()))
-    k_apply_df(const ApplyArgsDF a) {
+    k_apply_df(const __grid_constant__ ApplyArgsDF a) {
   constexpr int P2 = P * P, P3 = P2 * P;
   extern __shared__ __align__(16) unsigned char smraw[];
   float* sm = reinterpret_cast<float*>(smraw);
@@ -407,13 +526,9 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
   float* FSh = base + 8 * P3;
   float* FSl = FSh + 8 * P2;
   float* tabs = sm + (size_t)(cpb * nc + 1) * df_cell_floats<P, DG>();
-  ShDF t;
+  const ShDF t = make_shdf<P>(tabs);
   {
-    float* p = tabs;
-    t.Sh = p; t.Sl = p + P2; t.Dh = p + 2 * P2; t.Dl = p + 3 * P2;
-    p += 4 * P2;
-    t.d0h = p; t.d0l = p + P; t.d1h = p + 2 * P; t.d1l = p + 3 * P;
-    t.wh = p + 4 * P; t.wl = p + 5 * P;
+    float* p = tabs + 4 * P2;
     for (int i = tid; i < P2; i += blockDim.x) {
       tabs[i] = c_tabdf[P - 2].Sh[i];
       tabs[P2 + i] = c_tabdf[P - 2].Sl[i];
@@ -431,8 +546,7 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
   }
   __syncthreads();
   const int gx0 = a.g[0], gy0 = a.g[1], gz0 = a.g[2];
-  ApplyArgsDF ac = a;
-  ac.col = a.col + rr;
+  const int col = a.col + rr;
   // Cartesian quadrature weights times |K|/h_d^2 for this thread's (x, y)
   df wg[3];
   if constexpr (!CURVED) {
@@ -449,7 +563,6 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
     const int cx = cc % a.n[0];
     const int cy = (cc / a.n[0]) % a.n[1];
     const int cz = cc / (a.n[0] * a.n[1]);
-    const int col = ac.col;
     float rh[P], rl[P], oh[P], ol[P];
     // ---- gather the z-line (x = ta, y = tb), float64 -> double-float
     if constexpr (DG) {
@@ -478,61 +591,21 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
       }
     }
     // ---- values at Gauss points: z (registers), y, x
-    dmv<P, DF_S>(rh, rl, oh, ol);
-#pragma unroll
-    for (int z = 0; z < P; ++z) {
-      Ah[dx3<P>(ta, tb, z)] = oh[z];
-      Al[dx3<P>(ta, tb, z)] = ol[z];
-    }
+    dsweep<P, DF_S, false, false>(rh, rl, Ah, Al, dx3<P>(ta, tb, 0), P2);
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      rh[j] = Ah[dx3<P>(ta, j, tb)];
-      rl[j] = Al[dx3<P>(ta, j, tb)];
-    }
-    dmv<P, DF_S>(rh, rl, oh, ol);
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      Ah[dx3<P>(ta, j, tb)] = oh[j];
-      Al[dx3<P>(ta, j, tb)] = ol[j];
-    }
+    dline<P>(Ah, Al, dx3<P>(ta, 0, tb), P, rh, rl);
+    dsweep<P, DF_S, false, false>(rh, rl, Ah, Al, dx3<P>(ta, 0, tb), P);
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      rh[j] = Ah[dx3<P>(j, ta, tb)];
-      rl[j] = Al[dx3<P>(j, ta, tb)];
-    }
-    dmv<P, DF_S>(rh, rl, oh, ol);
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      Ah[dx3<P>(j, ta, tb)] = oh[j];
-      Al[dx3<P>(j, ta, tb)] = ol[j];
-    }
-    dmv<P, DF_D>(oh, ol, rh, rl);
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      Xh[dx3<P>(j, ta, tb)] = rh[j];
-      Xl[dx3<P>(j, ta, tb)] = rl[j];
-    }
+    dline<P>(Ah, Al, dx3<P>(0, ta, tb), 1, rh, rl);
+    dsweep<P, DF_S, false, false>(rh, rl, Ah, Al, dx3<P>(0, ta, tb), 1);
+    dline<P>(Ah, Al, dx3<P>(0, ta, tb), 1, rh, rl);  // own line
+    dsweep<P, DF_D, false, false>(rh, rl, Xh, Xl, dx3<P>(0, ta, tb), 1);
     __syncthreads();
     // ---- reference gradient: y into GY, z kept in registers
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      rh[j] = Ah[dx3<P>(ta, j, tb)];
-      rl[j] = Al[dx3<P>(ta, j, tb)];
-    }
-    dmv<P, DF_D>(rh, rl, oh, ol);
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      Yh[dx3<P>(ta, j, tb)] = oh[j];
-      Yl[dx3<P>(ta, j, tb)] = ol[j];
-    }
+    dline<P>(Ah, Al, dx3<P>(ta, 0, tb), P, rh, rl);
+    dsweep<P, DF_D, false, false>(rh, rl, Yh, Yl, dx3<P>(ta, 0, tb), P);
     float gzh[P], gzl[P];
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      rh[j] = Ah[dx3<P>(ta, tb, j)];
-      rl[j] = Al[dx3<P>(ta, tb, j)];
-    }
+    dline<P>(Ah, Al, dx3<P>(ta, tb, 0), P2, rh, rl);
     dmv<P, DF_D>(rh, rl, gzh, gzl);
     __syncthreads();
     // ---- quadrature-point operation t = kappa G_q grad u (Eq. 12)
@@ -583,66 +656,25 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
         rh[qz] = tz.h;
         rl[qz] = tz.l;
       }
-      dmtv<P, DF_D>(rh, rl, oh, ol);
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        Ah[dx3<P>(ta, tb, j)] = oh[j];
-        Al[dx3<P>(ta, tb, j)] = ol[j];
-      }
+      dsweep<P, DF_D, true, false>(rh, rl, Ah, Al, dx3<P>(ta, tb, 0), P2);
     }
     __syncthreads();
     // ---- transposed derivative y (added), x (added) then S^T x, y, z
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      rh[j] = Yh[dx3<P>(ta, j, tb)];
-      rl[j] = Yl[dx3<P>(ta, j, tb)];
-    }
-    dmtv<P, DF_D>(rh, rl, oh, ol);
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const int i = dx3<P>(ta, j, tb);
-      stv(Ah, Al, i, ld(Ah, Al, i) + df_make(oh[j], ol[j]));
-    }
+    dline<P>(Yh, Yl, dx3<P>(ta, 0, tb), P, rh, rl);
+    dsweep<P, DF_D, true, true>(rh, rl, Ah, Al, dx3<P>(ta, 0, tb), P);
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      rh[j] = Xh[dx3<P>(j, ta, tb)];
-      rl[j] = Xl[dx3<P>(j, ta, tb)];
-    }
-    dmtv<P, DF_D>(rh, rl, oh, ol);
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const df s = df_make(oh[j], ol[j]) + ld(Ah, Al, dx3<P>(j, ta, tb));
-      oh[j] = s.h;
-      ol[j] = s.l;
-    }
-    dmtv<P, DF_S>(oh, ol, rh, rl);
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      Ah[dx3<P>(j, ta, tb)] = rh[j];
-      Al[dx3<P>(j, ta, tb)] = rl[j];
-    }
+    dline<P>(Xh, Xl, dx3<P>(0, ta, tb), 1, rh, rl);
+    dsweep<P, DF_D, true, true>(rh, rl, Ah, Al, dx3<P>(0, ta, tb), 1);
+    dline<P>(Ah, Al, dx3<P>(0, ta, tb), 1, rh, rl);  // own line
+    dsweep<P, DF_S, true, false>(rh, rl, Ah, Al, dx3<P>(0, ta, tb), 1);
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      rh[j] = Ah[dx3<P>(ta, j, tb)];
-      rl[j] = Al[dx3<P>(ta, j, tb)];
-    }
-    dmtv<P, DF_S>(rh, rl, oh, ol);
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      Ah[dx3<P>(ta, j, tb)] = oh[j];
-      Al[dx3<P>(ta, j, tb)] = ol[j];
-    }
+    dline<P>(Ah, Al, dx3<P>(ta, 0, tb), P, rh, rl);
+    dsweep<P, DF_S, true, false>(rh, rl, Ah, Al, dx3<P>(ta, 0, tb), P);
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      rh[j] = Ah[dx3<P>(ta, tb, j)];
-      rl[j] = Al[dx3<P>(ta, tb, j)];
-    }
-    dmtv<P, DF_S>(rh, rl, oh, ol);
-    // ---- scatter (float64)
+    dline<P>(Ah, Al, dx3<P>(ta, tb, 0), P2, rh, rl);
+    // ---- S^T along z and scatter (float64)
     if constexpr (!DG) {
+      dmtv<P, DF_S>(rh, rl, oh, ol);
       const int X = cx * (P - 1) + ta, Y = cy * (P - 1) + tb;
       const bool bxy = X == 0 || X == gx0 - 1 || Y == 0 || Y == gy0 - 1;
       if (active) {
@@ -661,24 +693,18 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
       }
       __syncthreads();
     } else {
-#pragma unroll
-      for (int z = 0; z < P; ++z) {
-        Ah[dx3<P>(ta, tb, z)] = oh[z];
-        Al[dx3<P>(ta, tb, z)] = ol[z];
-      }
+      dsweep<P, DF_S, true, false>(rh, rl, Ah, Al, dx3<P>(ta, tb, 0), P2);
       __syncthreads();
-      df_face<P, CURVED, 0, 0>(ac, active, cx, cy, cz, Uh, Ul, Ah, Al, FSh,
-                               FSl, t, ta, tb);
-      df_face<P, CURVED, 0, 1>(ac, active, cx, cy, cz, Uh, Ul, Ah, Al, FSh,
-                               FSl, t, ta, tb);
-      df_face<P, CURVED, 1, 0>(ac, active, cx, cy, cz, Uh, Ul, Ah, Al, FSh,
-                               FSl, t, ta, tb);
-      df_face<P, CURVED, 1, 1>(ac, active, cx, cy, cz, Uh, Ul, Ah, Al, FSh,
-                               FSl, t, ta, tb);
-      df_face<P, CURVED, 2, 0>(ac, active, cx, cy, cz, Uh, Ul, Ah, Al, FSh,
-                               FSl, t, ta, tb);
-      df_face<P, CURVED, 2, 1>(ac, active, cx, cy, cz, Uh, Ul, Ah, Al, FSh,
-                               FSl, t, ta, tb);
+#pragma unroll 1
+      for (int D = 0; D < 3; ++D) {
+        // lower faces only where a cell of the block lies on the boundary
+        const int cD = D == 0 ? cx : (D == 1 ? cy : cz);
+        if (__syncthreads_or(active && cD == 0))
+          df_face_lower_rt<P, CURVED>(a, col, D, active, cx, cy, cz, Uh, Ul,
+                                      Ah, Al, FSh, FSl, tabs, ta, tb);
+        df_face_rt<P, CURVED, 1>(a, col, D, active, cx, cy, cz, Uh, Ul, Ah, Al,
+                                 FSh, FSl, t, ta, tb);
+      }
       if (active) {
 #pragma unroll
         for (int z = 0; z < P; ++z) {
@@ -689,6 +715,63 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
       }
       __syncthreads();
     }
+  }
+}
+
+// SIPG with each interior face evaluated once: adds the terms that the
+// cell below each interior face left for the cell above it (face buffer
+// slots 2D: value part at the face nodes, 2D+1: normal-slope part).  The
+// value part enters the face layer l = 0 along D, the slope part every
+// layer with the weight dphi_l(0) of the reference normal derivative.
+template <int P>
+__global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
+  constexpr int P2 = P * P, P3 = P2 * P;
+  // grid: x over the nodes of one row of cells along x, y over the rows
+  // (cy, cz), z over the columns of a batch
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n[0] * P3) return;
+  const int R = a.stride, col = blockIdx.z;
+  const int cx = i / P3, node = i - cx * P3;
+  const int x = node % P, y = (node / P) % P, z = node / P2;
+  const int rows = a.n[1] * a.n[2];
+  const float* d0h = c_tabdf[P - 2].d0h;
+  const float* d0l = c_tabdf[P - 2].d0l;
+  for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+    const int cy = row % a.n[1], cz = row / a.n[1];
+    const int cell = row * a.n[0] + cx;
+    const float2* fb = a.fb + (size_t)cell * 6 * P2 * R + col;
+    double* out = a.dst + ((size_t)cell * P3 + node) * R + col;
+    df s = df_from_double(*out);
+    // lower faces inside the mesh: value part on layer 0, slope part on
+    // every layer
+    if (cx > 0) {
+      const float2 g = fb[(size_t)(1 * P2 + y + P * z) * R];
+      df t = df_make(d0h[x], d0l[x]) * df_make(g.x, g.y);
+      if (x == 0) {
+        const float2 v = fb[(size_t)(0 * P2 + y + P * z) * R];
+        t = t + df_make(v.x, v.y);
+      }
+      s = s + t;
+    }
+    if (cy > 0) {
+      const float2 g = fb[(size_t)(3 * P2 + x + P * z) * R];
+      df t = df_make(d0h[y], d0l[y]) * df_make(g.x, g.y);
+      if (y == 0) {
+        const float2 v = fb[(size_t)(2 * P2 + x + P * z) * R];
+        t = t + df_make(v.x, v.y);
+      }
+      s = s + t;
+    }
+    if (cz > 0) {
+      const float2 g = fb[(size_t)(5 * P2 + x + P * y) * R];
+      df t = df_make(d0h[z], d0l[z]) * df_make(g.x, g.y);
+      if (z == 0) {
+        const float2 v = fb[(size_t)(4 * P2 + x + P * y) * R];
+        t = t + df_make(v.x, v.y);
+      }
+      s = s + t;
+    }
+    *out = df_to_double(s);
   }
 }
 
@@ -752,6 +835,18 @@ void run_apply_df_cols(const ApplyArgsDF& a0, int R, int cells_req,
     a.col = c0;
     run_apply_df<P, DG, CURVED>(a, cells, nc, s);
   }
+  if constexpr (DG) {
+    MFP_REQUIRE(a0.fb, "SIPG face buffer missing");
+    const int threads = 256;
+    const int bx = (a0.n[0] * P2 * P + threads - 1) / threads;
+    const int rows = a0.n[1] * a0.n[2];
+    const int by = rows < 65535 ? rows : 65535;
+    if (a0.ncells > 0) {
+      k_dg_face_add<P><<<dim3(bx, by, R), threads, 0, s>>>(a0);
+      MFP_CHECK_CUDA(cudaGetLastError());
+      note_launch();
+    }
+  }
 }
 
 inline df host_df(double v) {
@@ -783,6 +878,7 @@ inline ApplyArgsDF make_apply_args_df(const Level& L, const double* src,
   a.fdl = D.fdl;
   a.sgh = D.sgh;
   a.sgl = D.sgl;
+  a.fb = static_cast<float2*>(L.fbuf);
   a.kappa = host_df(L.kappa);
   a.kappa_one = L.kappa == 1.0;
   const double vol = L.h[0] * L.h[1] * L.h[2];

@@ -150,6 +150,10 @@ struct Level {
   void* t_x = nullptr;    // iterate (levels below the finest)
   void* t_b = nullptr;    // right-hand side (levels below the finest)
   int scratch_rhs = 0;
+  // float64 SIPG apply in double-float arithmetic: the face terms each cell
+  // leaves for its upper neighbours, [ncells][6][p^2] float pairs x fbuf_rhs
+  void* fbuf = nullptr;
+  int fbuf_rhs = 0;
 };
 
 template <typename T>
