@@ -325,7 +325,7 @@ __device__ __forceinline__ void df_face_rt(const ApplyArgsDF& a, int col,
                            FSl[2 * P2 + P * tb]);
       dacc s2n = acc_first(t.Dh[tb * P], t.Dl[tb * P], FSh[2 * P2 + ta],
                            FSl[2 * P2 + ta]);
-#pragma unroll
+      MFP_DF_LOOP
       for (int j = 1; j < P; ++j) {
         acc_mac(s1o, t.Dh[ta * P + j], t.Dl[ta * P + j], FSh[j + P * tb],
                 FSl[j + P * tb]);
@@ -400,7 +400,7 @@ __device__ __forceinline__ void df_face_rt(const ApplyArgsDF& a, int col,
       so.l = cv.l;
       sn.h = vn.h;
       sn.l = vn.l;
-#pragma unroll
+      MFP_DF_LOOP
       for (int j = 0; j < P; ++j) {
         acc_mac(so, t.Dh[j * P + ta], t.Dl[j * P + ta],
                 FSh[4 * P2 + j + P * tb], FSl[4 * P2 + j + P * tb]);
@@ -451,7 +451,7 @@ __device__ __forceinline__ void df_face_rt(const ApplyArgsDF& a, int col,
     const int i = n0 + lo * ls;
     stv(Ah, Al, i, ld(Ah, Al, i) + ld(FSh, FSl, ti));
     const df nf = ld(FSh, FSl, P2 + ti);
-#pragma unroll
+    MFP_DF_LOOP
     for (int l = 0; l < P; ++l) {
       const int j = n0 + l * ls;
       stv(Ah, Al, j, ld(Ah, Al, j) + df_make(dSh[l], dSl[l]) * nf);
@@ -604,17 +604,21 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
     // ---- reference gradient: y into GY, z kept in registers
     dline<P>(Ah, Al, dx3<P>(ta, 0, tb), P, rh, rl);
     dsweep<P, DF_D, false, false>(rh, rl, Yh, Yl, dx3<P>(ta, 0, tb), P);
-    float gzh[P], gzl[P];
-    dline<P>(Ah, Al, dx3<P>(ta, tb, 0), P2, rh, rl);
-    dmv<P, DF_D>(rh, rl, gzh, gzl);
+    dline<P>(Ah, Al, dx3<P>(ta, tb, 0), P2, rh, rl);  // z-line of values
     __syncthreads();
-    // ---- quadrature-point operation t = kappa G_q grad u (Eq. 12)
+    // ---- quadrature-point operation t = kappa G_q grad u (Eq. 12), the z
+    // derivative taken at each point from the z-line in registers
     {
-#pragma unroll
+      MFP_DF_LOOP
       for (int qz = 0; qz < P; ++qz) {
         const int q = dx3<P>(ta, tb, qz);
-        const df ux = ld(Xh, Xl, q), uy = ld(Yh, Yl, q),
-                 uz = df_make(gzh[qz], gzl[qz]);
+        dacc dz = acc_first(tdh<P, DF_D>(qz * P), tdl<P, DF_D>(qz * P), rh[0],
+                            rl[0]);
+#pragma unroll
+        for (int j = 1; j < P; ++j)
+          acc_mac(dz, tdh<P, DF_D>(qz * P + j), tdl<P, DF_D>(qz * P + j),
+                  rh[j], rl[j]);
+        const df ux = ld(Xh, Xl, q), uy = ld(Yh, Yl, q), uz = acc_get(dz);
         df tx, ty, tz;
         if constexpr (CURVED) {
           const size_t gb = (size_t)cc * 6 * P3 + q;
@@ -653,9 +657,9 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
         }
         stv(Xh, Xl, q, tx);
         stv(Yh, Yl, q, ty);
-        rh[qz] = tz.h;
-        rl[qz] = tz.l;
+        stv(Ah, Al, q, tz);
       }
+      dline<P>(Ah, Al, dx3<P>(ta, tb, 0), P2, rh, rl);  // own z-line
       dsweep<P, DF_D, true, false>(rh, rl, Ah, Al, dx3<P>(ta, tb, 0), P2);
     }
     __syncthreads();
@@ -726,52 +730,66 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
 template <int P>
 __global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
   constexpr int P2 = P * P, P3 = P2 * P;
-  // grid: x over the nodes of one row of cells along x, y over the rows
-  // (cy, cz), z over the columns of a batch
+  // one thread per node line along z (cell cx, x, y) of the row of cells
+  // (cy, cz) = blockIdx.y; blockIdx.z is the column of a batch
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n[0] * P3) return;
+  if (i >= a.n[0] * P2) return;
   const int R = a.stride, col = blockIdx.z;
-  const int cx = i / P3, node = i - cx * P3;
-  const int x = node % P, y = (node / P) % P, z = node / P2;
-  const int rows = a.n[1] * a.n[2];
+  const int cx = i / P2, xy = i - cx * P2;
+  const int x = xy % P, y = xy / P;
   const float* d0h = c_tabdf[P - 2].d0h;
   const float* d0l = c_tabdf[P - 2].d0l;
+  const int rows = a.n[1] * a.n[2];
   for (int row = blockIdx.y; row < rows; row += gridDim.y) {
     const int cy = row % a.n[1], cz = row / a.n[1];
-    const int cell = row * a.n[0] + cx;
-    const float2* fb = a.fb + (size_t)cell * 6 * P2 * R + col;
-    double* out = a.dst + ((size_t)cell * P3 + node) * R + col;
-    df s = df_from_double(*out);
-    // lower faces inside the mesh: value part on layer 0, slope part on
-    // every layer
+    const size_t cell = (size_t)row * a.n[0] + cx;
+    const float2* fb = a.fb + cell * 6 * P2 * R + col;
+    double* out = a.dst + (cell * P3 + xy) * R + col;
+    dacc s[P];
+#pragma unroll
+    for (int z = 0; z < P; ++z) {
+      const df u = df_from_double(out[(size_t)z * P2 * R]);
+      s[z].h = u.h;
+      s[z].l = u.l;
+    }
+    // lower faces inside the mesh: the slope part on every layer along the
+    // face normal (weight dphi_l(0)), the value part on layer 0
     if (cx > 0) {
-      const float2 g = fb[(size_t)(1 * P2 + y + P * z) * R];
-      df t = df_make(d0h[x], d0l[x]) * df_make(g.x, g.y);
-      if (x == 0) {
-        const float2 v = fb[(size_t)(0 * P2 + y + P * z) * R];
-        t = t + df_make(v.x, v.y);
+      const df w = df_make(d0h[x], d0l[x]);
+#pragma unroll
+      for (int z = 0; z < P; ++z) {
+        const float2 g = fb[(size_t)(1 * P2 + y + P * z) * R];
+        acc_mac(s[z], w.h, w.l, g.x, g.y);
+        if (x == 0) {
+          const float2 v = fb[(size_t)(0 * P2 + y + P * z) * R];
+          acc_add(s[z], df_make(v.x, v.y));
+        }
       }
-      s = s + t;
     }
     if (cy > 0) {
-      const float2 g = fb[(size_t)(3 * P2 + x + P * z) * R];
-      df t = df_make(d0h[y], d0l[y]) * df_make(g.x, g.y);
-      if (y == 0) {
-        const float2 v = fb[(size_t)(2 * P2 + x + P * z) * R];
-        t = t + df_make(v.x, v.y);
+      const df w = df_make(d0h[y], d0l[y]);
+#pragma unroll
+      for (int z = 0; z < P; ++z) {
+        const float2 g = fb[(size_t)(3 * P2 + x + P * z) * R];
+        acc_mac(s[z], w.h, w.l, g.x, g.y);
+        if (y == 0) {
+          const float2 v = fb[(size_t)(2 * P2 + x + P * z) * R];
+          acc_add(s[z], df_make(v.x, v.y));
+        }
       }
-      s = s + t;
     }
     if (cz > 0) {
-      const float2 g = fb[(size_t)(5 * P2 + x + P * y) * R];
-      df t = df_make(d0h[z], d0l[z]) * df_make(g.x, g.y);
-      if (z == 0) {
-        const float2 v = fb[(size_t)(4 * P2 + x + P * y) * R];
-        t = t + df_make(v.x, v.y);
+      const float2 g = fb[(size_t)(5 * P2 + xy) * R];
+      const float2 v = fb[(size_t)(4 * P2 + xy) * R];
+#pragma unroll
+      for (int z = 0; z < P; ++z) {
+        acc_mac(s[z], d0h[z], d0l[z], g.x, g.y);
+        if (z == 0) acc_add(s[z], df_make(v.x, v.y));
       }
-      s = s + t;
     }
-    *out = df_to_double(s);
+#pragma unroll
+    for (int z = 0; z < P; ++z)
+      out[(size_t)z * P2 * R] = df_to_double(acc_get(s[z]));
   }
 }
 
@@ -838,7 +856,7 @@ void run_apply_df_cols(const ApplyArgsDF& a0, int R, int cells_req,
   if constexpr (DG) {
     MFP_REQUIRE(a0.fb, "SIPG face buffer missing");
     const int threads = 256;
-    const int bx = (a0.n[0] * P2 * P + threads - 1) / threads;
+    const int bx = (a0.n[0] * P2 + threads - 1) / threads;
     const int rows = a0.n[1] * a0.n[2];
     const int by = rows < 65535 ? rows : 65535;
     if (a0.ncells > 0) {
