@@ -12,15 +12,14 @@
 #include "dev_tables.cuh"
 #include "df.cuh"
 
-// Resident 128-thread blocks per SM the register allocation must allow:
-// CG gains from more warps (latency of the gather and geometry loads), SIPG
-// from more registers (its face code spills below 128 per thread); measured
-// on 32^3 Q3/Q4 Cartesian and curved meshes.
-#ifndef MFP_DF_MIN_BLOCKS_CG
-#define MFP_DF_MIN_BLOCKS_CG 8
-#endif
-#ifndef MFP_DF_MIN_BLOCKS_DG
-#define MFP_DF_MIN_BLOCKS_DG 4
+// Resident blocks per SM the register allocation must allow (blocks of at
+// most 128 threads for p <= 5, 256 above), measured on 24^3..64^3 meshes
+// for k = 2..8: more resident warps hide the latency of the shared-memory
+// sweeps and the gathers, down to about 85 registers per thread; CG p >= 7
+// keeps its larger line arrays in registers.  MFP_DF_MIN_BLOCKS overrides
+// the table for experiments.
+#ifndef MFP_DF_MIN_BLOCKS
+#define MFP_DF_MIN_BLOCKS 0
 #endif
 
 namespace mfp {
@@ -481,14 +480,13 @@ __device__ __noinline__ void df_face_lower_rt(const ApplyArgsDF& a, int col,
   __syncthreads();
 }
 
-// Register budget: enough resident warps to hide the load latency
-// (blocks of at most 128 threads for p <= 5, 256 above).
 template <int P>
 constexpr int df_max_threads() { return P <= 5 ? 128 : 256; }
 template <int P, bool DG>
 constexpr int df_min_blocks() {
-  // p >= 6: no cap (the larger line arrays would spill kilobytes)
-  return P <= 5 ? (DG ? MFP_DF_MIN_BLOCKS_DG : MFP_DF_MIN_BLOCKS_CG) : 1;
+  if (MFP_DF_MIN_BLOCKS > 0) return MFP_DF_MIN_BLOCKS;
+  if (DG) return P <= 3 ? 5 : (P <= 5 ? 6 : 2);
+  return P <= 5 ? 8 : (P == 6 ? 3 : 1);
 }
 
 template <int P, bool DG>
