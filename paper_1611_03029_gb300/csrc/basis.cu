@@ -143,6 +143,22 @@ const HostTables& host_tables() {
         split(d.dphi1[i], t.d1h[i], t.d1l[i]);
         split(d.w[i], t.wh[i], t.wl[i]);
       }
+      // Gauss-point Lagrange basis at the ends of [0, 1], in long double
+      {
+        const int p = k + 1;
+        ld xg[kMaxP], wg[kMaxP];
+        gauss(p, xg, wg);
+        for (int i = 0; i < p; ++i) xg[i] = (xg[i] + 1) / 2;
+        for (int q = 0; q < p; ++q) {
+          split((double)lagrange(xg, p, q, 0.0L), t.gv0h[q], t.gv0l[q]);
+          split((double)lagrange(xg, p, q, 1.0L), t.gv1h[q], t.gv1l[q]);
+          split((double)lagrange_deriv(xg, p, q, 0.0L), t.gd0h[q], t.gd0l[q]);
+          split((double)lagrange_deriv(xg, p, q, 1.0L), t.gd1h[q], t.gd1l[q]);
+        }
+        for (int q = p; q < kMaxP; ++q)
+          t.gv0h[q] = t.gv0l[q] = t.gv1h[q] = t.gv1l[q] = t.gd0h[q] =
+              t.gd0l[q] = t.gd1h[q] = t.gd1l[q] = 0.f;
+      }
     }
   });
   return tabs;

@@ -191,27 +191,32 @@ __device__ __forceinline__ ShDF make_shdf(const float* tabs) {
   return t;
 }
 
-// One face of the own cell with the axis D a runtime value: the hot loop
-// holds one copy of the face code instead of one per axis, which keeps the
-// double-float kernel's instruction stream short enough for the
-// instruction caches.  Each interior face is evaluated once, by the cell
-// below it (S = 1): it adds both sides' terms, the upper neighbour's into
-// the face buffer fb (slot 2D: value part, 2D + 1: normal-slope part at the
-// neighbour's face nodes) for k_dg_face_add.  A boundary face is one-sided
+// One face of the own cell (axis D a runtime value, one copy of the face
+// code in the kernel).  The own side works on the cell's values at its
+// Gauss points: its trace and reference normal slope at face point
+// (ta, tb) come from the line of Gauss-point values along D through it
+// (Lagrange basis of the Gauss points at the cell end, exact for the
+// degree-k polynomial), and its value and normal-slope test terms go back
+// onto the same line of the Gauss-point accumulator A, which the cell's
+// S^T sweeps then take to the nodes.  Each interior face is evaluated
+// once, by the cell below it (S = 1): the upper neighbour's trace comes
+// from its float64 nodal values (face layer and normal slope, then S x S
+// to the face points), and its test terms go through S^T x S^T to its
+// face nodes and into the face buffer fb (slot 2D: value part, 2D + 1:
+// normal-slope part) for k_dg_face_add.  A boundary face is one-sided
 // with the mirror state of Eq. 7; an interior lower face (S = 0) adds
 // nothing here.  FS holds 8 hi arrays then 8 lo arrays.
 template <int P, bool CURVED, int S>
-__device__ __forceinline__ void df_face_rt(const ApplyArgsDF& a, int col,
+__device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
                                            int D, bool active, int cx, int cy,
                                            int cz, const float* Uh,
                                            const float* Ul, float* Ah,
                                            float* Al, float* FSh, float* FSl,
                                            const ShDF& t, int ta, int tb) {
   constexpr int P2 = P * P, P3 = P2 * P;
-  constexpr int NA = S ? 4 : 2;  // arrays carried through S^T
-  constexpr int lo = S ? P - 1 : 0;
   const int ti = ta + P * tb;
-  // node (l, ta, tb) of the own line normal to D is n0 + l * ls
+  // point (l, ta, tb) of the own line normal to D is n0 + l * ls (the same
+  // for Gauss points and nodes)
   const int ls = D == 0 ? 1 : (D == 1 ? P : P2);
   const int n0 = D == 0 ? P * ti : (D == 1 ? ta + P2 * tb : ti);
   const int cD = D == 0 ? cx : (D == 1 ? cy : cz);
@@ -225,65 +230,71 @@ __device__ __forceinline__ void df_face_rt(const ApplyArgsDF& a, int col,
   const int nb = pair ? cx + a.n[0] * (cy + a.n[1] * cz) +
                             (D == 0 ? 1 : (D == 1 ? a.n[0] : a.n[0] * a.n[1]))
                       : 0;
-  const float* dSh = S ? t.d1h : t.d0h;
-  const float* dSl = S ? t.d1l : t.d0l;
-  // F1: nodal face values and reference normal slopes of both sides (the
-  // upper neighbour's layer 0 and slope from float64 in HBM)
+  const DevTabDF& T = c_tabdf[P - 2];
+  const float* gvh = S ? T.gv1h : T.gv0h;
+  const float* gvl = S ? T.gv1l : T.gv0l;
+  const float* gdh = S ? T.gd1h : T.gd0h;
+  const float* gdl = S ? T.gd1l : T.gd0l;
+  // own trace and reference normal slope at the face point (ta, tb)
+  df uo, so;
   {
-    const df vo = ld(Uh, Ul, n0 + lo * ls);
-    dacc so = acc_first(dSh[0], dSl[0], Uh[n0], Ul[n0]);
+    dacc sv = acc_first(gvh[0], gvl[0], Uh[n0], Ul[n0]);
+    dacc sd = acc_first(gdh[0], gdl[0], Uh[n0], Ul[n0]);
 #pragma unroll
-    for (int l = 1; l < P; ++l)
-      acc_mac(so, dSh[l], dSl[l], Uh[n0 + l * ls], Ul[n0 + l * ls]);
-    df vn = df_make(0.f), dnn = df_make(0.f);
-    if constexpr (S == 1) {
-      if (pair) {
-        const double* u0 = a.src + ((size_t)nb * P3 + n0) * a.stride + col;
-        const size_t lstr = (size_t)ls * a.stride;
-        dacc sn;
-        sn.h = 0.f;
-        sn.l = 0.f;
-#pragma unroll
-        for (int l = 0; l < P; ++l) {
-          const df u = df_from_double(u0[l * lstr]);
-          if (l == 0) {
-            sn = acc_first(t.d0h[0], t.d0l[0], u.h, u.l);
-            vn = u;
-          } else {
-            acc_mac(sn, t.d0h[l], t.d0l[l], u.h, u.l);
-          }
-        }
-        dnn = acc_get(sn);
-      }
+    for (int l = 1; l < P; ++l) {
+      acc_mac(sv, gvh[l], gvl[l], Uh[n0 + l * ls], Ul[n0 + l * ls]);
+      acc_mac(sd, gdh[l], gdl[l], Uh[n0 + l * ls], Ul[n0 + l * ls]);
     }
-    stv(FSh, FSl, 0 * P2 + ti, vo);
-    stv(FSh, FSl, 1 * P2 + ti, acc_get(so));
+    uo = acc_get(sv);
+    so = acc_get(sd);
+  }
+  if constexpr (CURVED) stv(FSh, FSl, 0 * P2 + ti, uo);
+  // the upper neighbour's face layer and reference normal slope (nodal),
+  // interpolated to the face points: FS[2, 3] -> FS[6, 7] -> FS[2, 3]
+  if constexpr (S == 1) {
+    df vn = df_make(0.f), dnn = df_make(0.f);
+    if (pair) {
+      const double* u0 = a.src + ((size_t)nb * P3 + n0) * a.stride + col;
+      const size_t lstr = (size_t)ls * a.stride;
+      dacc sn;
+      sn.h = 0.f;
+      sn.l = 0.f;
+#pragma unroll
+      for (int l = 0; l < P; ++l) {
+        const df u = df_from_double(u0[l * lstr]);
+        if (l == 0) {
+          sn = acc_first(t.d0h[0], t.d0l[0], u.h, u.l);
+          vn = u;
+        } else {
+          acc_mac(sn, t.d0h[l], t.d0l[l], u.h, u.l);
+        }
+      }
+      dnn = acc_get(sn);
+    }
     stv(FSh, FSl, 2 * P2 + ti, vn);
     stv(FSh, FSl, 3 * P2 + ti, dnn);
-  }
-  __syncthreads();
-  // F2: interpolate along the first tangential axis (FS[arr] -> FS[4+arr])
+    __syncthreads();
 #pragma unroll 1
-  for (int arr = 0; arr < 4; ++arr) {
-    const float* ih = FSh + arr * P2 + P * tb;
-    const float* il = FSl + arr * P2 + P * tb;
-    dacc s = acc_first(t.Sh[ta * P], t.Sl[ta * P], ih[0], il[0]);
+    for (int arr = 2; arr < 4; ++arr) {
+      const float* ih = FSh + arr * P2 + P * tb;
+      const float* il = FSl + arr * P2 + P * tb;
+      dacc s = acc_first(t.Sh[ta * P], t.Sl[ta * P], ih[0], il[0]);
 #pragma unroll
-    for (int j = 1; j < P; ++j)
-      acc_mac(s, t.Sh[ta * P + j], t.Sl[ta * P + j], ih[j], il[j]);
-    stv(FSh, FSl, (4 + arr) * P2 + ti, acc_get(s));
-  }
-  __syncthreads();
-  // F3: along the second tangential axis (FS[4+arr] -> FS[arr])
+      for (int j = 1; j < P; ++j)
+        acc_mac(s, t.Sh[ta * P + j], t.Sl[ta * P + j], ih[j], il[j]);
+      stv(FSh, FSl, (4 + arr) * P2 + ti, acc_get(s));
+    }
+    __syncthreads();
 #pragma unroll 1
-  for (int arr = 0; arr < 4; ++arr) {
-    const float* ih = FSh + (4 + arr) * P2 + ta;
-    const float* il = FSl + (4 + arr) * P2 + ta;
-    dacc s = acc_first(t.Sh[tb * P], t.Sl[tb * P], ih[0], il[0]);
+    for (int arr = 2; arr < 4; ++arr) {
+      const float* ih = FSh + (4 + arr) * P2 + ta;
+      const float* il = FSl + (4 + arr) * P2 + ta;
+      dacc s = acc_first(t.Sh[tb * P], t.Sl[tb * P], ih[0], il[0]);
 #pragma unroll
-    for (int j = 1; j < P; ++j)
-      acc_mac(s, t.Sh[tb * P + j], t.Sl[tb * P + j], ih[P * j], il[P * j]);
-    stv(FSh, FSl, arr * P2 + ti, acc_get(s));
+      for (int j = 1; j < P; ++j)
+        acc_mac(s, t.Sh[tb * P + j], t.Sl[tb * P + j], ih[P * j], il[P * j]);
+      stv(FSh, FSl, arr * P2 + ti, acc_get(s));
+    }
   }
   if constexpr (CURVED) __syncthreads();
   // flux at the face quadrature points: value coefficient cv of the own
@@ -294,9 +305,8 @@ __device__ __forceinline__ void df_face_rt(const ApplyArgsDF& a, int col,
     const df kap = a.kfh ? df_make(a.kfh[(size_t)f * P2 + ti],
                                    a.kfl[(size_t)f * P2 + ti])
                          : a.kappa;
-    const df uo = ld(FSh, FSl, ti), q1 = ld(FSh, FSl, P2 + ti);
-    df un = ld(FSh, FSl, 2 * P2 + ti);
-    const df q3 = ld(FSh, FSl, 3 * P2 + ti);
+    df un = S ? ld(FSh, FSl, 2 * P2 + ti) : df_make(0.f);
+    const df q3 = S ? ld(FSh, FSl, 3 * P2 + ti) : df_make(0.f);
     df dno, dnn, dA, sig;
     df go1, go2, gn1, gn2;  // tangential test-slope factors, both sides
     df gvD, gnD;            // normal ones
@@ -306,7 +316,7 @@ __device__ __forceinline__ void df_face_rt(const ApplyArgsDF& a, int col,
       dA = w2 * a.fa[D];
       sig = a.sg[D];
       const df nsc = df_make(sgn * a.ns[D].h, sgn * a.ns[D].l);
-      dno = nsc * q1;
+      dno = nsc * so;
       dnn = bnd ? dno : nsc * q3;
       gvD = nsc;
       gnD = nsc;
@@ -316,43 +326,47 @@ __device__ __forceinline__ void df_face_rt(const ApplyArgsDF& a, int col,
       const size_t fb = (size_t)f * 7 * P2 + ti;
       dA = ld(a.fdh, a.fdl, fb);
       sig = df_make(a.sgh[f], a.sgl[f]);
-      // reference tangential slopes of both traces
+      // reference tangential slopes of the own trace
       dacc s1o = acc_first(t.Dh[ta * P], t.Dl[ta * P], FSh[P * tb],
                            FSl[P * tb]);
       dacc s2o = acc_first(t.Dh[tb * P], t.Dl[tb * P], FSh[ta], FSl[ta]);
-      dacc s1n = acc_first(t.Dh[ta * P], t.Dl[ta * P], FSh[2 * P2 + P * tb],
-                           FSl[2 * P2 + P * tb]);
-      dacc s2n = acc_first(t.Dh[tb * P], t.Dl[tb * P], FSh[2 * P2 + ta],
-                           FSl[2 * P2 + ta]);
       MFP_DF_LOOP
       for (int j = 1; j < P; ++j) {
         acc_mac(s1o, t.Dh[ta * P + j], t.Dl[ta * P + j], FSh[j + P * tb],
                 FSl[j + P * tb]);
         acc_mac(s2o, t.Dh[tb * P + j], t.Dl[tb * P + j], FSh[ta + P * j],
                 FSl[ta + P * j]);
-        acc_mac(s1n, t.Dh[ta * P + j], t.Dl[ta * P + j],
-                FSh[2 * P2 + j + P * tb], FSl[2 * P2 + j + P * tb]);
-        acc_mac(s2n, t.Dh[tb * P + j], t.Dl[tb * P + j],
-                FSh[2 * P2 + ta + P * j], FSl[2 * P2 + ta + P * j]);
       }
       const df t1o = acc_get(s1o), t2o = acc_get(s2o);
       // J^-1 n of the lower (L) and upper (R) cell, face-local components
-      const df LD = ld(a.fdh, a.fdl, fb + (1 + D) * P2),
-               L1 = ld(a.fdh, a.fdl, fb + (1 + T1) * P2),
-               L2 = ld(a.fdh, a.fdl, fb + (1 + T2) * P2);
       const df RD = ld(a.fdh, a.fdl, fb + (4 + D) * P2),
                R1 = ld(a.fdh, a.fdl, fb + (4 + T1) * P2),
                R2 = ld(a.fdh, a.fdl, fb + (4 + T2) * P2);
       if constexpr (S == 1) {  // own cell is the lower one: outward = +n
-        dacc so = acc_first(LD.h, LD.l, q1.h, q1.l);
-        acc_mac(so, L1.h, L1.l, t1o.h, t1o.l);
-        acc_mac(so, L2.h, L2.l, t2o.h, t2o.l);
+        const df LD = ld(a.fdh, a.fdl, fb + (1 + D) * P2),
+                 L1 = ld(a.fdh, a.fdl, fb + (1 + T1) * P2),
+                 L2 = ld(a.fdh, a.fdl, fb + (1 + T2) * P2);
+        // and of the neighbour's trace
+        dacc s1n = acc_first(t.Dh[ta * P], t.Dl[ta * P],
+                             FSh[2 * P2 + P * tb], FSl[2 * P2 + P * tb]);
+        dacc s2n = acc_first(t.Dh[tb * P], t.Dl[tb * P], FSh[2 * P2 + ta],
+                             FSl[2 * P2 + ta]);
+        MFP_DF_LOOP
+        for (int j = 1; j < P; ++j) {
+          acc_mac(s1n, t.Dh[ta * P + j], t.Dl[ta * P + j],
+                  FSh[2 * P2 + j + P * tb], FSl[2 * P2 + j + P * tb]);
+          acc_mac(s2n, t.Dh[tb * P + j], t.Dl[tb * P + j],
+                  FSh[2 * P2 + ta + P * j], FSl[2 * P2 + ta + P * j]);
+        }
+        dacc sa = acc_first(LD.h, LD.l, so.h, so.l);
+        acc_mac(sa, L1.h, L1.l, t1o.h, t1o.l);
+        acc_mac(sa, L2.h, L2.l, t2o.h, t2o.l);
         const df t1n = acc_get(s1n), t2n = acc_get(s2n);
-        dacc sn = acc_first(RD.h, RD.l, q3.h, q3.l);
-        acc_mac(sn, R1.h, R1.l, t1n.h, t1n.l);
-        acc_mac(sn, R2.h, R2.l, t2n.h, t2n.l);
-        dno = acc_get(so);
-        dnn = bnd ? dno : acc_get(sn);
+        dacc sb = acc_first(RD.h, RD.l, q3.h, q3.l);
+        acc_mac(sb, R1.h, R1.l, t1n.h, t1n.l);
+        acc_mac(sb, R2.h, R2.l, t2n.h, t2n.l);
+        dno = acc_get(sa);
+        dnn = bnd ? dno : acc_get(sb);
         gvD = LD;
         go1 = L1;
         go2 = L2;
@@ -360,10 +374,10 @@ __device__ __forceinline__ void df_face_rt(const ApplyArgsDF& a, int col,
         gn1 = R1;
         gn2 = R2;
       } else {  // own cell is the upper one (boundary only): outward = -n
-        dacc so = acc_first(RD.h, RD.l, q1.h, q1.l);
-        acc_mac(so, R1.h, R1.l, t1o.h, t1o.l);
-        acc_mac(so, R2.h, R2.l, t2o.h, t2o.l);
-        dno = -acc_get(so);
+        dacc sa = acc_first(RD.h, RD.l, so.h, so.l);
+        acc_mac(sa, R1.h, R1.l, t1o.h, t1o.l);
+        acc_mac(sa, R2.h, R2.l, t2o.h, t2o.l);
+        dno = -acc_get(sa);
         dnn = dno;
         gvD = -RD;
         go1 = -R1;
@@ -390,92 +404,87 @@ __device__ __forceinline__ void df_face_rt(const ApplyArgsDF& a, int col,
   }
   // fold the tangential test slopes into the value parts (D^T at the face
   // points)
-  {
-    df vo = cv, vn = -cv;
-    if constexpr (CURVED) {
-      __syncthreads();
-      dacc so, sn;
-      so.h = cv.h;
-      so.l = cv.l;
-      sn.h = vn.h;
-      sn.l = vn.l;
-      MFP_DF_LOOP
-      for (int j = 0; j < P; ++j) {
-        acc_mac(so, t.Dh[j * P + ta], t.Dl[j * P + ta],
-                FSh[4 * P2 + j + P * tb], FSl[4 * P2 + j + P * tb]);
-        acc_mac(so, t.Dh[j * P + tb], t.Dl[j * P + tb],
-                FSh[5 * P2 + ta + P * j], FSl[5 * P2 + ta + P * j]);
-        if constexpr (S == 1) {
-          acc_mac(sn, t.Dh[j * P + ta], t.Dl[j * P + ta],
-                  FSh[6 * P2 + j + P * tb], FSl[6 * P2 + j + P * tb]);
-          acc_mac(sn, t.Dh[j * P + tb], t.Dl[j * P + tb],
-                  FSh[7 * P2 + ta + P * j], FSl[7 * P2 + ta + P * j]);
-        }
+  df vo = cv, vn = -cv;
+  if constexpr (CURVED) {
+    __syncthreads();
+    dacc sa, sb;
+    sa.h = cv.h;
+    sa.l = cv.l;
+    sb.h = vn.h;
+    sb.l = vn.l;
+    MFP_DF_LOOP
+    for (int j = 0; j < P; ++j) {
+      acc_mac(sa, t.Dh[j * P + ta], t.Dl[j * P + ta],
+              FSh[4 * P2 + j + P * tb], FSl[4 * P2 + j + P * tb]);
+      acc_mac(sa, t.Dh[j * P + tb], t.Dl[j * P + tb],
+              FSh[5 * P2 + ta + P * j], FSl[5 * P2 + ta + P * j]);
+      if constexpr (S == 1) {
+        acc_mac(sb, t.Dh[j * P + ta], t.Dl[j * P + ta],
+                FSh[6 * P2 + j + P * tb], FSl[6 * P2 + j + P * tb]);
+        acc_mac(sb, t.Dh[j * P + tb], t.Dl[j * P + tb],
+                FSh[7 * P2 + ta + P * j], FSl[7 * P2 + ta + P * j]);
       }
-      vo = acc_get(so);
-      vn = acc_get(sn);
     }
-    stv(FSh, FSl, 0 * P2 + ti, vo);
-    stv(FSh, FSl, 1 * P2 + ti, c0o);
-    if constexpr (S == 1) {
-      stv(FSh, FSl, 2 * P2 + ti, vn);
-      stv(FSh, FSl, 3 * P2 + ti, c0n);
-    }
+    vo = acc_get(sa);
+    vn = acc_get(sb);
   }
-  __syncthreads();
-  // S^T along a (FS[arr] -> FS[4+arr]), then along b (-> FS[arr])
-#pragma unroll 1
-  for (int arr = 0; arr < NA; ++arr) {
-    const float* ih = FSh + arr * P2 + P * tb;
-    const float* il = FSl + arr * P2 + P * tb;
-    dacc s = acc_first(t.Sh[ta], t.Sl[ta], ih[0], il[0]);
-#pragma unroll
-    for (int j = 1; j < P; ++j)
-      acc_mac(s, t.Sh[j * P + ta], t.Sl[j * P + ta], ih[j], il[j]);
-    stv(FSh, FSl, (4 + arr) * P2 + ti, acc_get(s));
-  }
-  __syncthreads();
-#pragma unroll 1
-  for (int arr = 0; arr < NA; ++arr) {
-    const float* ih = FSh + (4 + arr) * P2 + ta;
-    const float* il = FSl + (4 + arr) * P2 + ta;
-    dacc s = acc_first(t.Sh[tb], t.Sl[tb], ih[0], il[0]);
-#pragma unroll
-    for (int j = 1; j < P; ++j)
-      acc_mac(s, t.Sh[j * P + tb], t.Sl[j * P + tb], ih[P * j], il[P * j]);
-    stv(FSh, FSl, arr * P2 + ti, acc_get(s));
-  }
-  // distribution onto the nodes of line (ta, tb): own thread's values only
+  // own test terms onto the line of Gauss points along D
   if (own) {
-    const int i = n0 + lo * ls;
-    stv(Ah, Al, i, ld(Ah, Al, i) + ld(FSh, FSl, ti));
-    const df nf = ld(FSh, FSl, P2 + ti);
     MFP_DF_LOOP
     for (int l = 0; l < P; ++l) {
       const int j = n0 + l * ls;
-      stv(Ah, Al, j, ld(Ah, Al, j) + df_make(dSh[l], dSl[l]) * nf);
+      dacc s;
+      s.h = Ah[j];
+      s.l = Al[j];
+      acc_mac(s, gvh[l], gvl[l], vo.h, vo.l);
+      acc_mac(s, gdh[l], gdl[l], c0o.h, c0o.l);
+      stv(Ah, Al, j, acc_get(s));
     }
   }
+  // the neighbour's test terms to its face nodes: S^T along a, then b
   if constexpr (S == 1) {
+    stv(FSh, FSl, 0 * P2 + ti, vn);
+    stv(FSh, FSl, 1 * P2 + ti, c0n);
+    __syncthreads();
+#pragma unroll 1
+    for (int arr = 0; arr < 2; ++arr) {
+      const float* ih = FSh + arr * P2 + P * tb;
+      const float* il = FSl + arr * P2 + P * tb;
+      dacc s = acc_first(t.Sh[ta], t.Sl[ta], ih[0], il[0]);
+#pragma unroll
+      for (int j = 1; j < P; ++j)
+        acc_mac(s, t.Sh[j * P + ta], t.Sl[j * P + ta], ih[j], il[j]);
+      stv(FSh, FSl, (4 + arr) * P2 + ti, acc_get(s));
+    }
+    __syncthreads();
+    df res[2];
+#pragma unroll
+    for (int arr = 0; arr < 2; ++arr) {
+      const float* ih = FSh + (4 + arr) * P2 + ta;
+      const float* il = FSl + (4 + arr) * P2 + ta;
+      dacc s = acc_first(t.Sh[tb], t.Sl[tb], ih[0], il[0]);
+#pragma unroll
+      for (int j = 1; j < P; ++j)
+        acc_mac(s, t.Sh[j * P + tb], t.Sl[j * P + tb], ih[P * j], il[P * j]);
+      res[arr] = acc_get(s);
+    }
     if (pair) {
       float2* fbn = a.fb + ((size_t)nb * 6 + 2 * D) * P2 * a.stride + col;
-      fbn[(size_t)ti * a.stride] =
-          make_float2(FSh[2 * P2 + ti], FSl[2 * P2 + ti]);
-      fbn[(size_t)(P2 + ti) * a.stride] =
-          make_float2(FSh[3 * P2 + ti], FSl[3 * P2 + ti]);
+      fbn[(size_t)ti * a.stride] = make_float2(res[0].h, res[0].l);
+      fbn[(size_t)(P2 + ti) * a.stride] = make_float2(res[1].h, res[1].l);
     }
   }
 }
 
 template <int P, bool CURVED>
-__device__ __noinline__ void df_face_lower_rt(const ApplyArgsDF& a, int col,
+__device__ __noinline__ void df_face_lower_gp(const ApplyArgsDF& a, int col,
                                               int D, bool active, int cx,
                                               int cy, int cz, const float* Uh,
                                               const float* Ul, float* Ah,
                                               float* Al, float* FSh,
                                               float* FSl, const float* tabs,
                                               int ta, int tb) {
-  df_face_rt<P, CURVED, 0>(a, col, D, active, cx, cy, cz, Uh, Ul, Ah, Al, FSh,
+  df_face_gp<P, CURVED, 0>(a, col, D, active, cx, cy, cz, Uh, Ul, Ah, Al, FSh,
                            FSl, make_shdf<P>(tabs), ta, tb);
   __syncthreads();
 }
@@ -519,7 +528,7 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
   float* Xl = base + 3 * P3;
   float* Yh = base + 4 * P3;  // GY
   float* Yl = base + 5 * P3;
-  float* Uh = base + 6 * P3;  // DG nodal input
+  float* Uh = base + 6 * P3;  // DG: values at the Gauss points
   float* Ul = base + 7 * P3;
   float* FSh = base + 8 * P3;
   float* FSl = FSh + 8 * P2;
@@ -570,8 +579,6 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
         const df u = df_from_double(active ? a.src[gi * a.stride + col] : 0.0);
         rh[z] = u.h;
         rl[z] = u.l;
-        Uh[dx3<P>(ta, tb, z)] = u.h;
-        Ul[dx3<P>(ta, tb, z)] = u.l;
       }
     } else {
       const int X = cx * (P - 1) + ta, Y = cy * (P - 1) + tb;
@@ -597,6 +604,13 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
     dline<P>(Ah, Al, dx3<P>(0, ta, tb), 1, rh, rl);
     dsweep<P, DF_S, false, false>(rh, rl, Ah, Al, dx3<P>(0, ta, tb), 1);
     dline<P>(Ah, Al, dx3<P>(0, ta, tb), 1, rh, rl);  // own line
+    if constexpr (DG) {  // values at the Gauss points for the face terms
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        Uh[dx3<P>(j, ta, tb)] = rh[j];
+        Ul[dx3<P>(j, ta, tb)] = rl[j];
+      }
+    }
     dsweep<P, DF_D, false, false>(rh, rl, Xh, Xl, dx3<P>(0, ta, tb), 1);
     __syncthreads();
     // ---- reference gradient: y into GY, z kept in registers
@@ -667,6 +681,21 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
     __syncthreads();
     dline<P>(Xh, Xl, dx3<P>(0, ta, tb), 1, rh, rl);
     dsweep<P, DF_D, true, true>(rh, rl, Ah, Al, dx3<P>(0, ta, tb), 1);
+    if constexpr (DG) {
+      // ---- SIPG face terms (Eq. 6, Eq. 7), added at the Gauss points
+      __syncthreads();
+#pragma unroll 1
+      for (int D = 0; D < 3; ++D) {
+        // lower faces only where a cell of the block lies on the boundary
+        const int cD = D == 0 ? cx : (D == 1 ? cy : cz);
+        if (__syncthreads_or(active && cD == 0))
+          df_face_lower_gp<P, CURVED>(a, col, D, active, cx, cy, cz, Uh, Ul,
+                                      Ah, Al, FSh, FSl, tabs, ta, tb);
+        df_face_gp<P, CURVED, 1>(a, col, D, active, cx, cy, cz, Uh, Ul, Ah, Al,
+                                 FSh, FSl, t, ta, tb);
+      }
+      __syncthreads();
+    }
     dline<P>(Ah, Al, dx3<P>(0, ta, tb), 1, rh, rl);  // own line
     dsweep<P, DF_S, true, false>(rh, rl, Ah, Al, dx3<P>(0, ta, tb), 1);
     __syncthreads();
@@ -696,17 +725,6 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
       __syncthreads();
     } else {
       dsweep<P, DF_S, true, false>(rh, rl, Ah, Al, dx3<P>(ta, tb, 0), P2);
-      __syncthreads();
-#pragma unroll 1
-      for (int D = 0; D < 3; ++D) {
-        // lower faces only where a cell of the block lies on the boundary
-        const int cD = D == 0 ? cx : (D == 1 ? cy : cz);
-        if (__syncthreads_or(active && cD == 0))
-          df_face_lower_rt<P, CURVED>(a, col, D, active, cx, cy, cz, Uh, Ul,
-                                      Ah, Al, FSh, FSl, tabs, ta, tb);
-        df_face_rt<P, CURVED, 1>(a, col, D, active, cx, cy, cz, Uh, Ul, Ah, Al,
-                                 FSh, FSl, t, ta, tb);
-      }
       if (active) {
 #pragma unroll
         for (int z = 0; z < P; ++z) {
@@ -743,46 +761,41 @@ __global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
     const size_t cell = (size_t)row * a.n[0] + cx;
     const float2* fb = a.fb + cell * 6 * P2 * R + col;
     double* out = a.dst + (cell * P3 + xy) * R + col;
+    // every load first (one memory round trip); slots of boundary faces
+    // are read but not used
+    const float2 f0 = make_float2(0.f, 0.f);
+    double u[P];
+    float2 gx[P], vx[P], gy[P], vy[P];
+#pragma unroll
+    for (int z = 0; z < P; ++z) {
+      u[z] = out[(size_t)z * P2 * R];
+      gx[z] = fb[(size_t)(1 * P2 + y + P * z) * R];
+      vx[z] = x == 0 ? fb[(size_t)(0 * P2 + y + P * z) * R] : f0;
+      gy[z] = fb[(size_t)(3 * P2 + x + P * z) * R];
+      vy[z] = y == 0 ? fb[(size_t)(2 * P2 + x + P * z) * R] : f0;
+    }
+    const float2 gz = fb[(size_t)(5 * P2 + xy) * R];
+    const float2 vz = fb[(size_t)(4 * P2 + xy) * R];
+    // lower faces inside the mesh: the slope part on every layer along the
+    // face normal (weight dphi_l(0)), the value part on layer 0
+    const float wxh = d0h[x], wxl = d0l[x], wyh = d0h[y], wyl = d0l[y];
     dacc s[P];
 #pragma unroll
     for (int z = 0; z < P; ++z) {
-      const df u = df_from_double(out[(size_t)z * P2 * R]);
-      s[z].h = u.h;
-      s[z].l = u.l;
-    }
-    // lower faces inside the mesh: the slope part on every layer along the
-    // face normal (weight dphi_l(0)), the value part on layer 0
-    if (cx > 0) {
-      const df w = df_make(d0h[x], d0l[x]);
-#pragma unroll
-      for (int z = 0; z < P; ++z) {
-        const float2 g = fb[(size_t)(1 * P2 + y + P * z) * R];
-        acc_mac(s[z], w.h, w.l, g.x, g.y);
-        if (x == 0) {
-          const float2 v = fb[(size_t)(0 * P2 + y + P * z) * R];
-          acc_add(s[z], df_make(v.x, v.y));
-        }
+      const df uz = df_from_double(u[z]);
+      s[z].h = uz.h;
+      s[z].l = uz.l;
+      if (cx > 0) {
+        acc_mac(s[z], wxh, wxl, gx[z].x, gx[z].y);
+        if (x == 0) acc_add(s[z], df_make(vx[z].x, vx[z].y));
       }
-    }
-    if (cy > 0) {
-      const df w = df_make(d0h[y], d0l[y]);
-#pragma unroll
-      for (int z = 0; z < P; ++z) {
-        const float2 g = fb[(size_t)(3 * P2 + x + P * z) * R];
-        acc_mac(s[z], w.h, w.l, g.x, g.y);
-        if (y == 0) {
-          const float2 v = fb[(size_t)(2 * P2 + x + P * z) * R];
-          acc_add(s[z], df_make(v.x, v.y));
-        }
+      if (cy > 0) {
+        acc_mac(s[z], wyh, wyl, gy[z].x, gy[z].y);
+        if (y == 0) acc_add(s[z], df_make(vy[z].x, vy[z].y));
       }
-    }
-    if (cz > 0) {
-      const float2 g = fb[(size_t)(5 * P2 + xy) * R];
-      const float2 v = fb[(size_t)(4 * P2 + xy) * R];
-#pragma unroll
-      for (int z = 0; z < P; ++z) {
-        acc_mac(s[z], d0h[z], d0l[z], g.x, g.y);
-        if (z == 0) acc_add(s[z], df_make(v.x, v.y));
+      if (cz > 0) {
+        acc_mac(s[z], d0h[z], d0l[z], gz.x, gz.y);
+        if (z == 0) acc_add(s[z], df_make(vz.x, vz.y));
       }
     }
 #pragma unroll

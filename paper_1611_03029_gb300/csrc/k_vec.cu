@@ -303,10 +303,24 @@ __device__ void column_sums(double v, int R, double* part, double* sh) {
   }
 }
 
-__device__ double finish_sum(int c, int R, const double* part) {
+// Sum over the grid's blocks of the partials of each column, by the whole
+// last block: thread (c, g) adds the partials g, g + groups, ... in order,
+// then a fixed pairwise tree over g; the result is valid for threadIdx.x < R.
+__device__ double finish_sum(int R, const double* part, double* sh) {
+  const int groups = blockDim.x / R;
+  const int c = threadIdx.x % R, g = threadIdx.x / R;
   double s = 0;
-  for (int b = 0; b < gridDim.x; ++b) s += part[b * R + c];
-  return s;
+  if (g < groups)
+    for (int b = g; b < (int)gridDim.x; b += groups) s += part[b * R + c];
+  __syncthreads();
+  sh[threadIdx.x] = g < groups ? s : 0.0;
+  __syncthreads();
+  for (int w = 1; w < groups; w *= 2) {
+    if (g < groups && g % (2 * w) == 0 && g + w < groups)
+      sh[threadIdx.x] += sh[threadIdx.x + w * R];
+    __syncthreads();
+  }
+  return sh[c];
 }
 
 // dot(a, b) per column and finishing operation on the slot-major scalars
@@ -331,9 +345,9 @@ __global__ void k_dot(const double* __restrict__ a,
       v += a[row * R + c] * b[row * R + c];
   column_sums(g < groups ? v : 0.0, R, part, sh);
   if (!last_block(cnt)) return;
+  const double s = finish_sum(R, part, sh);
   if (threadIdx.x < R) {
     const int cc = threadIdx.x;
-    const double s = finish_sum(cc, R, part);
 #define ST(slot) scal[(slot) * R + cc]
     switch (op) {
       case 0:
@@ -389,8 +403,8 @@ __global__ void k_cg_update(double* __restrict__ x, double* __restrict__ r,
   }
   column_sums(g < groups ? v : 0.0, R, part, sh);
   if (!last_block(cnt)) return;
-  if (threadIdx.x < R)
-    scal[S_RN2 * R + threadIdx.x] = finish_sum(threadIdx.x, R, part);
+  const double s = finish_sum(R, part, sh);
+  if (threadIdx.x < R) scal[S_RN2 * R + threadIdx.x] = s;
   if (threadIdx.x == 0) *cnt = 0u;
 }
 

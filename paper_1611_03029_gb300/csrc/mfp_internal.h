@@ -39,6 +39,10 @@ struct DevTabDF {
   float Dh[kMaxP * kMaxP], Dl[kMaxP * kMaxP];
   float d0h[kMaxP], d0l[kMaxP], d1h[kMaxP], d1l[kMaxP];
   float wh[kMaxP], wl[kMaxP];
+  // Lagrange basis on the Gauss points: values l_q(0), l_q(1) and slopes
+  // l_q'(0), l_q'(1) at the ends of [0, 1] (traces from quadrature data)
+  float gv0h[kMaxP], gv0l[kMaxP], gv1h[kMaxP], gv1l[kMaxP];
+  float gd0h[kMaxP], gd0l[kMaxP], gd1h[kMaxP], gd1l[kMaxP];
 };
 
 struct HostTables {
