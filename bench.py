@@ -132,44 +132,34 @@ class ClockSampler:
 # algorithmic work of one operator application
 # ---------------------------------------------------------------------------
 def apply_flops(disc, k, ncells, curved):
-    """Floating-point operations of one apply, counted from the algorithm:
-    12 sum-factorization sweeps of p^4 FMAs per cell, the quadrature-point
-    operation (21 flops curved, 5 Cartesian) and, for SIPG, the face work
-    (per face and side 15 p^3 FMAs Cartesian / 21 p^3 curved)."""
+    """Floating-point operations of one apply, counted from the algorithm
+    (FMA = 2): 12 sum-factorization sweeps of p^4 FMAs per cell, the
+    quadrature-point operation (21 flops curved, 5 Cartesian), the two
+    transposed accumulations and, for SIPG, each face once (3 per cell):
+    per side the normal slope on the nodes (p^3 FMAs), the interpolation of
+    value and slope to the face points (4 p^3), their transposes (4 p^3) and
+    the normal-slope test distribution (p^3), plus for curved cells the
+    tangential slopes and their fold (4 p^3); the flux arithmetic is 20
+    flops per face point (40 curved)."""
     p = k + 1
     cell = 2 * 12 * p ** 4 + (21 if curved else 5) * p ** 3 + 2 * p ** 3
     if disc == "dg":
-        cell += 6 * 2 * (21 if curved else 15) * p ** 3
+        side = (14 if curved else 10) * p ** 3
+        face = 2 * 2 * side + (40 if curved else 20) * p * p
+        cell += 3 * face
     return float(cell) * ncells
 
 
-def df_dot(n):
-    """FP32-pipe flops of one double-float dot product of length n: first
-    product 7 (FMUL + 3 FFMA), each further term 14 (FMUL, 3 FFMA, 7 FADD),
-    final TwoSum 6."""
-    return 14 * n - 1
+# One float64 multiply-add (2 flops) is one double-float multiply-accumulate
+# on the FP32 pipe: FMUL + 3 FFMA + 8 FADD/FSUB = 14 flops (FFMA = 2).
+DF_FLOPS_PER_FP64_FLOP = 7
 
 
 def apply_flops_df(disc, k, ncells, curved):
-    """FP32-pipe flops (FFMA = 2) of one double-float apply, counted from the
-    kernel's double-float operations: 12 sweeps of p^2 lines x p dots of
-    length p per cell, the quadrature-point operation, the two transposed
-    accumulations and, for SIPG, per face point 18 dots of length p (both
-    sides' normal slopes, interpolation of four traces, tangential slopes
-    when curved, two transposed interpolations), the flux arithmetic, the
-    curved fold and the distribution onto the own nodes."""
-    p = k + 1
-    dadd, dmul = 11, 10
-    cell = 12 * p ** 3 * df_dot(p) + 2 * p ** 3 * dadd
-    cell += p ** 3 * (3 * df_dot(3) if curved else 6 * dmul)
-    if disc == "dg":
-        dots = (18 if curved else 14) * df_dot(p)
-        flux = 6 * dmul + 3 * dadd + 4 + (3 * dmul + 2 * df_dot(3) if curved
-                                          else 5 * dmul)
-        fold = 28 * p if curved else 0
-        dist = dadd + p * (dmul + dadd)
-        cell += 6 * p * p * (dots + flux + fold + dist)
-    return float(cell) * ncells
+    """Algorithmic FP32-pipe work of one double-float apply: the method's
+    float64 flops (apply_flops) at 14 FP32-pipe flops per multiply-add.
+    It does not depend on how the kernel organizes the work."""
+    return DF_FLOPS_PER_FP64_FLOP * apply_flops(disc, k, ncells, curved)
 
 
 def apply_bytes(disc, k, n, curved, word=8):
@@ -427,7 +417,8 @@ def run_ours(args):
             "frac": ach / FP32_PEAK_TFLOPS,
             "traffic": TRAFFIC.get(kernel_hash()),
             "algorithmic_bytes": apply_bytes("dg", DEGREE, n, True),
-            "work": "FP32-pipe flops of the double-float operations "
+            "work": "the method's float64 flops (bench.apply_flops) at 14 "
+                    "FP32-pipe flops per double-float multiply-add "
                     "(bench.apply_flops_df)",
             "fp64_equivalent_TFLOP_s": dom["GFLOP_s"] / 1e3,
             "fp64_pipe_peak": FP64_PEAK_TFLOPS,

@@ -143,6 +143,30 @@ const HostTables& host_tables() {
         split(d.dphi1[i], t.d1h[i], t.d1l[i]);
         split(d.w[i], t.wh[i], t.wl[i]);
       }
+      // even-odd split of S, D and their transposes
+      {
+        const int p = k + 1, h = p / 2, mc = h + p % 2;
+        DevTabEO& e = tabs.eo[k - 1];
+        for (int w = 0; w < 4; ++w) {
+          const double* M = (w / 2) ? d.D : d.S;
+          const bool tr = w % 2;
+          auto m = [&](int q, int j) {
+            return tr ? M[j * p + q] : M[q * p + j];
+          };
+          for (int i = 0; i < kMaxH * kMaxH; ++i)
+            e.ah[w][i] = e.al[w][i] = e.bh[w][i] = e.bl[w][i] = 0.f;
+          for (int q = 0; q < mc; ++q) {
+            for (int j = 0; j < h; ++j) {
+              split(0.5 * (m(q, j) + m(q, p - 1 - j)), e.ah[w][q * kMaxH + j],
+                    e.al[w][q * kMaxH + j]);
+              split(0.5 * (m(q, j) - m(q, p - 1 - j)), e.bh[w][q * kMaxH + j],
+                    e.bl[w][q * kMaxH + j]);
+            }
+            if (p % 2)
+              split(m(q, h), e.ah[w][q * kMaxH + h], e.al[w][q * kMaxH + h]);
+          }
+        }
+      }
       // Gauss-point Lagrange basis at the ends of [0, 1], in long double
       {
         const int p = k + 1;

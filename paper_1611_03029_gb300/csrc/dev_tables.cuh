@@ -10,8 +10,14 @@
 namespace mfp {
 namespace {
 
+// The double-float kernels' TUs (MFP_DF_TABLES) hold the double-float and
+// even-odd tables only: every TU has 64 KB of constant memory.
+#ifndef MFP_DF_TABLES
 __constant__ DevTab<double> c_tab64[8];
 __constant__ DevTab<float> c_tab32[8];
+#else
+__constant__ DevTabEO c_tabeo[8];
+#endif
 __constant__ DevTabDF c_tabdf[8];
 
 // Uploads the tables to the current device once per device per TU.
@@ -23,12 +29,17 @@ inline void ensure_tables() {
   std::lock_guard<std::mutex> lk(mu);
   if (dev < 64 && done[dev]) return;
   const HostTables& h = host_tables();
+#ifndef MFP_DF_TABLES
   MFP_CHECK_CUDA(cudaMemcpyToSymbol(c_tab64, h.d, sizeof(h.d)));
   MFP_CHECK_CUDA(cudaMemcpyToSymbol(c_tab32, h.f, sizeof(h.f)));
+#else
+  MFP_CHECK_CUDA(cudaMemcpyToSymbol(c_tabeo, h.eo, sizeof(h.eo)));
+#endif
   MFP_CHECK_CUDA(cudaMemcpyToSymbol(c_tabdf, h.df, sizeof(h.df)));
   if (dev < 64) done[dev] = true;
 }
 
+#ifndef MFP_DF_TABLES
 // Table selectors (P = k+1; W picks the table).  With compile-time indices
 // these become constant-bank operands.
 enum TabId { T_S, T_D, T_DPHI, T_E0, T_E1, T_DPHI0, T_DPHI1, T_W, T_G, T_X };
@@ -105,6 +116,8 @@ __device__ __forceinline__ void load_tables_shared(T* sS, T* sD, T* sDphi,
     }
   }
 }
+
+#endif  // MFP_DF_TABLES
 
 // Dispatch a functor templated on P = k+1 (k in 1..8).
 template <typename F>

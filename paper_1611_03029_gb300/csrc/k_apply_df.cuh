@@ -9,6 +9,7 @@
 // conversions of the float64 inputs and outputs use the FP64 pipe.
 #pragma once
 
+#define MFP_DF_TABLES
 #include "dev_tables.cuh"
 #include "df.cuh"
 
@@ -105,25 +106,97 @@ __device__ __forceinline__ void dmtv(const float (&ih)[P],
 #define MFP_DF_LOOP _Pragma("unroll")
 #endif
 
+// Even-odd split of the sweeps (p >= 4, MFP_DF_EO): the mirror symmetry of
+// S and D (tables c_tabeo) halves the multiply-adds of each sweep for the
+// price of 2 p double-float additions.
+#ifndef MFP_DF_EO
+#define MFP_DF_EO 1
+#endif
+
 // o[base + q * st] (+)= sum_j M[q][j] in[j]  (TR: M[j][q]), q = 0..P-1
 template <int P, int W, bool TR, bool ADD>
 __device__ __forceinline__ void dsweep(const float (&ih)[P],
                                        const float (&il)[P], float* oh,
                                        float* ol, int base, int st) {
-  MFP_DF_LOOP
-  for (int q = 0; q < P; ++q) {
-    const int i0 = TR ? q : q * P;
-    constexpr int js = TR ? P : 1;
-    dacc s = acc_first(tdh<P, W>(i0), tdl<P, W>(i0), ih[0], il[0]);
+  if constexpr (P >= 4 && MFP_DF_EO) {
+    constexpr int H = P / 2, MC = H + P % 2;
+    constexpr int w = 2 * (W == DF_D ? 1 : 0) + (TR ? 1 : 0);
+    const DevTabEO& E = c_tabeo[P - 2];
+    float eh[MC], el[MC], odh[H], odl[H];
 #pragma unroll
-    for (int j = 1; j < P; ++j)
-      acc_mac(s, tdh<P, W>(i0 + j * js), tdl<P, W>(i0 + j * js), ih[j],
-              il[j]);
-    df r = acc_get(s);
-    const int o = base + q * st;
-    if constexpr (ADD) r = df_make(oh[o], ol[o]) + r;
-    oh[o] = r.h;
-    ol[o] = r.l;
+    for (int j = 0; j < H; ++j) {
+      const df xa = df_make(ih[j], il[j]);
+      const df xb = df_make(ih[P - 1 - j], il[P - 1 - j]);
+      const df e = xa + xb, o = xa - xb;
+      eh[j] = e.h;
+      el[j] = e.l;
+      odh[j] = o.h;
+      odl[j] = o.l;
+    }
+    if constexpr (P % 2 == 1) {
+      eh[H] = ih[H];
+      el[H] = il[H];
+    }
+    MFP_DF_LOOP
+    for (int q = 0; q < H; ++q) {
+      const int r = q * kMaxH;
+      dacc sa = acc_first(E.ah[w][r], E.al[w][r], eh[0], el[0]);
+#pragma unroll
+      for (int j = 1; j < MC; ++j)
+        acc_mac(sa, E.ah[w][r + j], E.al[w][r + j], eh[j], el[j]);
+      dacc sb = acc_first(E.bh[w][r], E.bl[w][r], odh[0], odl[0]);
+#pragma unroll
+      for (int j = 1; j < H; ++j)
+        acc_mac(sb, E.bh[w][r + j], E.bl[w][r + j], odh[j], odl[j]);
+      const df A = acc_get(sa), B = acc_get(sb);
+      df r1 = A + B, r2 = A - B;
+      if constexpr (W == DF_D) r2 = -r2;
+      const int o1 = base + q * st, o2 = base + (P - 1 - q) * st;
+      if constexpr (ADD) {
+        r1 = df_make(oh[o1], ol[o1]) + r1;
+        r2 = df_make(oh[o2], ol[o2]) + r2;
+      }
+      oh[o1] = r1.h;
+      ol[o1] = r1.l;
+      oh[o2] = r2.h;
+      ol[o2] = r2.l;
+    }
+    if constexpr (P % 2 == 1) {  // middle row: A (S) or B (D) only
+      constexpr int r = H * kMaxH;
+      dacc sm;
+      if constexpr (W == DF_S) {
+        sm = acc_first(E.ah[w][r], E.al[w][r], eh[0], el[0]);
+#pragma unroll
+        for (int j = 1; j < MC; ++j)
+          acc_mac(sm, E.ah[w][r + j], E.al[w][r + j], eh[j], el[j]);
+      } else {
+        sm = acc_first(E.bh[w][r], E.bl[w][r], odh[0], odl[0]);
+#pragma unroll
+        for (int j = 1; j < H; ++j)
+          acc_mac(sm, E.bh[w][r + j], E.bl[w][r + j], odh[j], odl[j]);
+      }
+      df rm = acc_get(sm);
+      const int o = base + H * st;
+      if constexpr (ADD) rm = df_make(oh[o], ol[o]) + rm;
+      oh[o] = rm.h;
+      ol[o] = rm.l;
+    }
+  } else {
+    MFP_DF_LOOP
+    for (int q = 0; q < P; ++q) {
+      const int i0 = TR ? q : q * P;
+      constexpr int js = TR ? P : 1;
+      dacc s = acc_first(tdh<P, W>(i0), tdl<P, W>(i0), ih[0], il[0]);
+#pragma unroll
+      for (int j = 1; j < P; ++j)
+        acc_mac(s, tdh<P, W>(i0 + j * js), tdl<P, W>(i0 + j * js), ih[j],
+                il[j]);
+      df r = acc_get(s);
+      const int o = base + q * st;
+      if constexpr (ADD) r = df_make(oh[o], ol[o]) + r;
+      oh[o] = r.h;
+      ol[o] = r.l;
+    }
   }
 }
 

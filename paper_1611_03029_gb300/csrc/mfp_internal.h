@@ -45,10 +45,28 @@ struct DevTabDF {
   float gd0h[kMaxP], gd0l[kMaxP], gd1h[kMaxP], gd1l[kMaxP];
 };
 
+// Even-odd split of the double-float 1D sweeps (DF kernels only).  The
+// matrices M = S, D and their transposes satisfy M[p-1-q][p-1-j] = s M[q][j]
+// (s = +1 for S, -1 for D: GLL nodes and Gauss points are symmetric), so
+// with h = p/2, e_j = x_j + x_{p-1-j}, o_j = x_j - x_{p-1-j} (j < h) and,
+// for odd p, e_h = x_h:
+//   A_q = sum_j a[q][j] e_j,  B_q = sum_{j<h} b[q][j] o_j,
+//   (M x)_q = A_q + B_q,  (M x)_{p-1-q} = s (A_q - B_q)   (q < h),
+// with a[q][j] = (M[q][j] + M[q][p-1-j]) / 2, b = the difference / 2,
+// a[q][h] = M[q][h]; the middle row of an odd p needs A (S) or B (D) only.
+// Index w = 2 W + TR (W: 0 = S, 1 = D; TR: transposed), rows and columns
+// up to kMaxH.
+constexpr int kMaxH = 5;
+struct DevTabEO {
+  float ah[4][kMaxH * kMaxH], al[4][kMaxH * kMaxH];
+  float bh[4][kMaxH * kMaxH], bl[4][kMaxH * kMaxH];
+};
+
 struct HostTables {
   DevTab<double> d[8];  // index k-1
   DevTab<float> f[8];
   DevTabDF df[8];
+  DevTabEO eo[8];
 };
 const HostTables& host_tables();
 
