@@ -66,13 +66,11 @@ int level_index(const mfp_ctx* c, const Level& L) {
 
 void drop_graphs(mfp_ctx* c);
 
-// Face buffer of the float64 SIPG apply in double-float arithmetic, grown
-// to R columns (never while a stream is being captured: the V-cycle's
-// levels are grown by ensure_scratch before the capture).
+// Face buffer of the SIPG applies (8 bytes per entry: a float, a float64
+// or a double-float pair), grown to R columns (never while a stream is being
+// captured: the V-cycle's levels are grown by ensure_scratch before it).
 void ensure_fbuf(mfp_ctx* c, Level& L, int R, cudaStream_t s) {
-  if (L.disc != MFP_SIPG || c->desc.fp64_arith != MFP_ARITH_DF ||
-      L.fbuf_rhs >= R)
-    return;
+  if (L.disc != MFP_SIPG || L.fbuf_rhs >= R) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (s) MFP_CHECK_CUDA(cudaStreamIsCapturing(s, &cs));
   MFP_REQUIRE(cs == cudaStreamCaptureStatusNone,
@@ -93,6 +91,7 @@ void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
   if (L.disc == MFP_CG)
     MFP_CHECK_CUDA(
         cudaMemsetAsync(dst, 0, (size_t)L.ndofs * R * sizeof(T), s));
+  ensure_fbuf(c, L, R, s);
   const int prec = sizeof(T) == 8 ? MFP_FP64 : MFP_FP32;
   const int cells = cells_for(c, level_index(c, L), prec, R);
   if constexpr (sizeof(T) == 8) {
@@ -100,7 +99,6 @@ void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
       const double* sd = reinterpret_cast<const double*>(src);
       double* dd = reinterpret_cast<double*>(dst);
       bool ok;
-      ensure_fbuf(c, L, R, s);
       if (L.disc == MFP_CG)
         ok = apply_cg_df_lo(L, sd, dd, R, cells, s) ||
              apply_cg_df_hi(L, sd, dd, R, cells, s);
@@ -204,11 +202,7 @@ void ensure_scratch(mfp_ctx* c, int R) {
     MFP_CHECK_CUDA(cudaMalloc(&L.t_b, bytes));
     L.scratch_rhs = R;
   }
-  // float64 applies: the outer CG's on the finest level, every level's in a
-  // float64 V-cycle
-  for (size_t l = 0; l < c->levels.size(); ++l)
-    if (c->vprec == MFP_FP64 || l + 1 == c->levels.size())
-      ensure_fbuf(c, c->levels[l], R, nullptr);
+  for (auto& L : c->levels) ensure_fbuf(c, L, R, nullptr);
   if (c->cg_rhs < R) {
     const int64_t n = c->levels.back().ndofs * (int64_t)R;
     dfree(c->cg_r);

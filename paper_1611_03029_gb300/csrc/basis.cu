@@ -117,6 +117,13 @@ void fill(DevTab<T>& t, int k) {
     t.dphi0[j] = (T)lagrange_deriv(xl, p, j, 0.0L);
     t.dphi1[j] = (T)lagrange_deriv(xl, p, j, 1.0L);
   }
+  for (int i = 0; i < kMaxP; ++i) t.gv0[i] = t.gv1[i] = t.gd0[i] = t.gd1[i] = 0;
+  for (int q = 0; q < p; ++q) {
+    t.gv0[q] = (T)lagrange(xg, p, q, 0.0L);
+    t.gv1[q] = (T)lagrange(xg, p, q, 1.0L);
+    t.gd0[q] = (T)lagrange_deriv(xg, p, q, 0.0L);
+    t.gd1[q] = (T)lagrange_deriv(xg, p, q, 1.0L);
+  }
 }
 
 }  // namespace
@@ -167,21 +174,12 @@ const HostTables& host_tables() {
           }
         }
       }
-      // Gauss-point Lagrange basis at the ends of [0, 1], in long double
-      {
-        const int p = k + 1;
-        ld xg[kMaxP], wg[kMaxP];
-        gauss(p, xg, wg);
-        for (int i = 0; i < p; ++i) xg[i] = (xg[i] + 1) / 2;
-        for (int q = 0; q < p; ++q) {
-          split((double)lagrange(xg, p, q, 0.0L), t.gv0h[q], t.gv0l[q]);
-          split((double)lagrange(xg, p, q, 1.0L), t.gv1h[q], t.gv1l[q]);
-          split((double)lagrange_deriv(xg, p, q, 0.0L), t.gd0h[q], t.gd0l[q]);
-          split((double)lagrange_deriv(xg, p, q, 1.0L), t.gd1h[q], t.gd1l[q]);
-        }
-        for (int q = p; q < kMaxP; ++q)
-          t.gv0h[q] = t.gv0l[q] = t.gv1h[q] = t.gv1l[q] = t.gd0h[q] =
-              t.gd0l[q] = t.gd1h[q] = t.gd1l[q] = 0.f;
+      // Gauss-point Lagrange basis at the ends of [0, 1]
+      for (int q = 0; q < kMaxP; ++q) {
+        split(d.gv0[q], t.gv0h[q], t.gv0l[q]);
+        split(d.gv1[q], t.gv1h[q], t.gv1l[q]);
+        split(d.gd0[q], t.gd0h[q], t.gd0l[q]);
+        split(d.gd1[q], t.gd1h[q], t.gd1l[q]);
       }
     }
   });

@@ -11,14 +11,15 @@ namespace mfp {
 namespace {
 
 // The double-float kernels' TUs (MFP_DF_TABLES) hold the double-float and
-// even-odd tables only: every TU has 64 KB of constant memory.
+// even-odd tables, the others the float64 and float ones: every TU has 64 KB
+// of constant memory.
 #ifndef MFP_DF_TABLES
 __constant__ DevTab<double> c_tab64[8];
 __constant__ DevTab<float> c_tab32[8];
 #else
 __constant__ DevTabEO c_tabeo[8];
-#endif
 __constant__ DevTabDF c_tabdf[8];
+#endif
 
 // Uploads the tables to the current device once per device per TU.
 inline void ensure_tables() {
@@ -34,15 +35,18 @@ inline void ensure_tables() {
   MFP_CHECK_CUDA(cudaMemcpyToSymbol(c_tab32, h.f, sizeof(h.f)));
 #else
   MFP_CHECK_CUDA(cudaMemcpyToSymbol(c_tabeo, h.eo, sizeof(h.eo)));
-#endif
   MFP_CHECK_CUDA(cudaMemcpyToSymbol(c_tabdf, h.df, sizeof(h.df)));
+#endif
   if (dev < 64) done[dev] = true;
 }
 
 #ifndef MFP_DF_TABLES
 // Table selectors (P = k+1; W picks the table).  With compile-time indices
 // these become constant-bank operands.
-enum TabId { T_S, T_D, T_DPHI, T_E0, T_E1, T_DPHI0, T_DPHI1, T_W, T_G, T_X };
+enum TabId {
+  T_S, T_D, T_DPHI, T_E0, T_E1, T_DPHI0, T_DPHI1, T_W, T_G, T_X,
+  T_GV0, T_GV1, T_GD0, T_GD1
+};
 
 template <typename T, int P, int W>
 __device__ __forceinline__ T tv(int i) {
@@ -61,6 +65,10 @@ __device__ __forceinline__ T tv(int i) {
   if constexpr (W == T_W) return t->w[i];
   if constexpr (W == T_G) return t->g[i];
   if constexpr (W == T_X) return t->x[i];
+  if constexpr (W == T_GV0) return t->gv0[i];
+  if constexpr (W == T_GV1) return t->gv1[i];
+  if constexpr (W == T_GD0) return t->gd0[i];
+  if constexpr (W == T_GD1) return t->gd1[i];
   return T(0);
 }
 

@@ -10,9 +10,9 @@
 //   points -> t_q = G_q grad u_q (kappa, w, det J, J^{-1} J^{-T}) ->
 //   D^T (z, y, x) -> S^T (x, y, z) -> scatter.
 // CG scatters with atomics into the node grid (boundary rows are identity);
-// SIPG adds the six face integrals of its own test functions (each interior
-// face is evaluated once from either side, with that side's outward normal;
-// Eq. 6 visits each face twice in the same way) and stores its block.
+// SIPG adds the face integrals at the Gauss points before the S^T sweeps:
+// the cell below each interior face evaluates it for both sides and leaves
+// the upper neighbour's share in a face buffer that k_dg_face_add_t adds.
 #pragma once
 
 #include "dev_tables.cuh"
@@ -33,6 +33,7 @@ struct ApplyArgs {
   const T* __restrict__ kface;  // [face][p^2] or null
   const T* __restrict__ fdata;  // curved SIPG: [face][7][p^2]
   const T* __restrict__ sigma;  // curved SIPG: [face]
+  T* fb;                        // SIPG face buffer [cell][6][p^2] x columns
   T kappa;
   T gs[3];  // Cartesian: |K| / h_d^2
   T ns[3];  // Cartesian: 1 / h_d
@@ -49,14 +50,6 @@ __device__ __forceinline__ int idx3(int x, int y, int z) {
   return x + P * (y + P * z);
 }
 
-// node (layer l along axis D, tangential coordinates a < b)
-template <int P, int D>
-__device__ __forceinline__ int fnode(int l, int a, int b) {
-  if constexpr (D == 0) return l + P * (a + P * b);
-  if constexpr (D == 1) return a + P * (l + P * b);
-  return a + P * (b + P * l);
-}
-
 // Shared-memory stride of one virtual cell, odd so that the columns of a
 // batch (adjacent threads, one virtual cell each) fall into distinct banks.
 template <typename T, int P, bool DG>
@@ -68,376 +61,268 @@ __host__ __device__ constexpr int table_smem_elems() {
   return 3 * P * P + 3 * P;
 }
 
-// One line of a p x p face array: Y[line] = M X[line] (or M^T) along the
-// first (DIR 0, index q + p c) or second (DIR 1, index c + p q) tangential
-// axis; the 1D matrix is a constant-bank operand.
-template <int P, typename T, int W, bool TRANS, int DIR>
-__device__ __forceinline__ void face_line(const T* X, T* Y, int c) {
-  T in[P], out[P];
-#pragma unroll
-  for (int j = 0; j < P; ++j) in[j] = X[DIR == 0 ? j + P * c : c + P * j];
-  if constexpr (TRANS)
-    mtv<T, P, W>(in, out);
-  else
-    mv<T, P, W>(in, out);
-#pragma unroll
-  for (int q = 0; q < P; ++q) Y[DIR == 0 ? q + P * c : c + P * q] = out[q];
-}
-
-// Face terms of SIPG (Eq. 6, mirror states Eq. 7) for one face of the own
-// cell, in three parts: the trace gather and the final scatter depend on the
-// face (axis D, side S: 0 lower, 1 upper) and are instantiated for each; the
-// interpolation to the face Gauss points, the flux and the transposed
-// interpolation are face-independent and exist once (the six faces run in a
-// loop, which keeps the kernel's code within the instruction cache).
-// Per-point parts use thread (ta, tb) for face point / node line (ta, tb);
-// interpolations are line sweeps, one line per thread.  FS: 8 p^2 arrays.
-template <int P, typename T, int D, int S>
-__device__ __forceinline__ void face_gather(const ApplyArgs<T>& a, bool active,
-                                            int nb, bool bnd, const T* U,
-                                            T* FS, int ta, int tb) {
+// One face of the own cell (axis D a runtime value), SIPG (Eq. 6, mirror
+// states Eq. 7).  The own side works on the cell's values at its Gauss
+// points U: its trace and reference normal slope at face point (ta, tb)
+// come from the line of U along D through it (Lagrange basis of the Gauss
+// points at the cell end, exact for the degree-k polynomial), and its test
+// terms go back onto the same line of the Gauss-point accumulator Aq ahead
+// of the cell's S^T sweeps.  Each interior face is evaluated once, by the
+// cell below it (S = 1): the upper neighbour's trace comes from its nodal
+// values (face layer and normal slope, then S x S to the face points, one
+// point per thread with the table rows in registers), and its test terms
+// go through S^T x S^T to its face nodes and into the face buffer fb (slot
+// 2D: value part, 2D + 1: normal-slope part) for k_dg_face_add_t.  A
+// boundary face is one-sided; an interior lower face (S = 0) adds nothing.
+template <int P, typename T, bool CURVED, int S>
+__device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
+                                        bool active, int cx, int cy, int cz,
+                                        const T* U, T* Aq, T* FS, const T* sS,
+                                        const T* sD, const T* sw, int ta,
+                                        int tb) {
   constexpr int P2 = P * P, P3 = P2 * P;
-  constexpr int SLO = S ? T_DPHI1 : T_DPHI0;  // own slope table
-  constexpr int SLN = S ? T_DPHI0 : T_DPHI1;  // neighbour slope table
-  constexpr int lo = S ? P - 1 : 0;
-  constexpr int ln = S ? 0 : P - 1;
+  constexpr int GV = S ? T_GV1 : T_GV0;
+  constexpr int GD = S ? T_GD1 : T_GD0;
   const int t = ta + P * tb;
-  T vo = U[fnode<P, D>(lo, ta, tb)];
-  T dno = T(0);
+  // point (l, ta, tb) of the own line normal to D is n0 + l * ls
+  const int ls = D == 0 ? 1 : (D == 1 ? P : P2);
+  const int n0 = D == 0 ? P * t : (D == 1 ? ta + P2 * tb : t);
+  const int cD = D == 0 ? cx : (D == 1 ? cy : cz);
+  const int f = a.face_off[D] + cx + (D == 0 ? S : 0) +
+                (a.n[0] + (D == 0)) *
+                    (cy + (D == 1 ? S : 0) +
+                     (a.n[1] + (D == 1)) * (cz + (D == 2 ? S : 0)));
+  const bool bnd = S ? cD + 1 >= a.n[D] : cD == 0;
+  const bool own = S == 1 || bnd;
+  const bool pair = S == 1 && !bnd && active;
+  const int nb = pair ? cx + a.n[0] * (cy + a.n[1] * cz) +
+                            (D == 0 ? 1 : (D == 1 ? a.n[0] : a.n[0] * a.n[1]))
+                      : 0;
+  // own trace and reference normal slope at the face point (ta, tb)
+  T uo = T(0), so = T(0);
 #pragma unroll
-  for (int l = 0; l < P; ++l)
-    dno = fma(tv<T, P, SLO>(l), U[fnode<P, D>(l, ta, tb)], dno);
-  T vn = T(0), dnn = T(0);
-  if (!bnd && active) {
-    const size_t cb = (size_t)nb * P3;
-#pragma unroll
-    for (int l = 0; l < P; ++l) {
-      const T u = a.src[(cb + fnode<P, D>(l, ta, tb)) * a.stride + a.col];
-      dnn = fma(tv<T, P, SLN>(l), u, dnn);
-      if (l == ln) vn = u;
-    }
+  for (int l = 0; l < P; ++l) {
+    const T u = U[n0 + l * ls];
+    uo = fma(tv<T, P, GV>(l), u, uo);
+    so = fma(tv<T, P, GD>(l), u, so);
   }
-  FS[0 * P2 + t] = vo;
-  FS[1 * P2 + t] = dno;
-  FS[2 * P2 + t] = vn;
-  FS[3 * P2 + t] = dnn;
-}
-
-template <int P, typename T, int D, int S>
-__device__ __forceinline__ void face_scatter(T* Aq, const T* FS, int ta,
-                                             int tb) {
-  constexpr int P2 = P * P;
-  constexpr int SLO = S ? T_DPHI1 : T_DPHI0;
-  constexpr int lo = S ? P - 1 : 0;
-  const int t = ta + P * tb;
-  const T vf = FS[0 * P2 + t], nf = FS[1 * P2 + t];
-  Aq[fnode<P, D>(lo, ta, tb)] += vf;
+  if constexpr (CURVED) FS[0 * P2 + t] = uo;
+  T un = T(0), q3 = T(0);
+  if constexpr (S == 1) {
+    // the upper neighbour's face layer and normal slope (nodal), then
+    // interpolated to the face points
+    T vn = T(0), dnn = T(0);
+    if (pair) {
+      const T* u0 = a.src + ((size_t)nb * P3 + n0) * a.stride + col;
+      const size_t lstr = (size_t)ls * a.stride;
 #pragma unroll
-  for (int l = 0; l < P; ++l)
-    Aq[fnode<P, D>(l, ta, tb)] += tv<T, P, SLO>(l) * nf;
-}
-
-// FS[0..3] = own value, own reference normal slope, neighbour value,
-// neighbour slope at the face nodes  ->  FS[0] = value part, FS[1] =
-// normal-slope part of the own test functions at the face nodes.
-template <int P, typename T, bool CURVED>
-__device__ __forceinline__ void face_core(const ApplyArgs<T>& a, int D, int S,
-                                          int f, bool bnd, T* FS, const T* sw,
-                                          int ta, int tb) {
-  constexpr int P2 = P * P;
-  const int t = ta + P * tb;
-  for (int it = t; it < 4 * P; it += P2)
-    face_line<P, T, T_S, false, 0>(FS + (it / P) * P2, FS + (4 + it / P) * P2,
-                                   it % P);
-  __syncthreads();
-  for (int it = t; it < 4 * P; it += P2)
-    face_line<P, T, T_S, false, 1>(FS + (4 + it / P) * P2, FS + (it / P) * P2,
-                                   it % P);
-  __syncthreads();
-  if constexpr (CURVED) {  // tangential slopes of both traces
-    for (int it = t; it < 4 * P; it += P2) {
-      const int k = it / P;  // 0: d_a u-, 1: d_b u-, 2: d_a u+, 3: d_b u+
-      const T* src = FS + (k < 2 ? 0 : 2) * P2;
-      if (k & 1)
-        face_line<P, T, T_D, false, 1>(src, FS + (4 + k) * P2, it % P);
-      else
-        face_line<P, T, T_D, false, 0>(src, FS + (4 + k) * P2, it % P);
+      for (int l = 0; l < P; ++l) {
+        const T u = u0[l * lstr];
+        dnn = fma(tv<T, P, T_DPHI0>(l), u, dnn);
+        if (l == 0) vn = u;
+      }
     }
+    FS[2 * P2 + t] = vn;
+    FS[3 * P2 + t] = dnn;
     __syncthreads();
+    T ra[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) ra[j] = sS[ta * P + j];
+    T s2 = T(0), s3 = T(0);
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      s2 = fma(ra[j], FS[2 * P2 + j + P * tb], s2);
+      s3 = fma(ra[j], FS[3 * P2 + j + P * tb], s3);
+    }
+    FS[6 * P2 + t] = s2;
+    FS[7 * P2 + t] = s3;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < P; ++j) ra[j] = sS[tb * P + j];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      un = fma(ra[j], FS[6 * P2 + ta + P * j], un);
+      q3 = fma(ra[j], FS[7 * P2 + ta + P * j], q3);
+    }
+    if constexpr (CURVED) FS[2 * P2 + t] = un;
   }
-  // flux at face quadrature point (ta, tb)
-  T cv, c0, c1 = T(0), c2 = T(0);
+  if constexpr (CURVED) __syncthreads();
+  // flux at the face quadrature point (ta, tb)
+  T cv, c0o, c0n;
   {
     const T kap = a.kface ? a.kface[(size_t)f * P2 + t] : a.kappa;
-    T uo = FS[0 * P2 + t], un = FS[2 * P2 + t], dno, dnn, dA, sig;
+    T dno, dnn, dA, sig, go1 = T(0), go2 = T(0), gn1 = T(0), gn2 = T(0), gvD,
+                              gnD;
     if constexpr (!CURVED) {
       const T nsc = (S ? T(1) : T(-1)) * a.ns[D];
       dA = sw[ta] * sw[tb] * a.fa[D];
       sig = a.sg[D];
-      dno = nsc * FS[1 * P2 + t];
-      dnn = bnd ? dno : nsc * FS[3 * P2 + t];
-      if (bnd) un = -uo;  // mirror state u+ = -u-, grad u+ = grad u- (Eq. 7)
-      const T kdA = kap * dA;
-      const T jump = uo - un;
-      cv = kdA * (sig * jump - T(0.5) * (dno + dnn));
-      c0 = T(-0.5) * kdA * jump * nsc;
+      dno = nsc * so;
+      dnn = bnd ? dno : nsc * q3;
+      gvD = nsc;
+      gnD = nsc;
     } else {
-      const T* fd = a.fdata + (size_t)f * 7 * P2;
-      dA = fd[t];
+      const int T1 = D == 0 ? 1 : 0;
+      const int T2 = D == 2 ? 1 : 2;
+      const T* fd = a.fdata + (size_t)f * 7 * P2 + t;
+      dA = fd[0];
       sig = a.sigma[f];
-      // reference gradients in (x, y, z) from (normal, first, second
-      // tangential) components
-      const T on = FS[1 * P2 + t], o1 = FS[4 * P2 + t], o2 = FS[5 * P2 + t];
-      const T nn = FS[3 * P2 + t], n1 = FS[6 * P2 + t], n2 = FS[7 * P2 + t];
-      const T gox = D == 0 ? on : o1, goy = D == 1 ? on : (D == 0 ? o1 : o2),
-              goz = D == 2 ? on : o2;
-      const T gnx = D == 0 ? nn : n1, gny = D == 1 ? nn : (D == 0 ? n1 : n2),
-              gnz = D == 2 ? nn : n2;
-      const int oo = S ? 1 : 4, on_ = S ? 4 : 1;  // own / neighbour J^{-1} n
-      const T sgn = S ? T(1) : T(-1);  // own outward normal is sgn * n
-      const T ox = fd[oo * P2 + t], oy = fd[(oo + 1) * P2 + t],
-              oz = fd[(oo + 2) * P2 + t];
-      const T mx = fd[on_ * P2 + t], my = fd[(on_ + 1) * P2 + t],
-              mz = fd[(on_ + 2) * P2 + t];
-      dno = sgn * (ox * gox + oy * goy + oz * goz);
-      dnn = bnd ? dno : sgn * (mx * gnx + my * gny + mz * gnz);
-      if (bnd) un = -uo;
-      const T kdA = kap * dA;
-      const T jump = uo - un;
-      cv = kdA * (sig * jump - T(0.5) * (dno + dnn));
-      const T cg = T(-0.5) * kdA * jump * sgn;
-      const T gD = D == 0 ? ox : (D == 1 ? oy : oz);
-      const T g1 = D == 0 ? oy : ox;
-      const T g2 = D == 2 ? oy : oz;
-      c0 = cg * gD;
-      c1 = cg * g1;
-      c2 = cg * g2;
-    }
-  }
-  __syncthreads();
-  FS[0 * P2 + t] = cv;
-  FS[1 * P2 + t] = c0;
-  if constexpr (CURVED) {
-    FS[2 * P2 + t] = c1;
-    FS[3 * P2 + t] = c2;
-    __syncthreads();
-    // tangential test slopes fold into the face-layer values
-    for (int it = t; it < 2 * P; it += P2) {
-      if (it < P)
-        face_line<P, T, T_D, true, 0>(FS + 2 * P2, FS + 4 * P2, it);
-      else
-        face_line<P, T, T_D, true, 1>(FS + 3 * P2, FS + 5 * P2, it - P);
-    }
-    __syncthreads();
-    FS[0 * P2 + t] += FS[4 * P2 + t] + FS[5 * P2 + t];
-  }
-  __syncthreads();
-  // S^T along a, then along b, for the value and normal-slope parts
-  for (int it = t; it < 2 * P; it += P2)
-    face_line<P, T, T_S, true, 0>(FS + (it / P) * P2, FS + (2 + it / P) * P2,
-                                  it % P);
-  __syncthreads();
-  for (int it = t; it < 2 * P; it += P2)
-    face_line<P, T, T_S, true, 1>(FS + (2 + it / P) * P2, FS + (it / P) * P2,
-                                  it % P);
-  __syncthreads();
-}
-
-// One face of the own cell with line sweeps (the float variant: per-point
-// table reads would saturate the load/store unit).
-template <int P, typename T, bool CURVED, int D, int S>
-__device__ __forceinline__ void face_contrib_ln(
-    const ApplyArgs<T>& a, bool active, int cx, int cy, int cz, const T* U,
-    T* Aq, T* FS, const T* sw, int ta, int tb) {
-  int m[3] = {a.n[0], a.n[1], a.n[2]};
-  m[D] += 1;
-  int fc[3] = {cx, cy, cz};
-  fc[D] += S;
-  const int f = a.face_off[D] + fc[0] + m[0] * (fc[1] + m[1] * fc[2]);
-  int nbc[3] = {cx, cy, cz};
-  nbc[D] += S ? 1 : -1;
-  const bool bnd = nbc[D] < 0 || nbc[D] >= a.n[D];
-  const int nb = bnd ? 0 : nbc[0] + a.n[0] * (nbc[1] + a.n[1] * nbc[2]);
-  face_gather<P, T, D, S>(a, active, nb, bnd, U, FS, ta, tb);
-  __syncthreads();
-  face_core<P, T, CURVED>(a, D, S, f, bnd, FS, sw, ta, tb);
-  face_scatter<P, T, D, S>(Aq, FS, ta, tb);
-  __syncthreads();
-}
-
-// One face of the own cell (axis D, side S: 0 lower, 1 upper), per face
-// point: thread (ta, tb) interpolates all four traces to its own Gauss point
-// with table rows from shared memory (the float64 variant: its FP64 pipe,
-// not the load/store unit, is the limit).  Adds the face integrals tested
-// with the own cell's basis into Aq (nodal values).
-template <int P, typename T, bool CURVED, int D, int S>
-__device__ __forceinline__ void face_contrib_pt(
-    const ApplyArgs<T>& a, bool active, int cx, int cy, int cz, const T* U,
-    T* Aq, T* FS, const T* sS, const T* sD, const T* s0, const T* s1,
-    const T* sw, int ta, int tb) {
-  constexpr int P2 = P * P, P3 = P2 * P;
-  constexpr int T1 = D == 0 ? 1 : 0;
-  constexpr int T2 = D == 2 ? 1 : 2;
-  const int t = ta + P * tb;
-  int m[3] = {a.n[0], a.n[1], a.n[2]};
-  m[D] += 1;
-  int fc[3] = {cx, cy, cz};
-  fc[D] += S;
-  const int f = a.face_off[D] + fc[0] + m[0] * (fc[1] + m[1] * fc[2]);
-  int nbc[3] = {cx, cy, cz};
-  nbc[D] += S ? 1 : -1;
-  const bool bnd = nbc[D] < 0 || nbc[D] >= a.n[D];
-  const int nb = bnd ? 0 : nbc[0] + a.n[0] * (nbc[1] + a.n[1] * nbc[2]);
-  const T* dS = S ? s1 : s0;  // own slope at its face
-  const T* dN = S ? s0 : s1;  // neighbour slope at its face
-  constexpr int lo = S ? P - 1 : 0;
-  constexpr int ln = S ? 0 : P - 1;
-  // F1: nodal face values and reference normal slopes of both sides
-  {
-    T vo = U[fnode<P, D>(lo, ta, tb)];
-    T dno = T(0);
-#pragma unroll
-    for (int l = 0; l < P; ++l) dno = fma(dS[l], U[fnode<P, D>(l, ta, tb)], dno);
-    T vn = T(0), dnn = T(0);
-    if (!bnd && active) {
-      const T* sp = a.src;
-      const size_t cb = (size_t)nb * P3;
-#pragma unroll
-      for (int l = 0; l < P; ++l) {
-        T u = sp[(cb + fnode<P, D>(l, ta, tb)) * a.stride + a.col];
-        dnn = fma(dN[l], u, dnn);
-        if (l == ln) vn = u;
-      }
-    }
-    FS[0 * P2 + t] = vo;
-    FS[1 * P2 + t] = dno;
-    FS[2 * P2 + t] = vn;
-    FS[3 * P2 + t] = dnn;
-  }
-  __syncthreads();
-  // F2: interpolate along the first tangential axis (a)
-#pragma unroll
-  for (int arr = 0; arr < 4; ++arr) {
-    T s = T(0);
-#pragma unroll
-    for (int j = 0; j < P; ++j)
-      s = fma(sS[ta * P + j], FS[arr * P2 + j + P * tb], s);
-    FS[(4 + arr) * P2 + t] = s;
-  }
-  __syncthreads();
-  // F3: along the second tangential axis (b)
-  T q[4];
-#pragma unroll
-  for (int arr = 0; arr < 4; ++arr) {
-    T s = T(0);
-#pragma unroll
-    for (int j = 0; j < P; ++j)
-      s = fma(sS[tb * P + j], FS[(4 + arr) * P2 + ta + P * j], s);
-    q[arr] = s;
-  }
-  __syncthreads();
-  if constexpr (CURVED) {
-    FS[0 * P2 + t] = q[0];
-    FS[2 * P2 + t] = q[2];
-    __syncthreads();
-  }
-  // flux at face quadrature point (ta, tb)
-  {
-    const T kap = a.kface ? a.kface[(size_t)f * P2 + t] : a.kappa;
-    T uo = q[0], un = q[2], dno, dnn, dA, sig;
-    T gvec[3] = {T(0), T(0), T(0)};  // own outward n J^{-T}... in xi coords
-    if constexpr (!CURVED) {
-      const T sgn = S ? T(1) : T(-1);
-      dA = sw[ta] * sw[tb] * a.fa[D];
-      sig = a.sg[D];
-      dno = sgn * a.ns[D] * q[1];
-      dnn = bnd ? dno : sgn * a.ns[D] * q[3];
-      gvec[D] = sgn * a.ns[D];
-    } else {
-      const T* fd = a.fdata + (size_t)f * 7 * P2;
-      dA = fd[t];
-      sig = a.sigma[f];
-      T go[3], gn[3];
-      go[D] = q[1];
-      gn[D] = q[3];
-      T s1o = T(0), s2o = T(0), s1n = T(0), s2n = T(0);
+      T t1o = T(0), t2o = T(0), t1n = T(0), t2n = T(0);
 #pragma unroll
       for (int j = 0; j < P; ++j) {
-        s1o = fma(sD[ta * P + j], FS[0 * P2 + j + P * tb], s1o);
-        s2o = fma(sD[tb * P + j], FS[0 * P2 + ta + P * j], s2o);
-        s1n = fma(sD[ta * P + j], FS[2 * P2 + j + P * tb], s1n);
-        s2n = fma(sD[tb * P + j], FS[2 * P2 + ta + P * j], s2n);
+        t1o = fma(sD[ta * P + j], FS[j + P * tb], t1o);
+        t2o = fma(sD[tb * P + j], FS[ta + P * j], t2o);
+        if constexpr (S == 1) {
+          t1n = fma(sD[ta * P + j], FS[2 * P2 + j + P * tb], t1n);
+          t2n = fma(sD[tb * P + j], FS[2 * P2 + ta + P * j], t2n);
+        }
       }
-      go[T1] = s1o;
-      go[T2] = s2o;
-      gn[T1] = s1n;
-      gn[T2] = s2n;
-      T nL[3], nR[3];
-#pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        nL[e] = fd[(1 + e) * P2 + t];
-        nR[e] = fd[(4 + e) * P2 + t];
+      // J^-1 n of the lower (L) and upper (R) cell, face-local components
+      const T RD = fd[(4 + D) * P2], R1 = fd[(4 + T1) * P2],
+              R2 = fd[(4 + T2) * P2];
+      if constexpr (S == 1) {  // own cell is the lower one: outward = +n
+        const T LD = fd[(1 + D) * P2], L1 = fd[(1 + T1) * P2],
+                L2 = fd[(1 + T2) * P2];
+        dno = LD * so + L1 * t1o + L2 * t2o;
+        dnn = bnd ? dno : RD * q3 + R1 * t1n + R2 * t2n;
+        gvD = LD;
+        go1 = L1;
+        go2 = L2;
+        gnD = RD;
+        gn1 = R1;
+        gn2 = R2;
+      } else {  // own cell is the upper one (boundary only): outward = -n
+        dno = -(RD * so + R1 * t1o + R2 * t2o);
+        dnn = dno;
+        gvD = -RD;
+        go1 = -R1;
+        go2 = -R2;
+        gnD = gvD;
       }
-      if constexpr (S == 1) {  // own cell is the left one: outward = +n
-        dno = nL[0] * go[0] + nL[1] * go[1] + nL[2] * go[2];
-        dnn = nR[0] * gn[0] + nR[1] * gn[1] + nR[2] * gn[2];
-#pragma unroll
-        for (int e = 0; e < 3; ++e) gvec[e] = nL[e];
-      } else {  // own cell is the right one: outward = -n
-        dno = -(nR[0] * go[0] + nR[1] * go[1] + nR[2] * go[2]);
-        dnn = -(nL[0] * gn[0] + nL[1] * gn[1] + nL[2] * gn[2]);
-#pragma unroll
-        for (int e = 0; e < 3; ++e) gvec[e] = -nR[e];
-      }
-      if (bnd) dnn = dno;
     }
     if (bnd) un = -uo;  // mirror state u+ = -u-, grad u+ = grad u- (Eq. 7)
     const T kdA = kap * dA;
     const T jump = uo - un;
-    const T avg = T(0.5) * (dno + dnn);
-    const T cv = kdA * (sig * jump - avg);
+    cv = kdA * (sig * jump - T(0.5) * (dno + dnn));
     const T cg = T(-0.5) * kdA * jump;
-    FS[4 * P2 + t] = cv;
-    FS[5 * P2 + t] = cg * gvec[D];
-    FS[6 * P2 + t] = cg * gvec[T1];
-    FS[7 * P2 + t] = cg * gvec[T2];
+    c0o = cg * gvD;
+    c0n = cg * gnD;
+    if constexpr (CURVED) {
+      FS[4 * P2 + t] = cg * go1;
+      FS[5 * P2 + t] = cg * go2;
+      if constexpr (S == 1) {
+        FS[6 * P2 + t] = cg * gn1;
+        FS[7 * P2 + t] = cg * gn2;
+      }
+    }
   }
-  __syncthreads();
-  // tangential test slopes fold into the face-layer values
-  T vq = FS[4 * P2 + t];
+  // fold the tangential test slopes into the value parts (D^T at the face
+  // points)
+  T vo = cv, vn = -cv;
   if constexpr (CURVED) {
+    __syncthreads();
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      vq = fma(sD[j * P + ta], FS[6 * P2 + j + P * tb], vq);
-      vq = fma(sD[j * P + tb], FS[7 * P2 + ta + P * j], vq);
+      vo = fma(sD[j * P + ta], FS[4 * P2 + j + P * tb], vo);
+      vo = fma(sD[j * P + tb], FS[5 * P2 + ta + P * j], vo);
+      if constexpr (S == 1) {
+        vn = fma(sD[j * P + ta], FS[6 * P2 + j + P * tb], vn);
+        vn = fma(sD[j * P + tb], FS[7 * P2 + ta + P * j], vn);
+      }
     }
   }
-  FS[0 * P2 + t] = vq;
-  FS[1 * P2 + t] = FS[5 * P2 + t];
-  __syncthreads();
-  // S^T along a
+  // own test terms onto the line of Gauss points along D
+  if (own) {
 #pragma unroll
-  for (int arr = 0; arr < 2; ++arr) {
-    T s = T(0);
-#pragma unroll
-    for (int j = 0; j < P; ++j)
-      s = fma(sS[j * P + ta], FS[arr * P2 + j + P * tb], s);
-    FS[(2 + arr) * P2 + t] = s;
+    for (int l = 0; l < P; ++l) {
+      T& y = Aq[n0 + l * ls];
+      y = fma(tv<T, P, GV>(l), vo, fma(tv<T, P, GD>(l), c0o, y));
+    }
   }
-  __syncthreads();
-  // S^T along b and distribution onto the own nodes of line (ta, tb)
-  {
-    T vf = T(0), nf = T(0);
+  // the neighbour's test terms to its face nodes: S^T along a, then b
+  if constexpr (S == 1) {
+    FS[0 * P2 + t] = vn;
+    FS[1 * P2 + t] = c0n;
+    __syncthreads();
+    T ra[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) ra[j] = sS[j * P + ta];
+    T s0 = T(0), s1 = T(0);
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      vf = fma(sS[j * P + tb], FS[2 * P2 + ta + P * j], vf);
-      nf = fma(sS[j * P + tb], FS[3 * P2 + ta + P * j], nf);
+      s0 = fma(ra[j], FS[j + P * tb], s0);
+      s1 = fma(ra[j], FS[P2 + j + P * tb], s1);
     }
-    Aq[fnode<P, D>(lo, ta, tb)] += vf;
+    FS[4 * P2 + t] = s0;
+    FS[5 * P2 + t] = s1;
+    __syncthreads();
 #pragma unroll
-    for (int l = 0; l < P; ++l) Aq[fnode<P, D>(l, ta, tb)] += dS[l] * nf;
+    for (int j = 0; j < P; ++j) ra[j] = sS[j * P + tb];
+    T r0 = T(0), r1 = T(0);
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      r0 = fma(ra[j], FS[4 * P2 + ta + P * j], r0);
+      r1 = fma(ra[j], FS[5 * P2 + ta + P * j], r1);
+    }
+    if (pair) {
+      T* fbn = a.fb + ((size_t)nb * 6 + 2 * D) * P2 * a.stride + col;
+      fbn[(size_t)t * a.stride] = r0;
+      fbn[(size_t)(P2 + t) * a.stride] = r1;
+    }
   }
+}
+
+template <int P, typename T, bool CURVED>
+__device__ __noinline__ void face_lower_gp(const ApplyArgs<T>& a, int col,
+                                           int D, bool active, int cx, int cy,
+                                           int cz, const T* U, T* Aq, T* FS,
+                                           const T* sS, const T* sD,
+                                           const T* sw, int ta, int tb) {
+  face_gp<P, T, CURVED, 0>(a, col, D, active, cx, cy, cz, U, Aq, FS, sS, sD,
+                           sw, ta, tb);
   __syncthreads();
+}
+
+// Adds the terms that the cell below each interior face left for the cell
+// above it (face buffer slots 2D: value part on the face layer, 2D + 1:
+// normal-slope part on every layer with the weight dphi_l(0)); one thread
+// per node line along z of a row of cells (blockIdx.y: cy, cz; blockIdx.z:
+// column).
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_dg_face_add_t(const ApplyArgs<T> a) {
+  constexpr int P2 = P * P, P3 = P2 * P;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n[0] * P2) return;
+  const int R = a.stride, col = blockIdx.z;
+  const int cx = i / P2, xy = i - cx * P2;
+  const int x = xy % P, y = xy / P;
+  const int rows = a.n[1] * a.n[2];
+  for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+    const int cy = row % a.n[1], cz = row / a.n[1];
+    const size_t cell = (size_t)row * a.n[0] + cx;
+    const T* fb = a.fb + cell * 6 * P2 * R + col;
+    T* out = a.dst + (cell * P3 + xy) * R + col;
+    T u[P], gx[P], vx[P], gy[P], vy[P];
+#pragma unroll
+    for (int z = 0; z < P; ++z) {
+      u[z] = out[(size_t)z * P2 * R];
+      gx[z] = fb[(size_t)(1 * P2 + y + P * z) * R];
+      vx[z] = x == 0 ? fb[(size_t)(0 * P2 + y + P * z) * R] : T(0);
+      gy[z] = fb[(size_t)(3 * P2 + x + P * z) * R];
+      vy[z] = y == 0 ? fb[(size_t)(2 * P2 + x + P * z) * R] : T(0);
+    }
+    const T gz = fb[(size_t)(5 * P2 + xy) * R];
+    const T vz = fb[(size_t)(4 * P2 + xy) * R];
+    const T wx = tv<T, P, T_DPHI0>(x), wy = tv<T, P, T_DPHI0>(y);
+#pragma unroll
+    for (int z = 0; z < P; ++z) {
+      T s = u[z];
+      if (cx > 0) s += fma(wx, gx[z], vx[z]);
+      if (cy > 0) s += fma(wy, gy[z], vy[z]);
+      if (cz > 0) s += fma(tv<T, P, T_DPHI0>(z), gz, z == 0 ? vz : T(0));
+      out[(size_t)z * P2 * R] = s;
+    }
+  }
 }
 
 // Work decomposition: a block owns `cpb` cells and `ncols` right-hand-side
@@ -468,7 +353,7 @@ __global__ void k_apply(const ApplyArgs<T> a) {
   T* Aq = base;
   T* GX = base + P3;
   T* GY = base + 2 * P3;
-  T* U = base + 3 * P3;   // DG: nodal input
+  T* U = base + 3 * P3;   // DG: values at the Gauss points
   T* FS = base + 4 * P3;  // DG: face scratch [8][p^2]
   T* tabs = sm + (size_t)(cpb * nc + 1) * cell_smem_elems<T, P, DG>();
   T* sS = tabs;
@@ -480,8 +365,7 @@ __global__ void k_apply(const ApplyArgs<T> a) {
   load_tables_shared<T, P>(sS, sD, sDphi, s0, s1, sw);
   __syncthreads();
   const int gx0 = a.g[0], gy0 = a.g[1], gz0 = a.g[2];
-  ApplyArgs<T> ac = a;
-  ac.col = a.col + rr;
+  const int col = a.col + rr;
 
   for (int cbase = blockIdx.x * cpb; cbase < a.ncells;
        cbase += gridDim.x * cpb) {
@@ -491,7 +375,6 @@ __global__ void k_apply(const ApplyArgs<T> a) {
     const int cx = cc % a.n[0];
     const int cy = (cc / a.n[0]) % a.n[1];
     const int cz = cc / (a.n[0] * a.n[1]);
-    const int col = ac.col;
     T r[P], o[P];
     T gp[PREFETCH ? 6 : 1][PREFETCH ? P : 1];
     if constexpr (PREFETCH) {
@@ -508,7 +391,6 @@ __global__ void k_apply(const ApplyArgs<T> a) {
       for (int z = 0; z < P; ++z) {
         const size_t gi = (size_t)cc * P3 + idx3<P>(ta, tb, z);
         r[z] = active ? a.src[gi * a.stride + col] : T(0);
-        U[idx3<P>(ta, tb, z)] = r[z];
       }
     } else {
       const int X = cx * (P - 1) + ta, Y = cy * (P - 1) + tb;
@@ -537,6 +419,10 @@ __global__ void k_apply(const ApplyArgs<T> a) {
     mv<T, P, T_S>(r, o);
 #pragma unroll
     for (int j = 0; j < P; ++j) Aq[idx3<P>(j, ta, tb)] = o[j];
+    if constexpr (DG) {  // values at the Gauss points for the face terms
+#pragma unroll
+      for (int j = 0; j < P; ++j) U[idx3<P>(j, ta, tb)] = o[j];
+    }
     mv<T, P, T_D>(o, r);
 #pragma unroll
     for (int j = 0; j < P; ++j) GX[idx3<P>(j, ta, tb)] = r[j];
@@ -601,6 +487,25 @@ __global__ void k_apply(const ApplyArgs<T> a) {
     mtv<T, P, T_D>(r, o);
 #pragma unroll
     for (int j = 0; j < P; ++j) o[j] += Aq[idx3<P>(j, ta, tb)];
+    if constexpr (DG) {
+      // ---- SIPG face terms (Eq. 6, Eq. 7), added at the Gauss points
+#pragma unroll
+      for (int j = 0; j < P; ++j) Aq[idx3<P>(j, ta, tb)] = o[j];
+      __syncthreads();
+#pragma unroll 1
+      for (int D = 0; D < 3; ++D) {
+        // lower faces only where a cell of the block lies on the boundary
+        const int cD = D == 0 ? cx : (D == 1 ? cy : cz);
+        if (__syncthreads_or(active && cD == 0))
+          face_lower_gp<P, T, CURVED>(a, col, D, active, cx, cy, cz, U, Aq,
+                                      FS, sS, sD, sw, ta, tb);
+        face_gp<P, T, CURVED, 1>(a, col, D, active, cx, cy, cz, U, Aq, FS, sS,
+                                 sD, sw, ta, tb);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < P; ++j) o[j] = Aq[idx3<P>(j, ta, tb)];
+    }
     mtv<T, P, T_S>(o, r);
 #pragma unroll
     for (int j = 0; j < P; ++j) Aq[idx3<P>(j, ta, tb)] = r[j];
@@ -634,27 +539,11 @@ __global__ void k_apply(const ApplyArgs<T> a) {
       }
       __syncthreads();
     } else {
-#pragma unroll
-      for (int z = 0; z < P; ++z) Aq[idx3<P>(ta, tb, z)] = o[z];
-      __syncthreads();
-      if constexpr (sizeof(T) == 4) {
-#define FACE(DD, SS)                                                          \
-  face_contrib_ln<P, T, CURVED, DD, SS>(ac, active, cx, cy, cz, U, Aq, FS, sw, \
-                                        ta, tb)
-        FACE(0, 0); FACE(0, 1); FACE(1, 0); FACE(1, 1); FACE(2, 0); FACE(2, 1);
-#undef FACE
-      } else {
-#define FACE(DD, SS)                                                          \
-  face_contrib_pt<P, T, CURVED, DD, SS>(ac, active, cx, cy, cz, U, Aq, FS, sS, \
-                                        sD, s0, s1, sw, ta, tb)
-        FACE(0, 0); FACE(0, 1); FACE(1, 0); FACE(1, 1); FACE(2, 0); FACE(2, 1);
-#undef FACE
-      }
       if (active) {
 #pragma unroll
         for (int z = 0; z < P; ++z) {
           const size_t gi = (size_t)cc * P3 + idx3<P>(ta, tb, z);
-          a.dst[gi * a.stride + col] = Aq[idx3<P>(ta, tb, z)];
+          a.dst[gi * a.stride + col] = o[z];
         }
       }
       __syncthreads();
@@ -726,6 +615,18 @@ void run_apply_cols(const ApplyArgs<T>& a0, int R, int cells_req,
     a.col = c0;
     run_apply<P, T, DG, CURVED>(a, cells, nc, s);
   }
+  if constexpr (DG) {
+    MFP_REQUIRE(a0.fb, "SIPG face buffer missing");
+    const int threads = 256;
+    const int bx = (a0.n[0] * P2 + threads - 1) / threads;
+    const int rows = a0.n[1] * a0.n[2];
+    const int by = rows < 65535 ? rows : 65535;
+    if (a0.ncells > 0) {
+      k_dg_face_add_t<P, T><<<dim3(bx, by, R), threads, 0, s>>>(a0);
+      MFP_CHECK_CUDA(cudaGetLastError());
+      note_launch();
+    }
+  }
 }
 
 template <typename T>
@@ -745,6 +646,7 @@ ApplyArgs<T> make_apply_args(const Level& L, const LevelData<T>& D,
   a.kface = D.kface;
   a.fdata = D.fdata;
   a.sigma = D.sigma;
+  a.fb = static_cast<T*>(L.fbuf);
   a.kappa = (T)L.kappa;
   const double vol = L.h[0] * L.h[1] * L.h[2];
   const double pen = L.penalty * (double)L.p * L.p;

@@ -30,6 +30,8 @@ struct DevTab {
   T w[kMaxP];             // Gauss weights on [0, 1]
   T g[kMaxP];             // Gauss points on [0, 1]
   T x[kMaxP];             // GLL points on [0, 1]
+  T gv0[kMaxP], gv1[kMaxP];  // Lagrange basis of the Gauss points at 0, 1
+  T gd0[kMaxP], gd1[kMaxP];  // and its slopes there
 };
 
 // The same tables as double-float pairs (value = hi + lo, |lo| <= ulp(hi)/2)
@@ -172,8 +174,9 @@ struct Level {
   void* t_x = nullptr;    // iterate (levels below the finest)
   void* t_b = nullptr;    // right-hand side (levels below the finest)
   int scratch_rhs = 0;
-  // float64 SIPG apply in double-float arithmetic: the face terms each cell
-  // leaves for its upper neighbours, [ncells][6][p^2] float pairs x fbuf_rhs
+  // SIPG applies: the face terms each cell leaves for its upper neighbours,
+  // [ncells][6][p^2] x fbuf_rhs entries of 8 bytes (float, float64 or a
+  // double-float pair; the applies of one level are stream-ordered)
   void* fbuf = nullptr;
   int fbuf_rhs = 0;
 };
