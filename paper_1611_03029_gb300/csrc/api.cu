@@ -88,6 +88,17 @@ void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
   LevelData<T>& D = level_data<T>(L);
   MFP_REQUIRE(D.valid, "level data of this precision was not built "
                        "(mg_precision must be MFP_FP32 for float applies)");
+  const T* dense = nullptr;
+  if constexpr (sizeof(T) == 8)
+    dense = reinterpret_cast<const T*>(L.dense64);
+  else
+    dense = reinterpret_cast<const T*>(L.dense32);
+  if (dense) {
+    launch_dense_apply<T>(dense, src, dst, (int)L.ndofs, R, L.dpart, L.dcnt,
+                          s);
+    L.applies += R;
+    return;
+  }
   if (L.disc == MFP_CG)
     MFP_CHECK_CUDA(
         cudaMemsetAsync(dst, 0, (size_t)L.ndofs * R * sizeof(T), s));
@@ -354,6 +365,45 @@ void estimate_eigenvalues(mfp_ctx* c, int l, cudaStream_t s) {
   L.applies = 0;
 }
 
+void to_float_array(const double* a, float*& b, int64_t n, cudaStream_t s);
+
+void free_dense(Level& L) {
+  dfree(L.dense64);
+  dfree(L.dense32);
+  dfree(L.dpart);
+  dfree(L.dcnt);
+}
+
+// Assembles the operator of a coarsest level with at most kDenseMax dofs as a
+// dense matrix, by matrix-free applies to blocks of identity columns.
+void assemble_dense(mfp_ctx* c, Level& L, cudaStream_t s) {
+  free_dense(L);
+  const int64_t n = L.ndofs;
+  if (n > kDenseMax) return;
+  const int blk = kMaxRhs;
+  double* A = dalloc<double>(n * n);
+  double* E = dalloc<double>(n * blk);
+  double* Y = dalloc<double>(n * blk);
+  for (int64_t c0 = 0; c0 < n; c0 += blk) {
+    const int R = (int)(n - c0 < blk ? n - c0 : blk);
+    launch_identity_block(E, n, c0, R, s);
+    apply_level<double>(c, L, E, Y, R, s);
+    launch_store_columns(Y, A, n, c0, R, s);
+  }
+  MFP_CHECK_CUDA(cudaStreamSynchronize(s));
+  dfree(E);
+  dfree(Y);
+  L.dpart = dalloc<double>((int64_t)kDenseSplit * kMaxRhs * n);
+  const int64_t nrb = (n + kDenseRows - 1) / kDenseRows;
+  MFP_CHECK_CUDA(cudaMalloc(&L.dcnt, nrb * kMaxRhs * sizeof(unsigned)));
+  MFP_CHECK_CUDA(
+      cudaMemsetAsync(L.dcnt, 0, nrb * kMaxRhs * sizeof(unsigned), s));
+  if (c->vprec == MFP_FP32) to_float_array(A, L.dense32, n * n, s);
+  L.dense64 = A;
+  L.applies = 0;
+  MFP_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
 void free_level(Level& L) {
   for (LevelData<double>* D : {&L.d64}) {
     dfree(D->G);
@@ -379,6 +429,7 @@ void free_level(Level& L) {
   dfree(L.t_x);
   dfree(L.t_b);
   dfree(L.fbuf);
+  free_dense(L);
 }
 
 void free_ctx(mfp_ctx* c) {
@@ -462,7 +513,9 @@ void build_levels(mfp_ctx* c, cudaStream_t s) {
       to_float_array(L.d64.dinv, L.d32.dinv, L.ndofs, s);
       L.d32.valid = true;
     }
+    if (l == 0) free_dense(L);  // stale after a coefficient change
     estimate_eigenvalues(c, (int)l, s);
+    if (l == 0 && c->levels.size() > 1) assemble_dense(c, L, s);
   }
   MFP_CHECK_CUDA(cudaStreamSynchronize(s));
 }

@@ -651,6 +651,90 @@ static int red_grid(int64_t rows, int R) {
   return (int)b;
 }
 
+// ---------------------------------------------------------------------------
+// Dense coarse operator (coarsest level, at most kDenseMax dofs).
+// ---------------------------------------------------------------------------
+// e = the columns c0 .. c0+R-1 of the identity, [n][R]
+__global__ void k_identity_block(double* e, int64_t n, int64_t c0, int R) {
+  GRID_STRIDE(i, n * R) {
+    const int64_t row = i / R;
+    e[i] = row == c0 + (i - row * R) ? 1.0 : 0.0;
+  }
+}
+
+// a[(c0 + r) * n + row] = y[row * R + r]  (column-major store)
+__global__ void k_store_columns(const double* y, double* a, int64_t n,
+                                int64_t c0, int R) {
+  GRID_STRIDE(i, n * R) {
+    const int64_t row = i % n, r = i / n;
+    a[(c0 + r) * n + row] = y[row * R + r];
+  }
+}
+
+// y = A x for column blockIdx.z of [n][R] vectors, A column-major n x n.
+// Block (row block, column range ks) forms partial sums over its range; the
+// last block of a row block to arrive adds the kDenseSplit partials in order
+// (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(kDenseRows)
+    k_dense_apply(const T* __restrict__ A, const T* __restrict__ x,
+                  T* __restrict__ y, int n, int R, double* part,
+                  unsigned* cnt) {
+  const int i = blockIdx.x * kDenseRows + threadIdx.x;
+  const int ks = blockIdx.y, r = blockIdx.z;
+  const int j0 = (int)((int64_t)n * ks / kDenseSplit);
+  const int j1 = (int)((int64_t)n * (ks + 1) / kDenseSplit);
+  T s = T(0);
+  if (i < n)
+    for (int j = j0; j < j1; ++j)
+      s = fma(A[(size_t)j * n + i], x[(size_t)j * R + r], s);
+  if (i < n) part[((size_t)ks * R + r) * n + i] = (double)s;
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    last = atomicAdd(&cnt[blockIdx.x * R + r], 1u) == kDenseSplit - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (i < n) {
+    double t = 0.0;
+    for (int k = 0; k < kDenseSplit; ++k)
+      t += part[((size_t)k * R + r) * n + i];
+    y[(size_t)i * R + r] = (T)t;
+  }
+  if (threadIdx.x == 0) cnt[blockIdx.x * R + r] = 0u;
+}
+
+void launch_identity_block(double* e, int64_t n, int64_t c0, int R,
+                           cudaStream_t s) {
+  k_identity_block<<<vec_grid(n * R), kVecThreads, 0, s>>>(e, n, c0, R);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+void launch_store_columns(const double* y, double* a, int64_t n, int64_t c0,
+                          int R, cudaStream_t s) {
+  k_store_columns<<<vec_grid(n * R), kVecThreads, 0, s>>>(y, a, n, c0, R);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+template <typename T>
+void launch_dense_apply(const T* A, const T* x, T* y, int n, int R,
+                        double* part, unsigned* cnt, cudaStream_t s) {
+  MFP_REQUIRE(n <= kDenseMax && R >= 1 && R <= kMaxRhs,
+              "dense coarse apply: size out of range");
+  const dim3 grid((n + kDenseRows - 1) / kDenseRows, kDenseSplit, R);
+  k_dense_apply<T><<<grid, kDenseRows, 0, s>>>(A, x, y, n, R, part, cnt);
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
+}
+template void launch_dense_apply<double>(const double*, const double*,
+                                         double*, int, int, double*,
+                                         unsigned*, cudaStream_t);
+template void launch_dense_apply<float>(const float*, const float*, float*,
+                                        int, int, double*, unsigned*,
+                                        cudaStream_t);
+
 void launch_dot(const double* a, const double* b, int64_t n, int R,
                 RedScratch& rs, double* scal, int op, double* hist, int hidx,
                 cudaStream_t s) {

@@ -119,6 +119,9 @@ enum ScalarSlot {
 };
 constexpr int kMaxRedBlocks = 1024;
 constexpr int kMaxRhs = 256;
+constexpr int kDenseMax = 2048;   // dofs of a coarsest level stored dense
+constexpr int kDenseRows = 128;   // rows per block of k_dense_apply
+constexpr int kDenseSplit = 16;   // column ranges per row block
 struct RedScratch {
   double* part = nullptr;  // [kMaxRedBlocks][R]
   unsigned* cnt = nullptr; // zero between launches
@@ -179,6 +182,14 @@ struct Level {
   // double-float pair; the applies of one level are stream-ordered)
   void* fbuf = nullptr;
   int fbuf_rhs = 0;
+  // Coarsest level with at most kDenseMax dofs: the operator assembled once
+  // as a dense column-major matrix (float64, and float for a float V-cycle).
+  // The coarse Chebyshev solve applies it with k_dense_apply: on a handful of
+  // cells the cell kernels are latency-bound (about 30 us per apply).
+  double* dense64 = nullptr;
+  float* dense32 = nullptr;
+  double* dpart = nullptr;   // partial sums [kDenseSplit][kMaxRhs][ndofs]
+  unsigned* dcnt = nullptr;  // arrival counters [row blocks][kMaxRhs]
 };
 
 template <typename T>
@@ -282,6 +293,14 @@ template <typename T>
 void launch_fill(T* x, T v, int64_t n, cudaStream_t s);
 void launch_invert_diag(const Level& L, double* diag, cudaStream_t s);
 void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t s);
+// dense coarse operator: assembly helpers and y = A x for R columns
+void launch_identity_block(double* e, int64_t n, int64_t c0, int R,
+                           cudaStream_t s);
+void launch_store_columns(const double* y, double* a, int64_t n, int64_t c0,
+                          int R, cudaStream_t s);
+template <typename T>
+void launch_dense_apply(const T* A, const T* x, T* y, int n, int R,
+                        double* part, unsigned* cnt, cudaStream_t s);
 void launch_to_double(const float* a, double* b, int64_t n, cudaStream_t s);
 template <typename T>
 void launch_cheb_first(const T* b, const T* dinv, T* d, T* x, const T* ax,

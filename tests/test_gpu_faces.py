@@ -63,3 +63,27 @@ def test_apply_is_deterministic(mfp):
     y0 = op.apply(u).cpu().numpy()
     for _ in range(3):
         assert np.array_equal(op.apply(u).cpu().numpy(), y0)
+
+
+@pytest.mark.parametrize("disc", ["cg", "dg"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_dense_coarse_level_apply(mfp, disc, prec):
+    # the coarsest level of a hierarchy (at most 2048 dofs) is applied from
+    # its assembled dense matrix; same operator as the oracle's coarse level,
+    # single and batched columns
+    from oracle import mg
+    dt = np.float64 if prec == "fp64" else np.float32
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    op = mfp.Poisson(4, 4, 4, 3, disc=disc, mapping="sine", map_param=0.1,
+                     mg_precision=prec)
+    assert op.n_levels == 2
+    P0 = mg.hierarchy(fem.Problem(4, 4, 4, 3, disc=disc, mapping="sine",
+                                  amp=0.1))[0]
+    A0 = fem.assemble(P0)
+    N = P0.n_dofs
+    assert op.n_dofs(0) == N
+    for R in (1, 3):
+        U = synthetic.random_vector(N, seed=50 + R, ncols=R).reshape(N, R)
+        Ut = torch.from_numpy(np.ascontiguousarray(U.astype(dt))).cuda()
+        Y = op.apply(Ut.reshape(-1), level=0, n_rhs=R).reshape(N, R)
+        assert rel_err(Y.cpu().numpy(), A0 @ U) <= tol, R
