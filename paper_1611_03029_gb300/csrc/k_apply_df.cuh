@@ -877,16 +877,28 @@ __global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
   }
 }
 
+template <int P, bool DG>
+size_t df_smem_bytes(int cpb, int ncols) {
+  return ((size_t)(cpb * ncols + 1) * df_cell_floats<P, DG>() +
+          df_table_floats<P>()) *
+         sizeof(float);
+}
+
+// Resident blocks per SM of a launch shape (cached per shape).
 template <int P, bool DG, bool CURVED>
-void run_apply_df(ApplyArgsDF a, int cpb, int ncols, cudaStream_t s) {
+int df_blocks_per_sm(int cpb, int ncols) {
+  static std::mutex mu;
+  static int cache[64][4] = {};
   constexpr int P2 = P * P;
-  a.cpb = cpb;
-  a.ncols = ncols;
   const int threads = ((cpb * ncols * P2 + 31) / 32) * 32;
-  const size_t smem =
-      ((size_t)(cpb * ncols + 1) * df_cell_floats<P, DG>() +
-       df_table_floats<P>()) *
-      sizeof(float);
+  const size_t smem = df_smem_bytes<P, DG>(cpb, ncols);
+  const bool cacheable = ncols == 1 && cpb < 64;
+  int dev = 0;
+  MFP_CHECK_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (cacheable && dev < 4 && cache[cpb][dev]) return cache[cpb][dev];
+  }
   auto kern = k_apply_df<P, DG, CURVED>;
   if (smem > 48 * 1024)
     MFP_CHECK_CUDA(cudaFuncSetAttribute(
@@ -894,6 +906,25 @@ void run_apply_df(ApplyArgsDF a, int cpb, int ncols, cudaStream_t s) {
   int per_sm = 0;
   MFP_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &per_sm, kern, threads, smem));
+  if (cacheable && dev < 4) {
+    std::lock_guard<std::mutex> lk(mu);
+    cache[cpb][dev] = per_sm;
+  }
+  return per_sm;
+}
+
+template <int P, bool DG, bool CURVED>
+void run_apply_df(ApplyArgsDF a, int cpb, int ncols, cudaStream_t s) {
+  constexpr int P2 = P * P;
+  a.cpb = cpb;
+  a.ncols = ncols;
+  const int threads = ((cpb * ncols * P2 + 31) / 32) * 32;
+  const size_t smem = df_smem_bytes<P, DG>(cpb, ncols);
+  auto kern = k_apply_df<P, DG, CURVED>;
+  const int per_sm = df_blocks_per_sm<P, DG, CURVED>(cpb, ncols);
+  if (smem > 48 * 1024)
+    MFP_CHECK_CUDA(cudaFuncSetAttribute(
+        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   MFP_REQUIRE(per_sm >= 1,
               "apply launch shape does not fit on an SM (cells per block too "
               "large for the registers or shared memory)");
