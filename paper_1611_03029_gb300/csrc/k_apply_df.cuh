@@ -100,8 +100,13 @@ __device__ __forceinline__ void dmtv(const float (&ih)[P],
 #ifndef MFP_DF_ROLL
 #define MFP_DF_ROLL 1
 #endif
+#ifndef MFP_DF_ROLL_BY
+#define MFP_DF_ROLL_BY 1
+#endif
+#define MFP_DF_STR2(x) #x
+#define MFP_DF_STR(x) MFP_DF_STR2(x)
 #if MFP_DF_ROLL
-#define MFP_DF_LOOP _Pragma("unroll (P >= 4 ? 1 : P)")
+#define MFP_DF_LOOP _Pragma(MFP_DF_STR(unroll(P >= 4 ? MFP_DF_ROLL_BY : P)))
 #else
 #define MFP_DF_LOOP _Pragma("unroll")
 #endif
