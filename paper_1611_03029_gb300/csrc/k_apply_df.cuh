@@ -45,6 +45,31 @@ struct ApplyArgsDF {
   int stride, col, cpb, ncols;
 };
 
+__device__ __forceinline__ df f2df(float2 v) { return df_make(v.x, v.y); }
+__device__ __forceinline__ float2 df2f(df v) { return make_float2(v.h, v.l); }
+__device__ __forceinline__ void st2(float2* a, int i, df v) { a[i] = df2f(v); }
+__device__ __forceinline__ dacc acc_first(float2 a, float2 b) {
+  return acc_first(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void acc_mac(dacc& s, float2 a, float2 b) {
+  acc_mac(s, a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ dacc acc_first(float ah, float al, float2 b) {
+  return acc_first(ah, al, b.x, b.y);
+}
+__device__ __forceinline__ void acc_mac(dacc& s, float ah, float al,
+                                        float2 b) {
+  acc_mac(s, ah, al, b.x, b.y);
+}
+
+__device__ __forceinline__ df ld(const float* h, const float* l, int i) {
+  return df_make(h[i], l[i]);
+}
+__device__ __forceinline__ void stv(float* h, float* l, int i, df v) {
+  h[i] = v.h;
+  l[i] = v.l;
+}
+
 enum DfTab { DF_S, DF_D };
 
 template <int P, int W>
@@ -121,8 +146,8 @@ __device__ __forceinline__ void dmtv(const float (&ih)[P],
 // o[base + q * st] (+)= sum_j M[q][j] in[j]  (TR: M[j][q]), q = 0..P-1
 template <int P, int W, bool TR, bool ADD>
 __device__ __forceinline__ void dsweep(const float (&ih)[P],
-                                       const float (&il)[P], float* oh,
-                                       float* ol, int base, int st) {
+                                       const float (&il)[P], float2* out,
+                                       int base, int st) {
   if constexpr (P >= 4 && MFP_DF_EO) {
     constexpr int H = P / 2, MC = H + P % 2;
     constexpr int w = 2 * (W == DF_D ? 1 : 0) + (TR ? 1 : 0);
@@ -158,13 +183,11 @@ __device__ __forceinline__ void dsweep(const float (&ih)[P],
       if constexpr (W == DF_D) r2 = -r2;
       const int o1 = base + q * st, o2 = base + (P - 1 - q) * st;
       if constexpr (ADD) {
-        r1 = df_make(oh[o1], ol[o1]) + r1;
-        r2 = df_make(oh[o2], ol[o2]) + r2;
+        r1 = f2df(out[o1]) + r1;
+        r2 = f2df(out[o2]) + r2;
       }
-      oh[o1] = r1.h;
-      ol[o1] = r1.l;
-      oh[o2] = r2.h;
-      ol[o2] = r2.l;
+      out[o1] = df2f(r1);
+      out[o2] = df2f(r2);
     }
     if constexpr (P % 2 == 1) {  // middle row: A (S) or B (D) only
       constexpr int r = H * kMaxH;
@@ -182,9 +205,8 @@ __device__ __forceinline__ void dsweep(const float (&ih)[P],
       }
       df rm = acc_get(sm);
       const int o = base + H * st;
-      if constexpr (ADD) rm = df_make(oh[o], ol[o]) + rm;
-      oh[o] = rm.h;
-      ol[o] = rm.l;
+      if constexpr (ADD) rm = f2df(out[o]) + rm;
+      out[o] = df2f(rm);
     }
   } else {
     MFP_DF_LOOP
@@ -198,22 +220,21 @@ __device__ __forceinline__ void dsweep(const float (&ih)[P],
                 il[j]);
       df r = acc_get(s);
       const int o = base + q * st;
-      if constexpr (ADD) r = df_make(oh[o], ol[o]) + r;
-      oh[o] = r.h;
-      ol[o] = r.l;
+      if constexpr (ADD) r = f2df(out[o]) + r;
+      out[o] = df2f(r);
     }
   }
 }
 
 // load the line base + j * st of a shared array into registers
 template <int P>
-__device__ __forceinline__ void dline(const float* h, const float* l,
-                                      int base, int st, float (&oh)[P],
-                                      float (&ol)[P]) {
+__device__ __forceinline__ void dline(const float2* x, int base, int st,
+                                      float (&oh)[P], float (&ol)[P]) {
 #pragma unroll
   for (int j = 0; j < P; ++j) {
-    oh[j] = h[base + j * st];
-    ol[j] = l[base + j * st];
+    const float2 v = x[base + j * st];
+    oh[j] = v.x;
+    ol[j] = v.y;
   }
 }
 
@@ -228,44 +249,33 @@ __device__ __forceinline__ int dfnode(int l, int a, int b) {
   return a + P * (b + P * l);
 }
 
-// odd stride: the columns of a batch fall into distinct shared-memory banks
+// Shared memory holds double-float values as float2 (hi, lo): one 64-bit
+// access per value.  Per virtual cell, in float2 units: A, X, Y (and U for
+// SIPG) of p^3 values, the SIPG face scratch of 8 p^2; the odd stride puts
+// the columns of a batch into distinct banks.
 template <int P, bool DG>
-__host__ __device__ constexpr int df_cell_floats() {
-  return ((DG ? 8 : 6) * P * P * P + (DG ? 16 * P * P : 0)) | 1;
+__host__ __device__ constexpr int df_cell_pairs() {
+  return ((DG ? 4 : 3) * P * P * P + (DG ? 8 * P * P : 0)) | 1;
 }
 template <int P>
-__host__ __device__ constexpr int df_table_floats() {
-  return 4 * P * P + 6 * P;
+__host__ __device__ constexpr int df_table_pairs() {
+  return 2 * P * P + 3 * P;
 }
 
 // shared DF table views (row-major p x p)
 struct ShDF {
-  const float *Sh, *Sl, *Dh, *Dl, *d0h, *d0l, *d1h, *d1l, *wh, *wl;
+  const float2 *S, *D, *d0, *d1, *w;
 };
 
-__device__ __forceinline__ df ld(const float* h, const float* l, int i) {
-  return df_make(h[i], l[i]);
-}
-__device__ __forceinline__ void stv(float* h, float* l, int i, df v) {
-  h[i] = v.h;
-  l[i] = v.l;
-}
-
 template <int P>
-__device__ __forceinline__ ShDF make_shdf(const float* tabs) {
+__device__ __forceinline__ ShDF make_shdf(const float2* tabs) {
   constexpr int P2 = P * P;
   ShDF t;
-  t.Sh = tabs;
-  t.Sl = tabs + P2;
-  t.Dh = tabs + 2 * P2;
-  t.Dl = tabs + 3 * P2;
-  const float* p = tabs + 4 * P2;
-  t.d0h = p;
-  t.d0l = p + P;
-  t.d1h = p + 2 * P;
-  t.d1l = p + 3 * P;
-  t.wh = p + 4 * P;
-  t.wl = p + 5 * P;
+  t.S = tabs;
+  t.D = tabs + P2;
+  t.d0 = tabs + 2 * P2;
+  t.d1 = t.d0 + P;
+  t.w = t.d1 + P;
   return t;
 }
 
@@ -287,9 +297,8 @@ __device__ __forceinline__ ShDF make_shdf(const float* tabs) {
 template <int P, bool CURVED, int S>
 __device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
                                            int D, bool active, int cx, int cy,
-                                           int cz, const float* Uh,
-                                           const float* Ul, float* Ah,
-                                           float* Al, float* FSh, float* FSl,
+                                           int cz, const float2* U,
+                                           float2* A, float2* FS,
                                            const ShDF& t, int ta, int tb) {
   constexpr int P2 = P * P, P3 = P2 * P;
   const int ti = ta + P * tb;
@@ -316,17 +325,17 @@ __device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
   // own trace and reference normal slope at the face point (ta, tb)
   df uo, so;
   {
-    dacc sv = acc_first(gvh[0], gvl[0], Uh[n0], Ul[n0]);
-    dacc sd = acc_first(gdh[0], gdl[0], Uh[n0], Ul[n0]);
+    dacc sv = acc_first(gvh[0], gvl[0], U[n0]);
+    dacc sd = acc_first(gdh[0], gdl[0], U[n0]);
 #pragma unroll
     for (int l = 1; l < P; ++l) {
-      acc_mac(sv, gvh[l], gvl[l], Uh[n0 + l * ls], Ul[n0 + l * ls]);
-      acc_mac(sd, gdh[l], gdl[l], Uh[n0 + l * ls], Ul[n0 + l * ls]);
+      acc_mac(sv, gvh[l], gvl[l], U[n0 + l * ls]);
+      acc_mac(sd, gdh[l], gdl[l], U[n0 + l * ls]);
     }
     uo = acc_get(sv);
     so = acc_get(sd);
   }
-  if constexpr (CURVED) stv(FSh, FSl, 0 * P2 + ti, uo);
+  if constexpr (CURVED) st2(FS, 0 * P2 + ti, uo);
   // the upper neighbour's face layer and reference normal slope (nodal),
   // interpolated to the face points: FS[2, 3] -> FS[6, 7] -> FS[2, 3]
   if constexpr (S == 1) {
@@ -341,37 +350,35 @@ __device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
       for (int l = 0; l < P; ++l) {
         const df u = df_from_double(u0[l * lstr]);
         if (l == 0) {
-          sn = acc_first(t.d0h[0], t.d0l[0], u.h, u.l);
+          sn = acc_first(t.d0[0], make_float2(u.h, u.l));
           vn = u;
         } else {
-          acc_mac(sn, t.d0h[l], t.d0l[l], u.h, u.l);
+          acc_mac(sn, t.d0[l], make_float2(u.h, u.l));
         }
       }
       dnn = acc_get(sn);
     }
-    stv(FSh, FSl, 2 * P2 + ti, vn);
-    stv(FSh, FSl, 3 * P2 + ti, dnn);
+    st2(FS, 2 * P2 + ti, vn);
+    st2(FS, 3 * P2 + ti, dnn);
     __syncthreads();
 #pragma unroll 1
     for (int arr = 2; arr < 4; ++arr) {
-      const float* ih = FSh + arr * P2 + P * tb;
-      const float* il = FSl + arr * P2 + P * tb;
-      dacc s = acc_first(t.Sh[ta * P], t.Sl[ta * P], ih[0], il[0]);
+      const float2* iv = FS + arr * P2 + P * tb;
+      dacc s = acc_first(t.S[ta * P], iv[0]);
 #pragma unroll
       for (int j = 1; j < P; ++j)
-        acc_mac(s, t.Sh[ta * P + j], t.Sl[ta * P + j], ih[j], il[j]);
-      stv(FSh, FSl, (4 + arr) * P2 + ti, acc_get(s));
+        acc_mac(s, t.S[ta * P + j], iv[j]);
+      st2(FS, (4 + arr) * P2 + ti, acc_get(s));
     }
     __syncthreads();
 #pragma unroll 1
     for (int arr = 2; arr < 4; ++arr) {
-      const float* ih = FSh + (4 + arr) * P2 + ta;
-      const float* il = FSl + (4 + arr) * P2 + ta;
-      dacc s = acc_first(t.Sh[tb * P], t.Sl[tb * P], ih[0], il[0]);
+      const float2* iv = FS + (4 + arr) * P2 + ta;
+      dacc s = acc_first(t.S[tb * P], iv[0]);
 #pragma unroll
       for (int j = 1; j < P; ++j)
-        acc_mac(s, t.Sh[tb * P + j], t.Sl[tb * P + j], ih[P * j], il[P * j]);
-      stv(FSh, FSl, arr * P2 + ti, acc_get(s));
+        acc_mac(s, t.S[tb * P + j], iv[P * j]);
+      st2(FS, arr * P2 + ti, acc_get(s));
     }
   }
   if constexpr (CURVED) __syncthreads();
@@ -383,14 +390,14 @@ __device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
     const df kap = a.kfh ? df_make(a.kfh[(size_t)f * P2 + ti],
                                    a.kfl[(size_t)f * P2 + ti])
                          : a.kappa;
-    df un = S ? ld(FSh, FSl, 2 * P2 + ti) : df_make(0.f);
-    const df q3 = S ? ld(FSh, FSl, 3 * P2 + ti) : df_make(0.f);
+    df un = S ? f2df(FS[2 * P2 + ti]) : df_make(0.f);
+    const df q3 = S ? f2df(FS[3 * P2 + ti]) : df_make(0.f);
     df dno, dnn, dA, sig;
     df go1, go2, gn1, gn2;  // tangential test-slope factors, both sides
     df gvD, gnD;            // normal ones
     if constexpr (!CURVED) {
       const float sgn = S ? 1.f : -1.f;
-      const df w2 = df_make(t.wh[ta], t.wl[ta]) * df_make(t.wh[tb], t.wl[tb]);
+      const df w2 = f2df(t.w[ta]) * f2df(t.w[tb]);
       dA = w2 * a.fa[D];
       sig = a.sg[D];
       const df nsc = df_make(sgn * a.ns[D].h, sgn * a.ns[D].l);
@@ -405,15 +412,12 @@ __device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
       dA = ld(a.fdh, a.fdl, fb);
       sig = df_make(a.sgh[f], a.sgl[f]);
       // reference tangential slopes of the own trace
-      dacc s1o = acc_first(t.Dh[ta * P], t.Dl[ta * P], FSh[P * tb],
-                           FSl[P * tb]);
-      dacc s2o = acc_first(t.Dh[tb * P], t.Dl[tb * P], FSh[ta], FSl[ta]);
+      dacc s1o = acc_first(t.D[ta * P], FS[P * tb]);
+      dacc s2o = acc_first(t.D[tb * P], FS[ta]);
       MFP_DF_LOOP
       for (int j = 1; j < P; ++j) {
-        acc_mac(s1o, t.Dh[ta * P + j], t.Dl[ta * P + j], FSh[j + P * tb],
-                FSl[j + P * tb]);
-        acc_mac(s2o, t.Dh[tb * P + j], t.Dl[tb * P + j], FSh[ta + P * j],
-                FSl[ta + P * j]);
+        acc_mac(s1o, t.D[ta * P + j], FS[j + P * tb]);
+        acc_mac(s2o, t.D[tb * P + j], FS[ta + P * j]);
       }
       const df t1o = acc_get(s1o), t2o = acc_get(s2o);
       // J^-1 n of the lower (L) and upper (R) cell, face-local components
@@ -425,16 +429,12 @@ __device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
                  L1 = ld(a.fdh, a.fdl, fb + (1 + T1) * P2),
                  L2 = ld(a.fdh, a.fdl, fb + (1 + T2) * P2);
         // and of the neighbour's trace
-        dacc s1n = acc_first(t.Dh[ta * P], t.Dl[ta * P],
-                             FSh[2 * P2 + P * tb], FSl[2 * P2 + P * tb]);
-        dacc s2n = acc_first(t.Dh[tb * P], t.Dl[tb * P], FSh[2 * P2 + ta],
-                             FSl[2 * P2 + ta]);
+        dacc s1n = acc_first(t.D[ta * P], FS[2 * P2 + P * tb]);
+        dacc s2n = acc_first(t.D[tb * P], FS[2 * P2 + ta]);
         MFP_DF_LOOP
         for (int j = 1; j < P; ++j) {
-          acc_mac(s1n, t.Dh[ta * P + j], t.Dl[ta * P + j],
-                  FSh[2 * P2 + j + P * tb], FSl[2 * P2 + j + P * tb]);
-          acc_mac(s2n, t.Dh[tb * P + j], t.Dl[tb * P + j],
-                  FSh[2 * P2 + ta + P * j], FSl[2 * P2 + ta + P * j]);
+          acc_mac(s1n, t.D[ta * P + j], FS[2 * P2 + j + P * tb]);
+          acc_mac(s2n, t.D[tb * P + j], FS[2 * P2 + ta + P * j]);
         }
         dacc sa = acc_first(LD.h, LD.l, so.h, so.l);
         acc_mac(sa, L1.h, L1.l, t1o.h, t1o.l);
@@ -472,11 +472,11 @@ __device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
     c0o = cg * gvD;
     c0n = cg * gnD;
     if constexpr (CURVED) {
-      stv(FSh, FSl, 4 * P2 + ti, cg * go1);
-      stv(FSh, FSl, 5 * P2 + ti, cg * go2);
+      st2(FS, 4 * P2 + ti, cg * go1);
+      st2(FS, 5 * P2 + ti, cg * go2);
       if constexpr (S == 1) {
-        stv(FSh, FSl, 6 * P2 + ti, cg * gn1);
-        stv(FSh, FSl, 7 * P2 + ti, cg * gn2);
+        st2(FS, 6 * P2 + ti, cg * gn1);
+        st2(FS, 7 * P2 + ti, cg * gn2);
       }
     }
   }
@@ -492,15 +492,11 @@ __device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
     sb.l = vn.l;
     MFP_DF_LOOP
     for (int j = 0; j < P; ++j) {
-      acc_mac(sa, t.Dh[j * P + ta], t.Dl[j * P + ta],
-              FSh[4 * P2 + j + P * tb], FSl[4 * P2 + j + P * tb]);
-      acc_mac(sa, t.Dh[j * P + tb], t.Dl[j * P + tb],
-              FSh[5 * P2 + ta + P * j], FSl[5 * P2 + ta + P * j]);
+      acc_mac(sa, t.D[j * P + ta], FS[4 * P2 + j + P * tb]);
+      acc_mac(sa, t.D[j * P + tb], FS[5 * P2 + ta + P * j]);
       if constexpr (S == 1) {
-        acc_mac(sb, t.Dh[j * P + ta], t.Dl[j * P + ta],
-                FSh[6 * P2 + j + P * tb], FSl[6 * P2 + j + P * tb]);
-        acc_mac(sb, t.Dh[j * P + tb], t.Dl[j * P + tb],
-                FSh[7 * P2 + ta + P * j], FSl[7 * P2 + ta + P * j]);
+        acc_mac(sb, t.D[j * P + ta], FS[6 * P2 + j + P * tb]);
+        acc_mac(sb, t.D[j * P + tb], FS[7 * P2 + ta + P * j]);
       }
     }
     vo = acc_get(sa);
@@ -512,38 +508,36 @@ __device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
     for (int l = 0; l < P; ++l) {
       const int j = n0 + l * ls;
       dacc s;
-      s.h = Ah[j];
-      s.l = Al[j];
+      s.h = A[j].x;
+      s.l = A[j].y;
       acc_mac(s, gvh[l], gvl[l], vo.h, vo.l);
       acc_mac(s, gdh[l], gdl[l], c0o.h, c0o.l);
-      stv(Ah, Al, j, acc_get(s));
+      st2(A, j, acc_get(s));
     }
   }
   // the neighbour's test terms to its face nodes: S^T along a, then b
   if constexpr (S == 1) {
-    stv(FSh, FSl, 0 * P2 + ti, vn);
-    stv(FSh, FSl, 1 * P2 + ti, c0n);
+    st2(FS, 0 * P2 + ti, vn);
+    st2(FS, 1 * P2 + ti, c0n);
     __syncthreads();
 #pragma unroll 1
     for (int arr = 0; arr < 2; ++arr) {
-      const float* ih = FSh + arr * P2 + P * tb;
-      const float* il = FSl + arr * P2 + P * tb;
-      dacc s = acc_first(t.Sh[ta], t.Sl[ta], ih[0], il[0]);
+      const float2* iv = FS + arr * P2 + P * tb;
+      dacc s = acc_first(t.S[ta], iv[0]);
 #pragma unroll
       for (int j = 1; j < P; ++j)
-        acc_mac(s, t.Sh[j * P + ta], t.Sl[j * P + ta], ih[j], il[j]);
-      stv(FSh, FSl, (4 + arr) * P2 + ti, acc_get(s));
+        acc_mac(s, t.S[j * P + ta], iv[j]);
+      st2(FS, (4 + arr) * P2 + ti, acc_get(s));
     }
     __syncthreads();
     df res[2];
 #pragma unroll
     for (int arr = 0; arr < 2; ++arr) {
-      const float* ih = FSh + (4 + arr) * P2 + ta;
-      const float* il = FSl + (4 + arr) * P2 + ta;
-      dacc s = acc_first(t.Sh[tb], t.Sl[tb], ih[0], il[0]);
+      const float2* iv = FS + (4 + arr) * P2 + ta;
+      dacc s = acc_first(t.S[tb], iv[0]);
 #pragma unroll
       for (int j = 1; j < P; ++j)
-        acc_mac(s, t.Sh[j * P + tb], t.Sl[j * P + tb], ih[P * j], il[P * j]);
+        acc_mac(s, t.S[j * P + tb], iv[P * j]);
       res[arr] = acc_get(s);
     }
     if (pair) {
@@ -557,13 +551,12 @@ __device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
 template <int P, bool CURVED>
 __device__ __noinline__ void df_face_lower_gp(const ApplyArgsDF& a, int col,
                                               int D, bool active, int cx,
-                                              int cy, int cz, const float* Uh,
-                                              const float* Ul, float* Ah,
-                                              float* Al, float* FSh,
-                                              float* FSl, const float* tabs,
+                                              int cy, int cz, const float2* U,
+                                              float2* A, float2* FS,
+                                              const float2* tabs,
                                               int ta, int tb) {
-  df_face_gp<P, CURVED, 0>(a, col, D, active, cx, cy, cz, Uh, Ul, Ah, Al, FSh,
-                           FSl, make_shdf<P>(tabs), ta, tb);
+  df_face_gp<P, CURVED, 0>(a, col, D, active, cx, cy, cz, U, A, FS,
+                           make_shdf<P>(tabs), ta, tb);
   __syncthreads();
 }
 
@@ -589,7 +582,7 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
     k_apply_df(const __grid_constant__ ApplyArgsDF a) {
   constexpr int P2 = P * P, P3 = P2 * P;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float* sm = reinterpret_cast<float*>(smraw);
+  float2* sm = reinterpret_cast<float2*>(smraw);
   const int cpb = a.cpb, nc = a.ncols;
   const int items = cpb * nc * P2;
   const int tid = threadIdx.x;
@@ -599,34 +592,25 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
   const int ta = rest % P, tb = (rest / P) % P;
   const int lc = item_ok ? rest / P2 : 0;
   const int v = item_ok ? lc * nc + rr : cpb * nc;
-  float* base = sm + (size_t)v * df_cell_floats<P, DG>();
-  float* Ah = base;
-  float* Al = base + P3;
-  float* Xh = base + 2 * P3;  // GX
-  float* Xl = base + 3 * P3;
-  float* Yh = base + 4 * P3;  // GY
-  float* Yl = base + 5 * P3;
-  float* Uh = base + 6 * P3;  // DG: values at the Gauss points
-  float* Ul = base + 7 * P3;
-  float* FSh = base + 8 * P3;
-  float* FSl = FSh + 8 * P2;
-  float* tabs = sm + (size_t)(cpb * nc + 1) * df_cell_floats<P, DG>();
+  float2* base = sm + (size_t)v * df_cell_pairs<P, DG>();
+  float2* A = base;
+  float2* X = base + P3;      // GX
+  float2* Y = base + 2 * P3;  // GY
+  float2* U = base + 3 * P3;  // DG: values at the Gauss points
+  float2* FS = base + 4 * P3;
+  float2* tabs = sm + (size_t)(cpb * nc + 1) * df_cell_pairs<P, DG>();
   const ShDF t = make_shdf<P>(tabs);
   {
-    float* p = tabs + 4 * P2;
+    const DevTabDF& T = c_tabdf[P - 2];
     for (int i = tid; i < P2; i += blockDim.x) {
-      tabs[i] = c_tabdf[P - 2].Sh[i];
-      tabs[P2 + i] = c_tabdf[P - 2].Sl[i];
-      tabs[2 * P2 + i] = c_tabdf[P - 2].Dh[i];
-      tabs[3 * P2 + i] = c_tabdf[P - 2].Dl[i];
+      tabs[i] = make_float2(T.Sh[i], T.Sl[i]);
+      tabs[P2 + i] = make_float2(T.Dh[i], T.Dl[i]);
     }
+    float2* p = tabs + 2 * P2;
     for (int i = tid; i < P; i += blockDim.x) {
-      p[i] = c_tabdf[P - 2].d0h[i];
-      p[P + i] = c_tabdf[P - 2].d0l[i];
-      p[2 * P + i] = c_tabdf[P - 2].d1h[i];
-      p[3 * P + i] = c_tabdf[P - 2].d1l[i];
-      p[4 * P + i] = c_tabdf[P - 2].wh[i];
-      p[5 * P + i] = c_tabdf[P - 2].wl[i];
+      p[i] = make_float2(T.d0h[i], T.d0l[i]);
+      p[P + i] = make_float2(T.d1h[i], T.d1l[i]);
+      p[2 * P + i] = make_float2(T.wh[i], T.wl[i]);
     }
   }
   __syncthreads();
@@ -635,7 +619,7 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
   // Cartesian quadrature weights times |K|/h_d^2 for this thread's (x, y)
   df wg[3];
   if constexpr (!CURVED) {
-    const df wab = ld(t.wh, t.wl, ta) * ld(t.wh, t.wl, tb);
+    const df wab = f2df(t.w[ta]) * f2df(t.w[tb]);
 #pragma unroll
     for (int d = 0; d < 3; ++d) wg[d] = wab * a.gs[d];
   }
@@ -674,27 +658,26 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
       }
     }
     // ---- values at Gauss points: z (registers), y, x
-    dsweep<P, DF_S, false, false>(rh, rl, Ah, Al, dx3<P>(ta, tb, 0), P2);
+    dsweep<P, DF_S, false, false>(rh, rl, A, dx3<P>(ta, tb, 0), P2);
     __syncthreads();
-    dline<P>(Ah, Al, dx3<P>(ta, 0, tb), P, rh, rl);
-    dsweep<P, DF_S, false, false>(rh, rl, Ah, Al, dx3<P>(ta, 0, tb), P);
+    dline<P>(A, dx3<P>(ta, 0, tb), P, rh, rl);
+    dsweep<P, DF_S, false, false>(rh, rl, A, dx3<P>(ta, 0, tb), P);
     __syncthreads();
-    dline<P>(Ah, Al, dx3<P>(0, ta, tb), 1, rh, rl);
-    dsweep<P, DF_S, false, false>(rh, rl, Ah, Al, dx3<P>(0, ta, tb), 1);
-    dline<P>(Ah, Al, dx3<P>(0, ta, tb), 1, rh, rl);  // own line
+    dline<P>(A, dx3<P>(0, ta, tb), 1, rh, rl);
+    dsweep<P, DF_S, false, false>(rh, rl, A, dx3<P>(0, ta, tb), 1);
+    dline<P>(A, dx3<P>(0, ta, tb), 1, rh, rl);  // own line
     if constexpr (DG) {  // values at the Gauss points for the face terms
 #pragma unroll
       for (int j = 0; j < P; ++j) {
-        Uh[dx3<P>(j, ta, tb)] = rh[j];
-        Ul[dx3<P>(j, ta, tb)] = rl[j];
+        U[dx3<P>(j, ta, tb)] = make_float2(rh[j], rl[j]);
       }
     }
-    dsweep<P, DF_D, false, false>(rh, rl, Xh, Xl, dx3<P>(0, ta, tb), 1);
+    dsweep<P, DF_D, false, false>(rh, rl, X, dx3<P>(0, ta, tb), 1);
     __syncthreads();
     // ---- reference gradient: y into GY, z kept in registers
-    dline<P>(Ah, Al, dx3<P>(ta, 0, tb), P, rh, rl);
-    dsweep<P, DF_D, false, false>(rh, rl, Yh, Yl, dx3<P>(ta, 0, tb), P);
-    dline<P>(Ah, Al, dx3<P>(ta, tb, 0), P2, rh, rl);  // z-line of values
+    dline<P>(A, dx3<P>(ta, 0, tb), P, rh, rl);
+    dsweep<P, DF_D, false, false>(rh, rl, Y, dx3<P>(ta, 0, tb), P);
+    dline<P>(A, dx3<P>(ta, tb, 0), P2, rh, rl);  // z-line of values
     __syncthreads();
     // ---- quadrature-point operation t = kappa G_q grad u (Eq. 12), the z
     // derivative taken at each point from the z-line in registers
@@ -708,7 +691,7 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
         for (int j = 1; j < P; ++j)
           acc_mac(dz, tdh<P, DF_D>(qz * P + j), tdl<P, DF_D>(qz * P + j),
                   rh[j], rl[j]);
-        const df ux = ld(Xh, Xl, q), uy = ld(Yh, Yl, q), uz = acc_get(dz);
+        const df ux = f2df(X[q]), uy = f2df(Y[q]), uz = acc_get(dz);
         df tx, ty, tz;
         if constexpr (CURVED) {
           const size_t gb = (size_t)cc * 6 * P3 + q;
@@ -730,7 +713,7 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
           ty = acc_get(sy);
           tz = acc_get(sz);
         } else {
-          const df wz = ld(t.wh, t.wl, qz);
+          const df wz = f2df(t.w[qz]);
           tx = (wg[0] * wz) * ux;
           ty = (wg[1] * wz) * uy;
           tz = (wg[2] * wz) * uz;
@@ -745,20 +728,20 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
           ty = a.kappa * ty;
           tz = a.kappa * tz;
         }
-        stv(Xh, Xl, q, tx);
-        stv(Yh, Yl, q, ty);
-        stv(Ah, Al, q, tz);
+        st2(X, q, tx);
+        st2(Y, q, ty);
+        st2(A, q, tz);
       }
-      dline<P>(Ah, Al, dx3<P>(ta, tb, 0), P2, rh, rl);  // own z-line
-      dsweep<P, DF_D, true, false>(rh, rl, Ah, Al, dx3<P>(ta, tb, 0), P2);
+      dline<P>(A, dx3<P>(ta, tb, 0), P2, rh, rl);  // own z-line
+      dsweep<P, DF_D, true, false>(rh, rl, A, dx3<P>(ta, tb, 0), P2);
     }
     __syncthreads();
     // ---- transposed derivative y (added), x (added) then S^T x, y, z
-    dline<P>(Yh, Yl, dx3<P>(ta, 0, tb), P, rh, rl);
-    dsweep<P, DF_D, true, true>(rh, rl, Ah, Al, dx3<P>(ta, 0, tb), P);
+    dline<P>(Y, dx3<P>(ta, 0, tb), P, rh, rl);
+    dsweep<P, DF_D, true, true>(rh, rl, A, dx3<P>(ta, 0, tb), P);
     __syncthreads();
-    dline<P>(Xh, Xl, dx3<P>(0, ta, tb), 1, rh, rl);
-    dsweep<P, DF_D, true, true>(rh, rl, Ah, Al, dx3<P>(0, ta, tb), 1);
+    dline<P>(X, dx3<P>(0, ta, tb), 1, rh, rl);
+    dsweep<P, DF_D, true, true>(rh, rl, A, dx3<P>(0, ta, tb), 1);
     if constexpr (DG) {
       // ---- SIPG face terms (Eq. 6, Eq. 7), added at the Gauss points
       __syncthreads();
@@ -767,20 +750,20 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
         // lower faces only where a cell of the block lies on the boundary
         const int cD = D == 0 ? cx : (D == 1 ? cy : cz);
         if (__syncthreads_or(active && cD == 0))
-          df_face_lower_gp<P, CURVED>(a, col, D, active, cx, cy, cz, Uh, Ul,
-                                      Ah, Al, FSh, FSl, tabs, ta, tb);
-        df_face_gp<P, CURVED, 1>(a, col, D, active, cx, cy, cz, Uh, Ul, Ah, Al,
-                                 FSh, FSl, t, ta, tb);
+          df_face_lower_gp<P, CURVED>(a, col, D, active, cx, cy, cz, U, A, FS,
+                                      tabs, ta, tb);
+        df_face_gp<P, CURVED, 1>(a, col, D, active, cx, cy, cz, U, A, FS, t,
+                                 ta, tb);
       }
       __syncthreads();
     }
-    dline<P>(Ah, Al, dx3<P>(0, ta, tb), 1, rh, rl);  // own line
-    dsweep<P, DF_S, true, false>(rh, rl, Ah, Al, dx3<P>(0, ta, tb), 1);
+    dline<P>(A, dx3<P>(0, ta, tb), 1, rh, rl);  // own line
+    dsweep<P, DF_S, true, false>(rh, rl, A, dx3<P>(0, ta, tb), 1);
     __syncthreads();
-    dline<P>(Ah, Al, dx3<P>(ta, 0, tb), P, rh, rl);
-    dsweep<P, DF_S, true, false>(rh, rl, Ah, Al, dx3<P>(ta, 0, tb), P);
+    dline<P>(A, dx3<P>(ta, 0, tb), P, rh, rl);
+    dsweep<P, DF_S, true, false>(rh, rl, A, dx3<P>(ta, 0, tb), P);
     __syncthreads();
-    dline<P>(Ah, Al, dx3<P>(ta, tb, 0), P2, rh, rl);
+    dline<P>(A, dx3<P>(ta, tb, 0), P2, rh, rl);
     // ---- S^T along z and scatter (float64)
     if constexpr (!DG) {
       dmtv<P, DF_S>(rh, rl, oh, ol);
@@ -802,13 +785,13 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
       }
       __syncthreads();
     } else {
-      dsweep<P, DF_S, true, false>(rh, rl, Ah, Al, dx3<P>(ta, tb, 0), P2);
+      dsweep<P, DF_S, true, false>(rh, rl, A, dx3<P>(ta, tb, 0), P2);
       if (active) {
 #pragma unroll
         for (int z = 0; z < P; ++z) {
           const size_t gi = (size_t)cc * P3 + dx3<P>(ta, tb, z);
           a.dst[gi * a.stride + col] =
-              df_to_double(ld(Ah, Al, dx3<P>(ta, tb, z)));
+              df_to_double(f2df(A[dx3<P>(ta, tb, z)]));
         }
       }
       __syncthreads();
@@ -884,9 +867,9 @@ __global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
 
 template <int P, bool DG>
 size_t df_smem_bytes(int cpb, int ncols) {
-  return ((size_t)(cpb * ncols + 1) * df_cell_floats<P, DG>() +
-          df_table_floats<P>()) *
-         sizeof(float);
+  return ((size_t)(cpb * ncols + 1) * df_cell_pairs<P, DG>() +
+          df_table_pairs<P>()) *
+         sizeof(float2);
 }
 
 // Resident blocks per SM of a launch shape (cached per shape).
