@@ -684,11 +684,20 @@ __global__ void __launch_bounds__(kDenseRows)
   const int ks = blockIdx.y, r = blockIdx.z;
   const int j0 = (int)((int64_t)n * ks / kDenseSplit);
   const int j1 = (int)((int64_t)n * (ks + 1) / kDenseSplit);
-  T s = T(0);
-  if (i < n)
-    for (int j = j0; j < j1; ++j)
-      s = fma(A[(size_t)j * n + i], x[(size_t)j * R + r], s);
-  if (i < n) part[((size_t)ks * R + r) * n + i] = (double)s;
+  // four independent partial sums keep several loads in flight
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  if (i < n) {
+    int j = j0;
+    for (; j + 3 < j1; j += 4) {
+      s0 = fma(A[(size_t)j * n + i], x[(size_t)j * R + r], s0);
+      s1 = fma(A[(size_t)(j + 1) * n + i], x[(size_t)(j + 1) * R + r], s1);
+      s2 = fma(A[(size_t)(j + 2) * n + i], x[(size_t)(j + 2) * R + r], s2);
+      s3 = fma(A[(size_t)(j + 3) * n + i], x[(size_t)(j + 3) * R + r], s3);
+    }
+    for (; j < j1; ++j)
+      s0 = fma(A[(size_t)j * n + i], x[(size_t)j * R + r], s0);
+    part[((size_t)ks * R + r) * n + i] = (double)((s0 + s1) + (s2 + s3));
+  }
   __shared__ bool last;
   __threadfence();
   __syncthreads();

@@ -121,7 +121,7 @@ constexpr int kMaxRedBlocks = 1024;
 constexpr int kMaxRhs = 256;
 constexpr int kDenseMax = 2048;   // dofs of a coarsest level stored dense
 constexpr int kDenseRows = 128;   // rows per block of k_dense_apply
-constexpr int kDenseSplit = 16;   // column ranges per row block
+constexpr int kDenseSplit = 32;   // column ranges per row block
 struct RedScratch {
   double* part = nullptr;  // [kMaxRedBlocks][R]
   unsigned* cnt = nullptr; // zero between launches
