@@ -4,9 +4,16 @@
 // (Eq. 6, Eq. 7) as k_apply.cuh, with float64 vectors in HBM and every
 // intermediate carried as a double-float pair (df.cuh).  On GB300 the FP64
 // pipe issues 2 DFMA per clock per SM while the FP32 pipe issues 128 FFMA;
-// a double-float multiply-add costs 11 FP32 instructions, so the FP32 pipe
-// delivers about 5x the FP64 rate at about 48 significant bits.  Only the
-// conversions of the float64 inputs and outputs use the FP64 pipe.
+// a double-float multiply-accumulate costs 12 FP32 instructions, so the FP32
+// pipe delivers about 5x the FP64 rate at about 48 significant bits.  Only
+// the conversions of the float64 inputs and outputs use the FP64 pipe.
+//
+// Per cell: gather, interpolation to the Gauss points (S along z, y, x,
+// even-odd split for p >= 4), collocation derivatives, the quadrature-point
+// operation, the transposed derivatives, then (SIPG) the face terms added at
+// the Gauss points (df_face_gp: each interior face once, by the cell below
+// it; the upper neighbour's share through the face buffer and
+// k_dg_face_add), then S^T along x, y, z and the store (CG: atomic scatter).
 #pragma once
 
 #define MFP_DF_TABLES
@@ -65,10 +72,6 @@ __device__ __forceinline__ void acc_mac(dacc& s, float ah, float al,
 __device__ __forceinline__ df ld(const float* h, const float* l, int i) {
   return df_make(h[i], l[i]);
 }
-__device__ __forceinline__ void stv(float* h, float* l, int i, df v) {
-  h[i] = v.h;
-  l[i] = v.l;
-}
 
 enum DfTab { DF_S, DF_D };
 
@@ -81,22 +84,6 @@ template <int P, int W>
 __device__ __forceinline__ float tdl(int i) {
   if constexpr (W == DF_S) return c_tabdf[P - 2].Sl[i];
   return c_tabdf[P - 2].Dl[i];
-}
-
-// out[q] = sum_j M[q][j] in[j]
-template <int P, int W>
-__device__ __forceinline__ void dmv(const float (&ih)[P], const float (&il)[P],
-                                    float (&oh)[P], float (&ol)[P]) {
-#pragma unroll
-  for (int q = 0; q < P; ++q) {
-    dacc s = acc_first(tdh<P, W>(q * P), tdl<P, W>(q * P), ih[0], il[0]);
-#pragma unroll
-    for (int j = 1; j < P; ++j)
-      acc_mac(s, tdh<P, W>(q * P + j), tdl<P, W>(q * P + j), ih[j], il[j]);
-    const df r = acc_get(s);
-    oh[q] = r.h;
-    ol[q] = r.l;
-  }
 }
 
 // out[j] = sum_q M[q][j] in[q]
@@ -241,12 +228,6 @@ __device__ __forceinline__ void dline(const float2* x, int base, int st,
 template <int P>
 __device__ __forceinline__ int dx3(int x, int y, int z) {
   return x + P * (y + P * z);
-}
-template <int P, int D>
-__device__ __forceinline__ int dfnode(int l, int a, int b) {
-  if constexpr (D == 0) return l + P * (a + P * b);
-  if constexpr (D == 1) return a + P * (l + P * b);
-  return a + P * (b + P * l);
 }
 
 // Shared memory holds double-float values as float2 (hi, lo): one 64-bit
