@@ -105,7 +105,10 @@ void mfp_desc_default(mfp_desc* desc);
 
 /* Create a context on the current CUDA device: builds every multigrid level
  * (geometry at quadrature points, inverse Jacobi diagonal, eigenvalue
- * estimates and Chebyshev parameters; Sec. 4.1 "setup").  Synchronises
+ * estimates and Chebyshev parameters; Sec. 4.1 "setup").  With more than
+ * one level and at most 2048 dofs on the coarsest level, that level's
+ * operator is also assembled once as a dense matrix (from matrix-free
+ * applies to identity columns) for the coarse Chebyshev solve.  Synchronises
  * `stream`.  *out receives an opaque handle owned by the library. */
 mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out);
 
@@ -167,7 +170,13 @@ mfp_status mfp_rhs_noalloc(mfp_ctx* ctx, int f_kind, const double* params_host,
  * identity rows / columns for CG Dirichlet nodes).  prec MFP_FP64 takes
  * double vectors, MFP_FP32 float vectors (FP32 level data must exist, i.e.
  * mg_precision FP32).  n_rhs = R >= 1 applies to R right-hand sides in the
- * batched layout in one launch.  src and dst must not alias. */
+ * batched layout; CG is one launch, SIPG one cell-kernel launch plus one
+ * launch that adds the face terms each cell left for its upper neighbours
+ * in a per-level face buffer (grown on first use with more columns, so the
+ * first apply with a new maximum R allocates and must not be inside a stream
+ * capture).  The result does not depend on launch shapes (no atomics for
+ * SIPG).  Applies of one level share that buffer and scratch: issue them in
+ * stream order.  src and dst must not alias. */
 mfp_status mfp_apply(mfp_ctx* ctx, int level, int prec, const void* src_dev,
                      void* dst_dev, int n_rhs, void* stream);
 
