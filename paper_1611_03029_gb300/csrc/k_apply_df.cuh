@@ -23,7 +23,7 @@
 // Resident blocks per SM the register allocation must allow (blocks of at
 // most 128 threads for p <= 5, 256 above), measured on 24^3..64^3 meshes
 // for k = 2..8: more resident warps hide the latency of the shared-memory
-// sweeps and the gathers, down to about 85 registers per thread; CG p >= 7
+// sweeps and the gathers, down to about 73 registers per thread; CG p >= 7
 // keeps its larger line arrays in registers.  MFP_DF_MIN_BLOCKS overrides
 // the table for experiments.
 #ifndef MFP_DF_MIN_BLOCKS
@@ -232,11 +232,21 @@ __device__ __forceinline__ int dx3(int x, int y, int z) {
 
 // Shared memory holds double-float values as float2 (hi, lo): one 64-bit
 // access per value.  Per virtual cell, in float2 units: A, X, Y (and U for
-// SIPG) of p^3 values, the SIPG face scratch of 8 p^2; the odd stride puts
-// the columns of a batch into distinct banks.
+// SIPG) of p^3 values and the SIPG face scratch of 8 p^2, which for p >= 4
+// reuses X and Y (dead while the faces run); the odd stride puts the
+// columns of a batch into distinct banks.
+#ifndef MFP_DF_FS_ALIAS
+#define MFP_DF_FS_ALIAS 1
+#endif
+template <int P>
+__host__ __device__ constexpr bool df_fs_alias() {
+  return MFP_DF_FS_ALIAS && 2 * P >= 8;
+}
 template <int P, bool DG>
 __host__ __device__ constexpr int df_cell_pairs() {
-  return ((DG ? 4 : 3) * P * P * P + (DG ? 8 * P * P : 0)) | 1;
+  return ((DG ? 4 : 3) * P * P * P +
+          (DG && !df_fs_alias<P>() ? 8 * P * P : 0)) |
+         1;
 }
 template <int P>
 __host__ __device__ constexpr int df_table_pairs() {
@@ -546,7 +556,7 @@ constexpr int df_max_threads() { return P <= 5 ? 128 : 256; }
 template <int P, bool DG>
 constexpr int df_min_blocks() {
   if (MFP_DF_MIN_BLOCKS > 0) return MFP_DF_MIN_BLOCKS;
-  if (DG) return P <= 3 ? 5 : (P <= 5 ? 6 : 2);
+  if (DG) return P <= 3 ? 5 : (P <= 5 ? 7 : 2);
   return P <= 5 ? 8 : (P == 6 ? 3 : 1);
 }
 
@@ -578,7 +588,7 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
   float2* X = base + P3;      // GX
   float2* Y = base + 2 * P3;  // GY
   float2* U = base + 3 * P3;  // DG: values at the Gauss points
-  float2* FS = base + 4 * P3;
+  float2* FS = df_fs_alias<P>() ? X : base + 4 * P3;
   float2* tabs = sm + (size_t)(cpb * nc + 1) * df_cell_pairs<P, DG>();
   const ShDF t = make_shdf<P>(tabs);
   {
