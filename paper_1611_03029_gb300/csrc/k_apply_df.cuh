@@ -648,14 +648,31 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
         rl[z] = u.l;
       }
     }
-    // ---- values at Gauss points: z (registers), y, x
-    dsweep<P, DF_S, false, false>(rh, rl, A, dx3<P>(ta, tb, 0), P2);
-    __syncthreads();
-    dline<P>(A, dx3<P>(ta, 0, tb), P, rh, rl);
-    dsweep<P, DF_S, false, false>(rh, rl, A, dx3<P>(ta, 0, tb), P);
-    __syncthreads();
-    dline<P>(A, dx3<P>(0, ta, tb), 1, rh, rl);
-    dsweep<P, DF_S, false, false>(rh, rl, A, dx3<P>(0, ta, tb), 1);
+    // ---- values at Gauss points: S along z, y, x (one copy of the sweep
+    // code for p >= 4: line (base, stride) of the thread per direction)
+    if constexpr (P >= 4 && MFP_DF_ROLL) {
+#pragma unroll
+      for (int j = 0; j < P; ++j)
+        A[dx3<P>(ta, tb, j)] = make_float2(rh[j], rl[j]);
+#pragma unroll 1
+      for (int d = 2; d >= 0; --d) {
+        const int b0 = d == 2   ? dx3<P>(ta, tb, 0)
+                       : d == 1 ? dx3<P>(ta, 0, tb)
+                                : dx3<P>(0, ta, tb);
+        const int st = d == 2 ? P2 : (d == 1 ? P : 1);
+        if (d < 2) __syncthreads();
+        dline<P>(A, b0, st, rh, rl);
+        dsweep<P, DF_S, false, false>(rh, rl, A, b0, st);
+      }
+    } else {
+      dsweep<P, DF_S, false, false>(rh, rl, A, dx3<P>(ta, tb, 0), P2);
+      __syncthreads();
+      dline<P>(A, dx3<P>(ta, 0, tb), P, rh, rl);
+      dsweep<P, DF_S, false, false>(rh, rl, A, dx3<P>(ta, 0, tb), P);
+      __syncthreads();
+      dline<P>(A, dx3<P>(0, ta, tb), 1, rh, rl);
+      dsweep<P, DF_S, false, false>(rh, rl, A, dx3<P>(0, ta, tb), 1);
+    }
     dline<P>(A, dx3<P>(0, ta, tb), 1, rh, rl);  // own line
     if constexpr (DG) {  // values at the Gauss points for the face terms
 #pragma unroll
@@ -748,13 +765,33 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
       }
       __syncthreads();
     }
-    dline<P>(A, dx3<P>(0, ta, tb), 1, rh, rl);  // own line
-    dsweep<P, DF_S, true, false>(rh, rl, A, dx3<P>(0, ta, tb), 1);
-    __syncthreads();
-    dline<P>(A, dx3<P>(ta, 0, tb), P, rh, rl);
-    dsweep<P, DF_S, true, false>(rh, rl, A, dx3<P>(ta, 0, tb), P);
-    __syncthreads();
-    dline<P>(A, dx3<P>(ta, tb, 0), P2, rh, rl);
+    // ---- S^T along x, y (and z for SIPG), one copy of the sweep for p >= 4
+    if constexpr (P >= 4 && MFP_DF_ROLL) {
+#pragma unroll 1
+      for (int d = 0; d < (DG ? 3 : 2); ++d) {
+        const int b0 = d == 0   ? dx3<P>(0, ta, tb)
+                       : d == 1 ? dx3<P>(ta, 0, tb)
+                                : dx3<P>(ta, tb, 0);
+        const int st = d == 0 ? 1 : (d == 1 ? P : P2);
+        if (d > 0) __syncthreads();
+        dline<P>(A, b0, st, rh, rl);
+        dsweep<P, DF_S, true, false>(rh, rl, A, b0, st);
+      }
+      if constexpr (!DG) {
+        __syncthreads();
+        dline<P>(A, dx3<P>(ta, tb, 0), P2, rh, rl);
+      }
+    } else {
+      dline<P>(A, dx3<P>(0, ta, tb), 1, rh, rl);  // own line
+      dsweep<P, DF_S, true, false>(rh, rl, A, dx3<P>(0, ta, tb), 1);
+      __syncthreads();
+      dline<P>(A, dx3<P>(ta, 0, tb), P, rh, rl);
+      dsweep<P, DF_S, true, false>(rh, rl, A, dx3<P>(ta, 0, tb), P);
+      __syncthreads();
+      dline<P>(A, dx3<P>(ta, tb, 0), P2, rh, rl);
+      if constexpr (DG)
+        dsweep<P, DF_S, true, false>(rh, rl, A, dx3<P>(ta, tb, 0), P2);
+    }
     // ---- S^T along z and scatter (float64)
     if constexpr (!DG) {
       dmtv<P, DF_S>(rh, rl, oh, ol);
@@ -776,7 +813,6 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
       }
       __syncthreads();
     } else {
-      dsweep<P, DF_S, true, false>(rh, rl, A, dx3<P>(ta, tb, 0), P2);
       if (active) {
 #pragma unroll
         for (int z = 0; z < P; ++z) {
