@@ -131,14 +131,19 @@ class Problem:
     a_cell        optional [ncells, p^3] coefficient at cell quadrature points
     a_face        optional [nfaces, p^2] coefficient at face quadrature points
     penalty_factor  sigma_F = penalty_factor (k+1)^2 / h_F (Sec. 2.2)
-    dirichlet     homogeneous Dirichlet data on the whole boundary; False drops
-                  the constraints (CG) or the boundary faces (DG), which is
-                  only used to test that constants are in the kernel
+    dirichlet     Dirichlet data on the boundary; False drops the constraints
+                  (CG) or the boundary faces (DG), which is only used to test
+                  that constants are in the kernel
+    box           (lo, hi): the domain is [lo, hi]^3, the image of the unit
+                  cube under x -> lo + (hi - lo) x after the mapping above
+    neumann_sides boundary sides with Neumann data (natural for CG, no
+                  operator terms on the SIPG faces, Eq. 7); side 2d is
+                  x_d = lo, side 2d+1 is x_d = hi; the others are Dirichlet
     """
 
     def __init__(self, nx, ny, nz, k, disc="cg", mapping="identity", amp=0.0,
                  kappa=1.0, a_cell=None, a_face=None, penalty_factor=1.0,
-                 dirichlet=True):
+                 dirichlet=True, box=(0.0, 1.0), neumann_sides=()):
         if disc not in ("cg", "dg"):
             raise ValueError(disc)
         self.n = (int(nx), int(ny), int(nz))
@@ -152,6 +157,12 @@ class Problem:
         self.a_face = None if a_face is None else np.asarray(a_face, float)
         self.penalty_factor = float(penalty_factor)
         self.dirichlet = bool(dirichlet)
+        self.box = (float(box[0]), float(box[1]))
+        if not self.box[1] > self.box[0]:
+            raise ValueError("box must have hi > lo")
+        self.neumann = frozenset(int(v) for v in neumann_sides)
+        if not self.neumann <= set(range(6)):
+            raise ValueError("neumann_sides must be in 0..5")
         self.h = tuple(1.0 / n for n in self.n)
         self.ncells = self.n[0] * self.n[1] * self.n[2]
         self.nodes1 = gll_points(self.k)
@@ -189,13 +200,18 @@ class Problem:
         return cx, cy, cz
 
     def phi_map(self, x):
-        """The analytic map of the unit cube onto itself (identity or sine)."""
+        """The analytic map of the unit cube (identity or sine), followed by
+        the affine map onto the box."""
         x = np.asarray(x, float)
-        if self.amp == 0.0:
-            return x.copy()
-        s = (np.sin(np.pi * x[..., 0]) * np.sin(np.pi * x[..., 1])
-             * np.sin(np.pi * x[..., 2]))
-        return x + self.amp * s[..., None]
+        y = x.copy()
+        if self.amp != 0.0:
+            s = (np.sin(np.pi * x[..., 0]) * np.sin(np.pi * x[..., 1])
+                 * np.sin(np.pi * x[..., 2]))
+            y = x + self.amp * s[..., None]
+        lo, hi = self.box
+        if (lo, hi) != (0.0, 1.0):
+            y = lo + (hi - lo) * y
+        return y
 
     def logical_points(self, cells, ref):
         """Unit-cube points of reference coordinates ref [M,3] in `cells`."""
@@ -261,10 +277,12 @@ class Problem:
             return mask
         g = self.grid
         i = np.arange(N)
-        ix, iy, iz = i % g[0], (i // g[0]) % g[1], i // (g[0] * g[1])
-        mask |= (ix == 0) | (ix == g[0] - 1)
-        mask |= (iy == 0) | (iy == g[1] - 1)
-        mask |= (iz == 0) | (iz == g[2] - 1)
+        idx = (i % g[0], (i // g[0]) % g[1], i // (g[0] * g[1]))
+        for d in range(3):
+            if 2 * d not in self.neumann:
+                mask |= idx[d] == 0
+            if 2 * d + 1 not in self.neumann:
+                mask |= idx[d] == g[d] - 1
         return mask
 
     def node_points(self):
@@ -389,7 +407,7 @@ def face_operators(prob, d, faces=None):
         side = np.where(left[~inner] >= 0, 1.0, -1.0)
         for s in (1.0, -1.0):
             sel = side == s
-            if not sel.any():
+            if not sel.any() or (2 * d + (s > 0)) in prob.neumann:
                 continue
             cs, fs = cells[sel], fb[sel]
             sd = _side_data(prob, cs, d, s)
@@ -502,3 +520,90 @@ def sine_solution(x):
 def sine_forcing(x):
     """f = 3 pi^2 sin sin sin = -Laplace(u) for kappa = 1."""
     return 3.0 * np.pi ** 2 * sine_solution(x)
+
+
+# --------------------------------------------------------------------------
+# Inhomogeneous boundary data (Eq. 7 and its continuous counterpart):
+# Dirichlet values g_D and Neumann fluxes g_N = kappa grad u . n (outward)
+# of a manufactured solution, moved to the right-hand side
+# --------------------------------------------------------------------------
+def _boundary_side(prob, d, s):
+    """Cells on boundary side x_d = lo (s = -1) or hi (s = +1) and their
+    face data at the face Gauss points (values, physical gradients, outward
+    normal, area element, points)."""
+    cx, cy, cz = prob.cell_coords(np.arange(prob.ncells))
+    c = (cx, cy, cz)[d]
+    cells = np.nonzero(c == (prob.n[d] - 1 if s > 0 else 0))[0]
+    return cells, _side_data(prob, cells, d, float(s))
+
+
+def neumann_vector(prob, grad_u):
+    """b_i = sum over Neumann sides of int kappa grad u . n phi_i ds
+    (natural boundary condition; SIPG: the extension of Eq. 7 leaves only
+    this data term on a Neumann face)."""
+    b = np.zeros(prob.n_dofs)
+    for side in sorted(prob.neumann):
+        d, s = side // 2, (1 if side % 2 else -1)
+        cells, sd = _boundary_side(prob, d, s)
+        faces = _boundary_face_ids(prob, d, s, cells)
+        kap = prob.kappa_face(faces)
+        gn = np.einsum("cmd,cmd->cm", grad_u(sd["x"]), sd["n"])
+        be = (kap * gn * sd["dA"]) @ sd["val"]
+        np.add.at(b, prob.dof_map(cells).ravel(), be.ravel())
+    return b
+
+
+def _boundary_face_ids(prob, d, s, cells):
+    cx, cy, cz = prob.cell_coords(cells)
+    fc = [cx, cy, cz]
+    fc[d] = fc[d] + (1 if s > 0 else 0)
+    m = list(prob.n)
+    m[d] += 1
+    off = sum(prob.n_faces_dir(e) for e in range(d))
+    return off + fc[0] + m[0] * (fc[1] + m[1] * fc[2])
+
+
+def sipg_dirichlet_vector(prob, u):
+    """SIPG data terms of the Dirichlet extension u+ = -u- + 2 g_D, grad u+ =
+    grad u- (Eq. 7): with the boundary form of face_terms the known part is
+    kappa dA (-d_n v g_D + 2 sigma v g_D), moved to the right-hand side."""
+    b = np.zeros(prob.n_dofs)
+    pen = prob.penalty_factor * prob.p ** 2
+    for d in range(3):
+        for s in (-1, 1):
+            if (2 * d + (s > 0)) in prob.neumann:
+                continue
+            cells, sd = _boundary_side(prob, d, s)
+            faces = _boundary_face_ids(prob, d, s, cells)
+            kap = prob.kappa_face(faces)
+            sigma = pen * sd["dA"].sum(1) / cell_volumes(prob, cells)
+            gd = u(sd["x"]) * kap * sd["dA"]
+            dn = np.einsum("cmid,cmd->cmi", sd["pg"], sd["n"])
+            be = (-np.einsum("cm,cmi->ci", gd, dn)
+                  + 2.0 * sigma[:, None] * (gd @ sd["val"]))
+            np.add.at(b, prob.dof_map(cells).ravel(), be.ravel())
+    return b
+
+
+def solve_manufactured(prob, f, u, grad_u):
+    """Discrete solution for -div(kappa grad u) = f with the Dirichlet data
+    of u on the Dirichlet sides and the Neumann flux of u on the Neumann
+    sides, by a sparse direct solve.  CG: interpolated Dirichlet values,
+    lifted out of the free rows (Sec. 2.1); SIPG: weakly imposed (Eq. 7)."""
+    import scipy.sparse.linalg as spla
+    b = load_vector(prob, f) + neumann_vector(prob, grad_u)
+    if prob.disc == "dg":
+        b = b + sipg_dirichlet_vector(prob, u)
+        return spla.spsolve(assemble(prob).tocsc(), b)
+    full = Problem(*prob.n, prob.k, disc="cg", mapping=prob.mapping,
+                   amp=prob.amp, kappa=prob.kappa, a_cell=prob.a_cell,
+                   a_face=prob.a_face, dirichlet=False, box=prob.box)
+    A = assemble(full)
+    dmask = prob.constrained()
+    x = np.zeros(prob.n_dofs)
+    x[dmask] = u(prob.node_points()[dmask])
+    free = ~dmask
+    b_full = load_vector(full, f) + neumann_vector(prob, grad_u)
+    rhs = b_full[free] - A[free][:, dmask] @ x[dmask]
+    x[free] = spla.spsolve(A[free][:, free].tocsc(), rhs)
+    return x

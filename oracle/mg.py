@@ -49,7 +49,8 @@ def coarsen_problem(prob):
     return fem.Problem(*nc, prob.k, disc=prob.disc, mapping=prob.mapping,
                        amp=prob.amp, kappa=prob.kappa, a_cell=a_cell,
                        a_face=a_face, penalty_factor=prob.penalty_factor,
-                       dirichlet=prob.dirichlet)
+                       dirichlet=prob.dirichlet, box=prob.box,
+                       neumann_sides=tuple(prob.neumann))
 
 
 def coarsen_coefficient(prob, nc):
