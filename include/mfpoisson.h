@@ -96,11 +96,24 @@ typedef struct {
                             [2^-80, 2^127] in magnitude (smaller ones lose
                             their low part).  MFP_ARITH_NATIVE uses DFMA.
                             Float64 vectors in HBM either way.             */
+  int neumann_sides;     /* sides with Neumann data: bit 2e for x_e = lo,
+                            bit 2e+1 for x_e = hi (e = 0, 1, 2 for x, y, z).
+                            CG: those nodes stay free (natural condition);
+                            SIPG: no operator terms on those boundary faces
+                            (Eq. 7 leaves only data there).  The other sides
+                            are Dirichlet (identity rows for CG, the mirror
+                            state of Eq. 7 for SIPG).  0 (default): all six
+                            Dirichlet; at least one side must stay Dirichlet
+                            (values 0..62).                                 */
+  double box_lo, box_hi; /* domain [box_lo, box_hi]^3: the unit cube mapped
+                            by `mapping`, then by x -> box_lo + (box_hi -
+                            box_lo) x (default 0, 1; Sec. 5 uses -1, 1)     */
 } mfp_desc;
 
 /* Fill `desc` with the defaults (1 cell, k=1, CG, identity map, kappa 1,
  * penalty_factor 1, FP64 V-cycle, Chebyshev degree 5, 15 CG iterations,
- * double-float arithmetic for float64 applies). */
+ * double-float arithmetic for float64 applies, Dirichlet on all sides,
+ * domain [0, 1]^3). */
 void mfp_desc_default(mfp_desc* desc);
 
 /* Create a context on the current CUDA device: builds every multigrid level
@@ -135,12 +148,20 @@ mfp_status mfp_set_coefficient(mfp_ctx* ctx, const double* a_cell_dev,
                                const double* a_face_dev, void* stream);
 
 /* Load vector b_i = sum_q w_q det J f(x_q) phi_i(x_q) on the finest level
- * (Eq. 4 / Eq. 6 right-hand side, homogeneous Dirichlet data), written to
- * b_dev[i * stride] (stride >= 1, e.g. R for column r of a batch when the
- * pointer is offset by r).  f_kind 0: f = 3 pi^2 sin(pi x) sin(pi y)
- * sin(pi z) (params unused); f_kind 1: f = sum_j A_j exp(-|x - c_j|^2 /
- * w_j^2) with params_host = n_terms blocks (c_x, c_y, c_z, w, A).  Zero on
- * constrained (CG boundary) dofs. */
+ * (Eq. 4 / Eq. 6 right-hand side), written to b_dev[i * stride] (stride >=
+ * 1, e.g. R for column r of a batch when the pointer is offset by r).
+ *  - f_kind 0: f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) (params unused),
+ *    homogeneous boundary data: zero on constrained (CG Dirichlet) dofs.
+ *  - f_kind 1: f = sum_j A_j exp(-|x - c_j|^2 / w_j^2) with params_host =
+ *    n_terms blocks (c_x, c_y, c_z, w, A), homogeneous boundary data.
+ *  - f_kind 2: the problem whose exact solution is u = sum_j A_j exp(-|x -
+ *    c_j|^2 / w_j^2) (same params; Sec. 5 uses three such terms on
+ *    (-1, 1)^3): f = -kappa Laplace u, Dirichlet data u on the Dirichlet
+ *    sides and Neumann data kappa grad u . n on the Neumann sides.  CG: a
+ *    constrained dof holds u at its node and the free rows have the lifted
+ *    data subtracted (so the solve returns the complete solution); SIPG:
+ *    the data terms of Eq. 7 on Dirichlet faces.  Needs the constant
+ *    coefficient (MFP_ERR_ARG after mfp_set_coefficient). */
 mfp_status mfp_rhs(mfp_ctx* ctx, int f_kind, const double* params_host,
                    int n_terms, double* b_dev, int64_t stride, void* stream);
 

@@ -585,25 +585,31 @@ def sipg_dirichlet_vector(prob, u):
     return b
 
 
-def solve_manufactured(prob, f, u, grad_u):
-    """Discrete solution for -div(kappa grad u) = f with the Dirichlet data
-    of u on the Dirichlet sides and the Neumann flux of u on the Neumann
-    sides, by a sparse direct solve.  CG: interpolated Dirichlet values,
-    lifted out of the free rows (Sec. 2.1); SIPG: weakly imposed (Eq. 7)."""
-    import scipy.sparse.linalg as spla
+def manufactured_rhs(prob, f, u, grad_u):
+    """Right-hand side for -div(kappa grad u) = f with the Dirichlet data of
+    u on the Dirichlet sides and the Neumann flux of u on the Neumann sides,
+    for the matrix of `assemble(prob)`: load vector plus Neumann data; SIPG:
+    plus the data terms of Eq. 7; CG: the constrained rows hold the
+    interpolated Dirichlet values and the free rows have them lifted out,
+    b_f - A_fc g_c (Sec. 2.1), so that the system's solution is complete."""
     b = load_vector(prob, f) + neumann_vector(prob, grad_u)
     if prob.disc == "dg":
-        b = b + sipg_dirichlet_vector(prob, u)
-        return spla.spsolve(assemble(prob).tocsc(), b)
+        return b + sipg_dirichlet_vector(prob, u)
     full = Problem(*prob.n, prob.k, disc="cg", mapping=prob.mapping,
                    amp=prob.amp, kappa=prob.kappa, a_cell=prob.a_cell,
                    a_face=prob.a_face, dirichlet=False, box=prob.box)
-    A = assemble(full)
     dmask = prob.constrained()
-    x = np.zeros(prob.n_dofs)
-    x[dmask] = u(prob.node_points()[dmask])
-    free = ~dmask
-    b_full = load_vector(full, f) + neumann_vector(prob, grad_u)
-    rhs = b_full[free] - A[free][:, dmask] @ x[dmask]
-    x[free] = spla.spsolve(A[free][:, free].tocsc(), rhs)
-    return x
+    g = np.zeros(prob.n_dofs)
+    g[dmask] = u(prob.node_points()[dmask])
+    b = b - assemble(full) @ g
+    b[dmask] = g[dmask]
+    return b
+
+
+def solve_manufactured(prob, f, u, grad_u):
+    """Discrete solution of the problem of manufactured_rhs by a sparse
+    direct solve.  CG: interpolated Dirichlet values (Sec. 2.1); SIPG:
+    weakly imposed (Eq. 7)."""
+    import scipy.sparse.linalg as spla
+    b = manufactured_rhs(prob, f, u, grad_u)
+    return spla.spsolve(assemble(prob).tocsc(), b)

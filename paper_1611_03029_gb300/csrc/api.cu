@@ -575,6 +575,9 @@ void mfp_desc_default(mfp_desc* d) {
   d->cheb_degree = 5;
   d->eig_cg_iters = 15;
   d->fp64_arith = MFP_ARITH_DF;
+  d->neumann_sides = 0;
+  d->box_lo = 0.0;
+  d->box_hi = 1.0;
 }
 
 const char* mfp_last_error(void) { return g_err.c_str(); }
@@ -595,6 +598,12 @@ mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out) {
                     std::fabs(d.map_param) * 3.14159265358979 * std::sqrt(3.0) < 1.0,
                 "map_param too large: the mapping would fold");
     MFP_REQUIRE(d.kappa > 0, "kappa must be > 0");
+    MFP_REQUIRE(d.neumann_sides >= 0 && d.neumann_sides < 63,
+                "neumann_sides must be a mask of sides 0..5 that leaves at "
+                "least one Dirichlet side");
+    MFP_REQUIRE(std::isfinite(d.box_lo) && std::isfinite(d.box_hi) &&
+                    d.box_hi > d.box_lo,
+                "box_hi must exceed box_lo");
     MFP_REQUIRE(d.penalty_factor > 0, "penalty_factor must be > 0");
     MFP_REQUIRE(d.cheb_degree >= 1 && d.cheb_degree <= 64,
                 "cheb_degree must be in 1..64");
@@ -648,10 +657,15 @@ mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out) {
       L.kappa = d.kappa;
       L.penalty = d.penalty_factor;
       L.ncells = (int64_t)L.n[0] * L.n[1] * L.n[2];
+      L.box_lo = d.box_lo;
+      L.box_len = d.box_hi - d.box_lo;
       for (int e = 0; e < 3; ++e) {
         L.gdim[e] = L.n[e] * L.k + 1;
-        L.h[e] = 1.0 / L.n[e];
+        L.h[e] = L.box_len / L.n[e];
+        L.bc.lo[e] = (d.neumann_sides >> (2 * e)) & 1 ? -1 : 0;
+        L.bc.hi[e] = (d.neumann_sides >> (2 * e + 1)) & 1 ? -1 : L.gdim[e] - 1;
       }
+      L.bc.neumann = d.neumann_sides;
       L.ndofs = d.disc == MFP_CG ? (int64_t)L.gdim[0] * L.gdim[1] * L.gdim[2]
                                  : L.ncells * L.p * L.p * L.p;
       int64_t off = 0;
@@ -748,10 +762,12 @@ mfp_status mfp_rhs(mfp_ctx* c, int f_kind, const double* params, int nterms,
                    double* b, int64_t stride, void* stream) {
   API_BEGIN
   MFP_REQUIRE(c && b, "null argument");
-  MFP_REQUIRE(f_kind == 0 || f_kind == 1, "unknown f_kind");
+  MFP_REQUIRE(f_kind >= 0 && f_kind <= 2, "unknown f_kind");
   MFP_REQUIRE(stride >= 1, "stride must be >= 1");
+  MFP_REQUIRE(f_kind != 2 || !c->has_coef,
+              "f_kind 2 needs the constant coefficient");
   cudaStream_t s = st(stream);
-  if (f_kind == 1) {
+  if (f_kind >= 1) {
     MFP_REQUIRE(params && nterms >= 1 && nterms <= 4096, "bad Gaussian terms");
     if (c->params_cap < nterms) {
       dfree(c->params);

@@ -27,6 +27,8 @@ struct ApplyArgs {
   int n[3];
   int ncells;
   int g[3];          // CG node grid
+  int blo[3], bhi[3];  // CG: constrained node coordinates per axis (-1: none)
+  int neumann;         // SIPG: bit 2d + s = Neumann side (no face terms)
   int face_off[3];
   const T* __restrict__ G;      // curved: [cell][6][p^3]
   const T* __restrict__ kcell;  // [cell][p^3] or null
@@ -93,7 +95,9 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
                     (cy + (D == 1 ? S : 0) +
                      (a.n[1] + (D == 1)) * (cz + (D == 2 ? S : 0)));
   const bool bnd = S ? cD + 1 >= a.n[D] : cD == 0;
-  const bool own = S == 1 || bnd;
+  // a boundary face on a Neumann side has no operator terms
+  const bool own =
+      (S == 1 || bnd) && !(bnd && ((a.neumann >> (2 * D + S)) & 1));
   const bool pair = S == 1 && !bnd && active;
   const int nb = pair ? cx + a.n[0] * (cy + a.n[1] * cz) +
                             (D == 0 ? 1 : (D == 1 ? a.n[0] : a.n[0] * a.n[1]))
@@ -364,7 +368,7 @@ __global__ void k_apply(const ApplyArgs<T> a) {
   T* sw = s1 + P;
   load_tables_shared<T, P>(sS, sD, sDphi, s0, s1, sw);
   __syncthreads();
-  const int gx0 = a.g[0], gy0 = a.g[1], gz0 = a.g[2];
+  const int gx0 = a.g[0], gy0 = a.g[1];
   const int col = a.col + rr;
 
   for (int cbase = blockIdx.x * cpb; cbase < a.ncells;
@@ -394,11 +398,12 @@ __global__ void k_apply(const ApplyArgs<T> a) {
       }
     } else {
       const int X = cx * (P - 1) + ta, Y = cy * (P - 1) + tb;
-      const bool bxy = X == 0 || X == gx0 - 1 || Y == 0 || Y == gy0 - 1;
+      const bool bxy = X == a.blo[0] || X == a.bhi[0] || Y == a.blo[1] ||
+                       Y == a.bhi[1];
 #pragma unroll
       for (int z = 0; z < P; ++z) {
         const int Z = cz * (P - 1) + z;
-        const bool con = bxy || Z == 0 || Z == gz0 - 1;
+        const bool con = bxy || Z == a.blo[2] || Z == a.bhi[2];
         const size_t gi = (size_t)X + (size_t)gx0 * (Y + (size_t)gy0 * Z);
         r[z] = (active && !con) ? a.src[gi * a.stride + col] : T(0);
       }
@@ -496,7 +501,8 @@ __global__ void k_apply(const ApplyArgs<T> a) {
       for (int D = 0; D < 3; ++D) {
         // lower faces only where a cell of the block lies on the boundary
         const int cD = D == 0 ? cx : (D == 1 ? cy : cz);
-        if (__syncthreads_or(active && cD == 0))
+        if (!((a.neumann >> (2 * D)) & 1) &&
+            __syncthreads_or(active && cD == 0))
           face_lower_gp<P, T, CURVED>(a, col, D, active, cx, cy, cz, U, Aq,
                                       FS, sS, sD, sw, ta, tb);
         face_gp<P, T, CURVED, 1>(a, col, D, active, cx, cy, cz, U, Aq, FS, sS,
@@ -522,12 +528,13 @@ __global__ void k_apply(const ApplyArgs<T> a) {
     // ---- scatter
     if constexpr (!DG) {
       const int X = cx * (P - 1) + ta, Y = cy * (P - 1) + tb;
-      const bool bxy = X == 0 || X == gx0 - 1 || Y == 0 || Y == gy0 - 1;
+      const bool bxy = X == a.blo[0] || X == a.bhi[0] || Y == a.blo[1] ||
+                       Y == a.bhi[1];
       if (active) {
 #pragma unroll
         for (int z = 0; z < P; ++z) {
           const int Z = cz * (P - 1) + z;
-          const bool con = bxy || Z == 0 || Z == gz0 - 1;
+          const bool con = bxy || Z == a.blo[2] || Z == a.bhi[2];
           const size_t gi =
               ((size_t)X + (size_t)gx0 * (Y + (size_t)gy0 * Z)) * a.stride +
               col;
@@ -670,8 +677,11 @@ ApplyArgs<T> make_apply_args(const Level& L, const LevelData<T>& D,
   for (int d = 0; d < 3; ++d) {
     a.n[d] = L.n[d];
     a.g[d] = L.gdim[d];
+    a.blo[d] = L.bc.lo[d];
+    a.bhi[d] = L.bc.hi[d];
     a.face_off[d] = L.face_off[d];
   }
+  a.neumann = L.bc.neumann;
   a.ncells = (int)L.ncells;
   a.G = D.G;
   a.kcell = D.kcell;

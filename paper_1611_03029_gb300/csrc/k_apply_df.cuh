@@ -39,6 +39,8 @@ struct ApplyArgsDF {
   int n[3];
   int ncells;
   int g[3];
+  int blo[3], bhi[3];        // CG: constrained node coordinates (-1: none)
+  int neumann;               // SIPG: bit 2d + s = Neumann side
   int face_off[3];
   const float *Gh, *Gl;      // curved: [cell][6][p^3]
   const float *kch, *kcl;    // [cell][p^3] or null
@@ -303,7 +305,9 @@ __device__ __forceinline__ void df_face_gp(const ApplyArgsDF& a, int col,
                     (cy + (D == 1 ? S : 0) +
                      (a.n[1] + (D == 1)) * (cz + (D == 2 ? S : 0)));
   const bool bnd = S ? cD + 1 >= a.n[D] : cD == 0;
-  const bool own = S == 1 || bnd;
+  // a boundary face on a Neumann side has no operator terms
+  const bool own =
+      (S == 1 || bnd) && !(bnd && ((a.neumann >> (2 * D + S)) & 1));
   const bool pair = S == 1 && !bnd && active;
   const int nb = pair ? cx + a.n[0] * (cy + a.n[1] * cz) +
                             (D == 0 ? 1 : (D == 1 ? a.n[0] : a.n[0] * a.n[1]))
@@ -605,7 +609,7 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
     }
   }
   __syncthreads();
-  const int gx0 = a.g[0], gy0 = a.g[1], gz0 = a.g[2];
+  const int gx0 = a.g[0], gy0 = a.g[1];
   const int col = a.col + rr;
   // Cartesian quadrature weights times |K|/h_d^2 for this thread's (x, y)
   df wg[3];
@@ -635,11 +639,12 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
       }
     } else {
       const int X = cx * (P - 1) + ta, Y = cy * (P - 1) + tb;
-      const bool bxy = X == 0 || X == gx0 - 1 || Y == 0 || Y == gy0 - 1;
+      const bool bxy = X == a.blo[0] || X == a.bhi[0] || Y == a.blo[1] ||
+                       Y == a.bhi[1];
 #pragma unroll
       for (int z = 0; z < P; ++z) {
         const int Z = cz * (P - 1) + z;
-        const bool con = bxy || Z == 0 || Z == gz0 - 1;
+        const bool con = bxy || Z == a.blo[2] || Z == a.bhi[2];
         const size_t gi = (size_t)X + (size_t)gx0 * (Y + (size_t)gy0 * Z);
         const df u = df_from_double((active && !con)
                                         ? a.src[gi * a.stride + col]
@@ -757,7 +762,8 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
       for (int D = 0; D < 3; ++D) {
         // lower faces only where a cell of the block lies on the boundary
         const int cD = D == 0 ? cx : (D == 1 ? cy : cz);
-        if (__syncthreads_or(active && cD == 0))
+        if (!((a.neumann >> (2 * D)) & 1) &&
+            __syncthreads_or(active && cD == 0))
           df_face_lower_gp<P, CURVED>(a, col, D, active, cx, cy, cz, U, A, FS,
                                       tabs, ta, tb);
         df_face_gp<P, CURVED, 1>(a, col, D, active, cx, cy, cz, U, A, FS, t,
@@ -796,12 +802,13 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
     if constexpr (!DG) {
       dmtv<P, DF_S>(rh, rl, oh, ol);
       const int X = cx * (P - 1) + ta, Y = cy * (P - 1) + tb;
-      const bool bxy = X == 0 || X == gx0 - 1 || Y == 0 || Y == gy0 - 1;
+      const bool bxy = X == a.blo[0] || X == a.bhi[0] || Y == a.blo[1] ||
+                       Y == a.bhi[1];
       if (active) {
 #pragma unroll
         for (int z = 0; z < P; ++z) {
           const int Z = cz * (P - 1) + z;
-          const bool con = bxy || Z == 0 || Z == gz0 - 1;
+          const bool con = bxy || Z == a.blo[2] || Z == a.bhi[2];
           const size_t gi =
               ((size_t)X + (size_t)gx0 * (Y + (size_t)gy0 * Z)) * a.stride +
               col;
@@ -1012,8 +1019,11 @@ inline ApplyArgsDF make_apply_args_df(const Level& L, const double* src,
   for (int d = 0; d < 3; ++d) {
     a.n[d] = L.n[d];
     a.g[d] = L.gdim[d];
+    a.blo[d] = L.bc.lo[d];
+    a.bhi[d] = L.bc.hi[d];
     a.face_off[d] = L.face_off[d];
   }
+  a.neumann = L.bc.neumann;
   a.ncells = (int)L.ncells;
   const LevelDF& D = L.ddf;
   a.Gh = D.Gh;

@@ -15,6 +15,7 @@ struct GradArgs {
   int n[3];
   int g[3];
   int face_off[3];
+  Bc bc;  // constrained CG nodes; SIPG faces on Neumann sides
   int disc;
   bool curved;
   double gs[3], ns[3], fa[3], sg[3];
@@ -49,8 +50,7 @@ __global__ void k_grad_cells(GradArgs a, const double* __restrict__ u,
     } else {
       const int X = cx * (P - 1) + ix, Y = cy * (P - 1) + iy,
                 Z = cz * (P - 1) + iz;
-      const bool con = X == 0 || Y == 0 || Z == 0 || X == a.g[0] - 1 ||
-                       Y == a.g[1] - 1 || Z == a.g[2] - 1;
+      const bool con = bc_con(a.bc, X, Y, Z);
       const size_t gi = (size_t)X + (size_t)a.g[0] * (Y + (size_t)a.g[1] * Z);
       vu = con ? 0.0 : u[gi];
       vl = con ? 0.0 : lam[gi];
@@ -220,6 +220,8 @@ __global__ void k_grad_faces(GradArgs a, int D, const double* __restrict__ u,
       const double uu = val[sd][0], ll = val[sd][1];
       const double du = sgn * dn[sd][0], dl = sgn * dn[sd][1];
       form = -ll * du - uu * dl + 2.0 * sig * ll * uu;
+      // a face on a Neumann side has no term of the form (Eq. 7)
+      if ((a.bc.neumann >> (2 * D + (hasL ? 1 : 0))) & 1) form = 0.0;
     }
     gf[f * P2 + q] = -dA * form;
   }
@@ -236,6 +238,7 @@ void launch_gradient(const Level& L, const double* u, const double* lam,
     a.g[d] = L.gdim[d];
     a.face_off[d] = L.face_off[d];
   }
+  a.bc = L.bc;
   a.disc = L.disc;
   a.curved = L.curved;
   const double vol = L.h[0] * L.h[1] * L.h[2];

@@ -11,8 +11,9 @@ namespace {
 struct GeoArgs {
   int n[3];
   int p;
-  double h[3];
+  double h[3];  // cell size on the unit cube (1 / n)
   double amp;
+  double lo, len;  // then x -> lo + len x onto the box [lo, lo + len]^3
 };
 
 // All tables of degree P-1 in shared memory.
@@ -58,9 +59,9 @@ __device__ void support_points(const GeoArgs& g, const ShTab<P>& t, int cx,
     double y = (cy + t.x[ay]) * g.h[1];
     double z = (cz + t.x[az]) * g.h[2];
     phi_map(g.amp, x, y, z);
-    X[3 * a] = x;
-    X[3 * a + 1] = y;
-    X[3 * a + 2] = z;
+    X[3 * a] = g.lo + g.len * x;
+    X[3 * a + 1] = g.lo + g.len * y;
+    X[3 * a + 2] = g.lo + g.len * z;
   }
 }
 
@@ -266,6 +267,7 @@ struct DiagArgs {
   int n[3];
   int g[3];
   int face_off[3];
+  Bc bc;
   int disc;
   bool curved;
   double kappa;
@@ -321,6 +323,7 @@ __global__ void k_diagonal(DiagArgs a, double* diag) {
           fc[D] += S;
           const size_t f = a.face_off[D] + fc[0] + m[0] * (fc[1] + m[1] * fc[2]);
           const bool bnd = (S == 0 && cc[D] == 0) || (S == 1 && cc[D] == a.n[D] - 1);
+          if (bnd && ((a.bc.neumann >> (2 * D + S)) & 1)) continue;  // Neumann
           const int lo = S ? P - 1 : 0;
           const double* dS = S ? t.d1 : t.d0;
           const bool onface = ii[D] == lo;
@@ -357,8 +360,7 @@ __global__ void k_diagonal(DiagArgs a, double* diag) {
     } else {
       const int X = cx * (P - 1) + ix, Y = cy * (P - 1) + iy,
                 Z = cz * (P - 1) + iz;
-      const bool con = X == 0 || Y == 0 || Z == 0 || X == a.g[0] - 1 ||
-                       Y == a.g[1] - 1 || Z == a.g[2] - 1;
+      const bool con = bc_con(a.bc, X, Y, Z);
       if (!con)
         atomicAdd(diag + (size_t)X + (size_t)a.g[0] * (Y + (size_t)a.g[1] * Z),
                   acc);
@@ -377,7 +379,30 @@ struct RhsArgs {
   int nterms;
   const double* params;  // device copy, nterms * 5
   int64_t stride;
+  Bc bc;
+  double kappa;           // constant coefficient (kind 2)
+  int face_off[3];
+  const double* sigma;    // curved SIPG: penalty per face
+  double sg[3];           // Cartesian SIPG: penalty of a d-face
 };
+
+// kind 2: u = sum_j A_j exp(-|x - c_j|^2 / w_j^2); returns u(x) and grad u.
+__device__ double gauss_sum(const RhsArgs& a, const double (&x)[3],
+                            double (&gr)[3]) {
+  double u = 0;
+  gr[0] = gr[1] = gr[2] = 0;
+  for (int j = 0; j < a.nterms; ++j) {
+    const double* c = a.params + 5 * j;
+    const double dx = x[0] - c[0], dy = x[1] - c[1], dz = x[2] - c[2];
+    const double iw2 = 1.0 / (c[3] * c[3]);
+    const double e = c[4] * exp(-(dx * dx + dy * dy + dz * dz) * iw2);
+    u += e;
+    gr[0] -= 2.0 * iw2 * dx * e;
+    gr[1] -= 2.0 * iw2 * dy * e;
+    gr[2] -= 2.0 * iw2 * dz * e;
+  }
+  return u;
+}
 
 __device__ double forcing(const RhsArgs& a, double x, double y, double z) {
   if (a.kind == 0) {
@@ -388,7 +413,15 @@ __device__ double forcing(const RhsArgs& a, double x, double y, double z) {
   for (int j = 0; j < a.nterms; ++j) {
     const double* c = a.params + 5 * j;
     const double dx = x - c[0], dy = y - c[1], dz = z - c[2];
-    f += c[4] * exp(-(dx * dx + dy * dy + dz * dz) / (c[3] * c[3]));
+    if (a.kind == 1) {
+      f += c[4] * exp(-(dx * dx + dy * dy + dz * dz) / (c[3] * c[3]));
+    } else {
+      // kind 2: f = -kappa Laplace u, Laplace of exp(-r^2/w^2) in 3D being
+      // (4 r^2 / w^2 - 6) / w^2 times the exponential
+      const double iw2 = 1.0 / (c[3] * c[3]);
+      const double r2 = (dx * dx + dy * dy + dz * dz) * iw2;
+      f += a.kappa * iw2 * (6.0 - 4.0 * r2) * c[4] * exp(-r2);
+    }
   }
   return f;
 }
@@ -423,10 +456,10 @@ __global__ void k_rhs(RhsArgs a, double* b) {
       jacobian<P>(X, v, s, J, x);
       wdet = inv3(J, I);
     } else {
-      x[0] = (cx + t.g[qx]) * g.h[0];
-      x[1] = (cy + t.g[qy]) * g.h[1];
-      x[2] = (cz + t.g[qz]) * g.h[2];
-      wdet = g.h[0] * g.h[1] * g.h[2];
+      x[0] = g.lo + g.len * (cx + t.g[qx]) * g.h[0];
+      x[1] = g.lo + g.len * (cy + t.g[qy]) * g.h[1];
+      x[2] = g.lo + g.len * (cz + t.g[qz]) * g.h[2];
+      wdet = g.len * g.len * g.len * g.h[0] * g.h[1] * g.h[2];
     }
     wdet *= t.w[qx] * t.w[qy] * t.w[qz];
     F[q] = wdet * forcing(a, x[0], x[1], x[2]);
@@ -444,10 +477,232 @@ __global__ void k_rhs(RhsArgs a, double* b) {
     } else {
       const int X_ = cx * (P - 1) + ix, Y = cy * (P - 1) + iy,
                 Z = cz * (P - 1) + iz;
-      const bool con = X_ == 0 || Y == 0 || Z == 0 || X_ == a.g[0] - 1 ||
-                       Y == a.g[1] - 1 || Z == a.g[2] - 1;
+      const bool con = bc_con(a.bc, X_, Y, Z);
       if (!con)
         atomicAdd(b + ((size_t)X_ + (size_t)a.g[0] * (Y + (size_t)a.g[1] * Z)) *
+                          a.stride,
+                  acc);
+    }
+  }
+}
+
+// kind 2, CG: Dirichlet data on the constrained nodes, lifted out of the
+// free rows (Sec. 2.1): a constrained row takes the data value at its node,
+// a free row i loses a(g_h, phi_i) with g_h the cell's interpolant of the
+// data on its constrained nodes, i.e. sum_q grad_xi phi_i . M_q grad_xi g_h
+// with M_q = w_q det J kappa J^{-1} J^{-T}.  Runs after k_rhs.
+template <int P>
+__global__ void k_rhs_lift(RhsArgs a, double* b) {
+  constexpr int P3 = P * P * P;
+  __shared__ ShTab<P> t;
+  __shared__ double X[3 * P3];
+  __shared__ double gN[P3];
+  __shared__ double Fl[3 * P3];
+  const GeoArgs& g = a.geo;
+  const int cell = blockIdx.x;
+  const int c3[3] = {cell % g.n[0], (cell / g.n[0]) % g.n[1],
+                     cell / (g.n[0] * g.n[1])};
+  // only cells with a node on a Dirichlet side (uniform over the block)
+  bool touch = false;
+  for (int d = 0; d < 3; ++d)
+    touch = touch || (c3[d] == 0 && a.bc.lo[d] == 0) ||
+            (c3[d] == g.n[d] - 1 && a.bc.hi[d] >= 0);
+  if (!touch) return;
+  load_shtab<P>(t);
+  __syncthreads();
+  const bool curved = g.amp != 0.0;
+  if (curved) support_points<P>(g, t, c3[0], c3[1], c3[2], X);
+  __syncthreads();
+  for (int i = threadIdx.x; i < P3; i += blockDim.x) {
+    const int ii[3] = {i % P, (i / P) % P, i / (P * P)};
+    const int64_t N[3] = {(int64_t)c3[0] * (P - 1) + ii[0],
+                          (int64_t)c3[1] * (P - 1) + ii[1],
+                          (int64_t)c3[2] * (P - 1) + ii[2]};
+    double v = 0;
+    if (bc_con(a.bc, N[0], N[1], N[2])) {
+      double x[3], gr[3];
+      for (int d = 0; d < 3; ++d)
+        x[d] = curved ? X[3 * i + d]
+                      : g.lo + g.len * (c3[d] + t.x[ii[d]]) * g.h[d];
+      v = gauss_sum(a, x, gr);
+      b[(N[0] + (int64_t)a.g[0] * (N[1] + (int64_t)a.g[1] * N[2])) *
+        a.stride] = v;  // the same value from every cell of the node
+    }
+    gN[i] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < P3; q += blockDim.x) {
+    const int qq[3] = {q % P, (q / P) % P, q / (P * P)};
+    double r[3] = {0, 0, 0};  // grad_xi g_h at the point
+    for (int j = 0; j < P3; ++j) {
+      const double gj = gN[j];
+      if (gj == 0.0) continue;
+      const int jx = j % P, jy = (j / P) % P, jz = j / (P * P);
+      const double sx = t.S[qq[0] * P + jx], sy = t.S[qq[1] * P + jy],
+                   sz = t.S[qq[2] * P + jz];
+      r[0] += t.Dphi[qq[0] * P + jx] * sy * sz * gj;
+      r[1] += sx * t.Dphi[qq[1] * P + jy] * sz * gj;
+      r[2] += sx * sy * t.Dphi[qq[2] * P + jz] * gj;
+    }
+    const double w =
+        t.w[qq[0]] * t.w[qq[1]] * t.w[qq[2]] * a.kappa;
+    if (curved) {
+      double v[3][P], s[3][P];
+      for (int e = 0; e < 3; ++e)
+        for (int j = 0; j < P; ++j) {
+          v[e][j] = t.S[qq[e] * P + j];
+          s[e][j] = t.Dphi[qq[e] * P + j];
+        }
+      double J[3][3], I[3][3], x[3];
+      jacobian<P>(X, v, s, J, x);
+      const double det = inv3(J, I);
+      double pr[3];  // J^{-T} grad_xi g_h
+      for (int d = 0; d < 3; ++d)
+        pr[d] = I[0][d] * r[0] + I[1][d] * r[1] + I[2][d] * r[2];
+      for (int e = 0; e < 3; ++e)
+        Fl[3 * q + e] =
+            w * det * (I[e][0] * pr[0] + I[e][1] * pr[1] + I[e][2] * pr[2]);
+    } else {
+      double H[3], det = 1;
+      for (int d = 0; d < 3; ++d) {
+        H[d] = g.len * g.h[d];
+        det *= H[d];
+      }
+      for (int e = 0; e < 3; ++e) Fl[3 * q + e] = w * det * r[e] / (H[e] * H[e]);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < P3; i += blockDim.x) {
+    const int ii[3] = {i % P, (i / P) % P, i / (P * P)};
+    const int64_t N[3] = {(int64_t)c3[0] * (P - 1) + ii[0],
+                          (int64_t)c3[1] * (P - 1) + ii[1],
+                          (int64_t)c3[2] * (P - 1) + ii[2]};
+    if (bc_con(a.bc, N[0], N[1], N[2])) continue;
+    double acc = 0;
+    for (int q = 0; q < P3; ++q) {
+      const int qx = q % P, qy = (q / P) % P, qz = q / (P * P);
+      const double sx = t.S[qx * P + ii[0]], sy = t.S[qy * P + ii[1]],
+                   sz = t.S[qz * P + ii[2]];
+      acc += t.Dphi[qx * P + ii[0]] * sy * sz * Fl[3 * q] +
+             sx * t.Dphi[qy * P + ii[1]] * sz * Fl[3 * q + 1] +
+             sx * sy * t.Dphi[qz * P + ii[2]] * Fl[3 * q + 2];
+    }
+    atomicAdd(b + (N[0] + (int64_t)a.g[0] * (N[1] + (int64_t)a.g[1] * N[2])) *
+                      a.stride,
+              -acc);
+  }
+}
+
+// kind 2: boundary data on the faces of side `side` (x_D = lo for side 2D,
+// hi for 2D + 1), one block per face, one cell per face (so SIPG adds
+// without atomics; the sides go in separate launches).
+//  - Neumann side: the natural term int phi_i kappa grad u . n ds (Eq. 1
+//    with Neumann data; SIPG: the only term Eq. 7 leaves on such a face).
+//  - SIPG Dirichlet side: the data part of the extension u+ = 2 g - u- of
+//    Eq. 7, kappa dA (2 sigma g phi_i - g d_n phi_i).
+template <int P>
+__global__ void k_rhs_face(RhsArgs a, int side, double* b) {
+  constexpr int P2 = P * P, P3 = P2 * P;
+  __shared__ ShTab<P> t;
+  __shared__ double X[3 * P3];
+  __shared__ double cv[P2], cm[3 * P2];
+  const GeoArgs& g = a.geo;
+  const int D = side / 2, s = side % 2;
+  const int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
+  const bool neu = (a.bc.neumann >> side) & 1;
+  int c3[3];
+  c3[D] = s ? g.n[D] - 1 : 0;
+  c3[T1] = blockIdx.x % g.n[T1];
+  c3[T2] = blockIdx.x / g.n[T1];
+  const int cell = c3[0] + g.n[0] * (c3[1] + g.n[1] * c3[2]);
+  int m[3] = {g.n[0], g.n[1], g.n[2]};
+  m[D] += 1;
+  int fc[3] = {c3[0], c3[1], c3[2]};
+  fc[D] += s;
+  const int64_t f =
+      a.face_off[D] + fc[0] + (int64_t)m[0] * (fc[1] + (int64_t)m[1] * fc[2]);
+  load_shtab<P>(t);
+  __syncthreads();
+  const bool curved = g.amp != 0.0;
+  if (curved) support_points<P>(g, t, c3[0], c3[1], c3[2], X);
+  __syncthreads();
+  const double* dS = s ? t.d1 : t.d0;  // GLL basis slopes at the cell end
+  const int end = s ? P - 1 : 0;
+  for (int q = threadIdx.x; q < P2; q += blockDim.x) {
+    const int qa = q % P, qb = q / P;
+    double x[3], I[3][3], det;
+    if (curved) {
+      double v[3][P], sl[3][P];
+      for (int j = 0; j < P; ++j) {
+        v[D][j] = j == end ? 1.0 : 0.0;
+        sl[D][j] = dS[j];
+        v[T1][j] = t.S[qa * P + j];
+        sl[T1][j] = t.Dphi[qa * P + j];
+        v[T2][j] = t.S[qb * P + j];
+        sl[T2][j] = t.Dphi[qb * P + j];
+      }
+      double J[3][3];
+      jacobian<P>(X, v, sl, J, x);
+      det = inv3(J, I);
+    } else {
+      double r[3];
+      r[D] = s;
+      r[T1] = t.g[qa];
+      r[T2] = t.g[qb];
+      det = 1;
+      for (int d = 0; d < 3; ++d) {
+        const double H = g.len * g.h[d];
+        x[d] = g.lo + H * (c3[d] + r[d]);
+        for (int e = 0; e < 3; ++e) I[d][e] = d == e ? 1.0 / H : 0.0;
+        det *= H;
+      }
+    }
+    // outward unit normal: +-(row D of J^{-1}) normalised; area element
+    const double nl = sqrt(I[D][0] * I[D][0] + I[D][1] * I[D][1] +
+                           I[D][2] * I[D][2]);
+    const double sg = s ? 1.0 : -1.0;
+    double n[3];
+    for (int d = 0; d < 3; ++d) n[d] = sg * I[D][d] / nl;
+    const double kdA = a.kappa * t.w[qa] * t.w[qb] * det * nl;
+    double gr[3];
+    const double u = gauss_sum(a, x, gr);
+    if (neu) {
+      cv[q] = kdA * (gr[0] * n[0] + gr[1] * n[1] + gr[2] * n[2]);
+      for (int e = 0; e < 3; ++e) cm[3 * q + e] = 0.0;
+    } else {
+      const double sig = a.sigma ? a.sigma[f] : a.sg[D];
+      cv[q] = 2.0 * sig * kdA * u;
+      // d_n phi = (J^{-1} n) . grad_xi phi
+      for (int e = 0; e < 3; ++e)
+        cm[3 * q + e] =
+            -kdA * u * (I[e][0] * n[0] + I[e][1] * n[1] + I[e][2] * n[2]);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < P3; i += blockDim.x) {
+    const int ii[3] = {i % P, (i / P) % P, i / P2};
+    const bool on = ii[D] == end;
+    if (a.disc != MFP_SIPG && !on) continue;  // CG: Neumann data only
+    double acc = 0;
+    for (int q = 0; q < P2; ++q) {
+      const int qa = q % P, qb = q / P;
+      const double va = t.S[qa * P + ii[T1]], vb = t.S[qb * P + ii[T2]];
+      double gref[3];
+      gref[D] = dS[ii[D]] * va * vb;
+      gref[T1] = on ? t.Dphi[qa * P + ii[T1]] * vb : 0.0;
+      gref[T2] = on ? va * t.Dphi[qb * P + ii[T2]] : 0.0;
+      const double phi = on ? va * vb : 0.0;
+      acc += cv[q] * phi + cm[3 * q] * gref[0] + cm[3 * q + 1] * gref[1] +
+             cm[3 * q + 2] * gref[2];
+    }
+    if (a.disc == MFP_SIPG) {
+      b[((size_t)cell * P3 + i) * a.stride] += acc;
+    } else {
+      const int64_t N[3] = {(int64_t)c3[0] * (P - 1) + ii[0],
+                            (int64_t)c3[1] * (P - 1) + ii[1],
+                            (int64_t)c3[2] * (P - 1) + ii[2]};
+      if (!bc_con(a.bc, N[0], N[1], N[2]))
+        atomicAdd(b + (N[0] + (int64_t)a.g[0] * (N[1] + (int64_t)a.g[1] * N[2])) *
                           a.stride,
                   acc);
     }
@@ -528,10 +783,12 @@ GeoArgs geo_args(const Level& L) {
   GeoArgs g;
   for (int d = 0; d < 3; ++d) {
     g.n[d] = L.n[d];
-    g.h[d] = L.h[d];
+    g.h[d] = 1.0 / L.n[d];
   }
   g.p = L.p;
   g.amp = L.map_amp;
+  g.lo = L.box_lo;
+  g.len = L.box_len;
   return g;
 }
 
@@ -586,6 +843,7 @@ void launch_diagonal(const Level& L, double* diag, cudaStream_t s) {
     a.g[d] = L.gdim[d];
     a.face_off[d] = L.face_off[d];
   }
+  a.bc = L.bc;
   a.disc = L.disc;
   a.curved = L.curved;
   a.kappa = L.kappa;
@@ -623,6 +881,13 @@ void launch_rhs(const Level& L, int kind, const double* params_dev,
   a.nterms = nterms;
   a.params = params_dev;
   a.stride = stride;
+  a.bc = L.bc;
+  a.kappa = L.kappa;
+  for (int d = 0; d < 3; ++d) {
+    a.face_off[d] = L.face_off[d];
+    a.sg[d] = L.penalty * (double)L.p * L.p / L.h[d];
+  }
+  a.sigma = L.curved ? L.d64.sigma : nullptr;
   k_zero_strided<<<256, 256, 0, s>>>(b, L.ndofs, stride);
   MFP_CHECK_CUDA(cudaGetLastError());
   note_launch();
@@ -630,9 +895,25 @@ void launch_rhs(const Level& L, int kind, const double* params_dev,
     constexpr int P = decltype(pc)::value;
     const int thr = P * P * P < 256 ? ((P * P * P + 31) / 32) * 32 : 256;
     k_rhs<P><<<(int)L.ncells, thr, 0, s>>>(a, b);
+    MFP_CHECK_CUDA(cudaGetLastError());
+    note_launch();
+    if (kind != 2) return;
+    // boundary data (kind 2): CG lifting, then one launch per side
+    if (L.disc == MFP_CG) {
+      k_rhs_lift<P><<<(int)L.ncells, thr, 0, s>>>(a, b);
+      MFP_CHECK_CUDA(cudaGetLastError());
+      note_launch();
+    }
+    for (int side = 0; side < 6; ++side) {
+      const bool neu = (L.bc.neumann >> side) & 1;
+      if (!neu && L.disc == MFP_CG) continue;  // lifted above
+      const int D = side / 2;
+      const int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
+      k_rhs_face<P><<<L.n[T1] * L.n[T2], thr, 0, s>>>(a, side, b);
+      MFP_CHECK_CUDA(cudaGetLastError());
+      note_launch();
+    }
   });
-  MFP_CHECK_CUDA(cudaGetLastError());
-  note_launch();
 }
 
 void launch_coarsen_coefficient(const Level& fine, const Level& coarse,

@@ -26,15 +26,14 @@ __global__ void k_fill(T* x, T v, int64_t n) {
   GRID_STRIDE(i, n) x[i] = v;
 }
 
-__global__ void k_invert_diag(double* d, int64_t n, int g0, int g1, int g2,
+__global__ void k_invert_diag(double* d, int64_t n, int g0, int g1, Bc bc,
                               int cg) {
   GRID_STRIDE(i, n) {
     bool con = false;
     if (cg) {
       const int64_t ix = i % g0, iy = (i / g0) % g1,
                     iz = i / ((int64_t)g0 * g1);
-      con = ix == 0 || iy == 0 || iz == 0 || ix == g0 - 1 || iy == g1 - 1 ||
-            iz == g2 - 1;
+      con = bc_con(bc, ix, iy, iz);
     }
     d[i] = con ? 1.0 : 1.0 / d[i];
   }
@@ -109,6 +108,7 @@ struct XferArgs {
   int gc[3];  // coarse CG grid
   int gf[3];  // fine CG grid
   int nf[3];  // fine cells per axis
+  Bc bcc, bcf;  // CG constrained nodes of the coarse / fine grid
   int dg;
   int stride;  // columns (batched layout)
   int col;
@@ -135,12 +135,6 @@ __device__ void load_embedding(T* E, int dg) {
   }
 }
 
-__device__ __forceinline__ bool on_boundary(int X, int Y, int Z,
-                                            const int (&g)[3]) {
-  return X == 0 || Y == 0 || Z == 0 || X == g[0] - 1 || Y == g[1] - 1 ||
-         Z == g[2] - 1;
-}
-
 template <typename T, int P>
 __global__ void k_prolongate(XferArgs a, const T* __restrict__ xc,
                              T* __restrict__ xf) {
@@ -163,7 +157,7 @@ __global__ void k_prolongate(XferArgs a, const T* __restrict__ xc,
       v = xc[((size_t)C * P * P * P + i) * a.stride + a.col];
     } else {
       const int X = cx * K + ix, Y = cy * K + iy, Z = cz * K + iz;
-      v = on_boundary(X, Y, Z, a.gc)
+      v = bc_con(a.bcc, X, Y, Z)
               ? T(0)
               : xc[((size_t)X + (size_t)a.gc[0] * (Y + (size_t)a.gc[1] * Z)) *
                        a.stride +
@@ -203,7 +197,7 @@ __global__ void k_prolongate(XferArgs a, const T* __restrict__ xc,
       if (!own) continue;
       const int X = 2 * K * cx + fx, Y = 2 * K * cy + fy, Z = 2 * K * cz + fz;
       const size_t gi = (size_t)X + (size_t)a.gf[0] * (Y + (size_t)a.gf[1] * Z);
-      xf[gi * a.stride + a.col] = on_boundary(X, Y, Z, a.gf) ? T(0) : s;
+      xf[gi * a.stride + a.col] = bc_con(a.bcf, X, Y, Z) ? T(0) : s;
     }
   }
 }
@@ -237,7 +231,7 @@ __global__ void k_restrict(XferArgs a, const T* __restrict__ xf,
                        (fy < 2 * K || cy == a.nc[1] - 1) &&
                        (fz < 2 * K || cz == a.nc[2] - 1);
       const int X = 2 * K * cx + fx, Y = 2 * K * cy + fy, Z = 2 * K * cz + fz;
-      v = (!own || on_boundary(X, Y, Z, a.gf))
+      v = (!own || bc_con(a.bcf, X, Y, Z))
               ? T(0)
               : xf[((size_t)X + (size_t)a.gf[0] * (Y + (size_t)a.gf[1] * Z)) *
                        a.stride +
@@ -268,7 +262,7 @@ __global__ void k_restrict(XferArgs a, const T* __restrict__ xf,
       xc[((size_t)C * P * P * P + i) * a.stride + a.col] = s;
     } else {
       const int X = cx * K + ix, Y = cy * K + iy, Z = cz * K + iz;
-      if (!on_boundary(X, Y, Z, a.gc))
+      if (!bc_con(a.bcc, X, Y, Z))
         atomicAdd(xc + ((size_t)X + (size_t)a.gc[0] * (Y + (size_t)a.gc[1] * Z)) *
                            a.stride +
                       a.col,
@@ -419,15 +413,14 @@ __global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z,
 
 // Start vector of the eigenvalue estimate: 1 + 0.1 sin(i), 0 on constrained
 // dofs.
-__global__ void k_start_vector(double* v, int64_t n, int g0, int g1, int g2,
+__global__ void k_start_vector(double* v, int64_t n, int g0, int g1, Bc bc,
                                int cg) {
   GRID_STRIDE(i, n) {
     bool con = false;
     if (cg) {
       const int64_t ix = i % g0, iy = (i / g0) % g1,
                     iz = i / ((int64_t)g0 * g1);
-      con = ix == 0 || iy == 0 || iz == 0 || ix == g0 - 1 || iy == g1 - 1 ||
-            iz == g2 - 1;
+      con = bc_con(bc, ix, iy, iz);
     }
     v[i] = con ? 0.0 : 1.0 + 0.1 * sin((double)i);
   }
@@ -507,7 +500,7 @@ template void launch_fill<float>(float*, float, int64_t, cudaStream_t);
 
 void launch_invert_diag(const Level& L, double* diag, cudaStream_t s) {
   k_invert_diag<<<vec_grid(L.ndofs), kVecThreads, 0, s>>>(
-      diag, L.ndofs, L.gdim[0], L.gdim[1], L.gdim[2], L.disc == MFP_CG);
+      diag, L.ndofs, L.gdim[0], L.gdim[1], L.bc, L.disc == MFP_CG);
   MFP_CHECK_CUDA(cudaGetLastError());
   note_launch();
 }
@@ -582,6 +575,8 @@ static XferArgs xfer_args(const Level& fine, const Level& coarse, int stride,
     a.gf[d] = fine.gdim[d];
     a.nf[d] = fine.n[d];
   }
+  a.bcc = coarse.bc;
+  a.bcf = fine.bc;
   a.dg = fine.disc == MFP_SIPG;
   a.stride = stride;
   a.col = col;
@@ -768,7 +763,7 @@ void launch_cg_p(double* p, const double* z, int64_t n, int R,
 }
 void launch_start_vector(const Level& L, double* v, cudaStream_t s) {
   k_start_vector<<<vec_grid(L.ndofs), kVecThreads, 0, s>>>(
-      v, L.ndofs, L.gdim[0], L.gdim[1], L.gdim[2], L.disc == MFP_CG);
+      v, L.ndofs, L.gdim[0], L.gdim[1], L.bc, L.disc == MFP_CG);
   MFP_CHECK_CUDA(cudaGetLastError());
   note_launch();
 }

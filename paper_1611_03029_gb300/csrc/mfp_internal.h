@@ -128,6 +128,25 @@ struct RedScratch {
 };
 
 // ---------------------------------------------------------------------------
+// Boundary conditions of the six sides x_d = lo / hi (side 2d / 2d + 1).
+// CG: node (X, Y, Z) of the node grid is Dirichlet-constrained when one of
+// its coordinates equals the lo / hi entry of its axis; a Neumann side holds
+// -1 there, which no coordinate matches (natural boundary condition, Eq. 4).
+// SIPG: bit 2d + s of `neumann` drops the operator terms of the faces on
+// side (d, s) (the extension of Eq. 7 leaves only data there).
+// ---------------------------------------------------------------------------
+struct Bc {
+  int lo[3] = {0, 0, 0};
+  int hi[3] = {0, 0, 0};
+  int neumann = 0;
+};
+__host__ __device__ __forceinline__ bool bc_con(const Bc& b, int64_t X,
+                                                int64_t Y, int64_t Z) {
+  return X == b.lo[0] || X == b.hi[0] || Y == b.lo[1] || Y == b.hi[1] ||
+         Z == b.lo[2] || Z == b.hi[2];
+}
+
+// ---------------------------------------------------------------------------
 // Level data
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -159,7 +178,9 @@ struct Level {
   int64_t ncells = 0, ndofs = 0, nfaces = 0;
   int gdim[3] = {0, 0, 0};    // CG node grid
   int face_off[3] = {0, 0, 0};
-  double h[3] = {0, 0, 0};
+  double h[3] = {0, 0, 0};     // physical cell size (box length / n)
+  double box_lo = 0.0, box_len = 1.0;  // domain [box_lo, box_lo + box_len]^3
+  Bc bc;
   double kappa = 1.0;
   double penalty = 1.0;
   double map_amp = 0.0;

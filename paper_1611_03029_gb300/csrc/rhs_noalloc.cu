@@ -44,11 +44,13 @@ extern "C" mfp_status mfp_rhs_noalloc(mfp_ctx* ctx, int f_kind,
   try {
     clear_error();
     MFP_REQUIRE(ctx && b_dev, "null argument");
-    MFP_REQUIRE(f_kind == 0 || f_kind == 1, "unknown f_kind");
+    MFP_REQUIRE(f_kind >= 0 && f_kind <= 2, "unknown f_kind");
     MFP_REQUIRE(stride >= 1, "stride must be >= 1");
+    MFP_REQUIRE(f_kind != 2 || !ctx->has_coef,
+                "f_kind 2 needs the constant coefficient");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double* params = nullptr;
-    if (f_kind == 1) {
+    if (f_kind >= 1) {
       MFP_REQUIRE(params_host && n_terms >= 1, "bad Gaussian terms");
       MFP_REQUIRE(n_terms <= kNoAllocMaxTerms,
                   "n_terms exceeds the allocation-free maximum of 4096 "

@@ -31,7 +31,9 @@ class MfpDesc(ctypes.Structure):
                 ("mg_precision", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int),
                 ("eig_cg_iters", ctypes.c_int),
-                ("fp64_arith", ctypes.c_int)]
+                ("fp64_arith", ctypes.c_int),
+                ("neumann_sides", ctypes.c_int),
+                ("box_lo", ctypes.c_double), ("box_hi", ctypes.c_double)]
 
 
 class MfpError(RuntimeError):
@@ -116,6 +118,16 @@ def _stream(stream):
 
 
 _PREC = {"fp64": MFP_FP64, "fp32": MFP_FP32, "mixed": MFP_MIXED}
+
+
+def neumann_mask(sides):
+    """Bit mask of the Neumann sides: side 2e is x_e = lo, 2e+1 is x_e = hi."""
+    m = 0
+    for s in sides:
+        if not 0 <= int(s) <= 5:
+            raise ValueError("Neumann sides are 0..5")
+        m |= 1 << int(s)
+    return m
 _DT = {MFP_FP64: torch.float64, MFP_FP32: torch.float32}
 
 
@@ -126,7 +138,8 @@ class Poisson:
     def __init__(self, nx, ny, nz, degree, disc="cg", n_levels=0,
                  mapping="identity", map_param=0.0, kappa=1.0,
                  penalty_factor=1.0, mg_precision="fp64", cheb_degree=5,
-                 eig_cg_iters=15, fp64_arith="df", stream=None):
+                 eig_cg_iters=15, fp64_arith="df", neumann_sides=(),
+                 box=(0.0, 1.0), stream=None):
         L = lib()
         d = MfpDesc()
         L.mfp_desc_default(ctypes.byref(d))
@@ -142,6 +155,8 @@ class Poisson:
         d.eig_cg_iters = eig_cg_iters
         d.fp64_arith = {"df": MFP_ARITH_DF, "native": MFP_ARITH_NATIVE}[
             fp64_arith]
+        d.neumann_sides = neumann_mask(neumann_sides)
+        d.box_lo, d.box_hi = float(box[0]), float(box[1])
         self.desc = d
         self.disc = disc
         self.degree = degree
