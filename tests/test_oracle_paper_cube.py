@@ -62,3 +62,42 @@ def test_boundary_data_are_consistent():
     pts = P.node_points()
     # Dirichlet exactly on the nodes with some coordinate at +1
     assert np.array_equal(c, np.any(np.isclose(pts, 1.0), axis=1))
+
+
+# ---------------------------------------------------------------------------
+# Exactness: a quadratic u lies in Q_k (k >= 2) and every integrand on affine
+# cells is a polynomial the (k+1)-point Gauss rule integrates exactly, so
+# CG (interpolated Dirichlet data, Sec. 2.1) and SIPG (Eq. 6 / Eq. 7, a
+# consistent method) both return u itself, whatever the Neumann sides.
+# ---------------------------------------------------------------------------
+def _quad_u(x):
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    return 1.0 + X - 2.0 * Y + 0.5 * Z + X * Y - Z * Z + 0.3 * Y * Z
+
+
+def _quad_grad(x):
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    return np.stack([1.0 + Y, -2.0 + X + 0.3 * Z, 0.5 - 2.0 * Z + 0.3 * Y], -1)
+
+
+def _quad_f(x):
+    return np.full(x.shape[:-1], 2.0)      # -Laplace(u)
+
+
+@pytest.mark.parametrize("disc", ["cg", "dg"])
+@pytest.mark.parametrize("sides,box", [((0, 2, 4), (-1.0, 1.0)),
+                                       ((1, 3), (0.0, 1.0)),
+                                       ((5,), (-0.5, 2.0)),
+                                       ((), (-1.0, 1.0))])
+def test_boundary_data_reproduce_quadratics(disc, sides, box):
+    P = fem.Problem(2, 3, 2, 2, disc=disc, box=box, neumann_sides=sides,
+                    penalty_factor=3.0)
+    x = fem.solve_manufactured(P, _quad_f, _quad_u, _quad_grad)
+    assert np.abs(x - fem.interpolate(P, _quad_u)).max() < 1e-11
+
+
+def test_neumann_term_sign_matters():
+    # flipping the Neumann data (a wrong normal orientation) breaks exactness
+    P = fem.Problem(2, 2, 2, 2, box=(-1.0, 1.0), neumann_sides=(0, 3))
+    x = fem.solve_manufactured(P, _quad_f, _quad_u, lambda y: -_quad_grad(y))
+    assert np.abs(x - fem.interpolate(P, _quad_u)).max() > 1e-3
