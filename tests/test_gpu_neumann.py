@@ -109,11 +109,16 @@ def test_boundary_data_rhs(mfp, disc, mapping, k, n, sides, kappa):
     ref = fem.manufactured_rhs(P, lambda x: kappa * cube.f(x), cube.u,
                                cube.grad_u)
     assert rel_err(b, ref) <= 1e-11
-    # a column of a batch (stride) gets the same values
+    # a column of a batch (stride) gets the same values; CG rows are sums
+    # of atomic adds in arbitrary order, equal up to rounding
     R = 3
     out = torch.zeros(P.n_dofs * R, dtype=torch.float64, device="cuda")
     op.rhs(2, cube_params(), out=out[1:], stride=R)
-    assert np.array_equal(out.reshape(-1, R)[:, 1].cpu().numpy(), b)
+    col = out.reshape(-1, R)[:, 1].cpu().numpy()
+    if disc == "dg":
+        assert np.array_equal(col, b)
+    else:
+        assert rel_err(col, b) <= 1e-14
 
 
 @pytest.mark.parametrize("disc,k,n,limit", [("cg", 2, (8, 8, 8), 20),
