@@ -1,7 +1,8 @@
 """Seeded synthetic inputs shared by the tests, bench.py and the oracle
 legs.  Holds none of the method's arithmetic: random vectors, the
-Gaussian-sum forcing parameters and the log-coefficient Fourier field
-sampled at the physical positions of the Gauss points of a Cartesian mesh.
+Gaussian-sum forcing parameters, the log-coefficient Fourier field and the
+strongly varying coefficient sampled at the physical positions of the Gauss
+points of a Cartesian mesh.
 """
 import numpy as np
 
@@ -111,3 +112,23 @@ def log_coefficient(n, p, seed):
     a_cell = np.exp(fourier_field(modes, cell_points(n, p)))
     a_face = np.exp(fourier_field(modes, face_points(n, p)))
     return a_cell, a_face
+
+
+def strong_coefficient_field(x):
+    """The strongly varying diffusivity of the paper's shell example (Sec. 5),
+    1 + 10^6 prod_e cos(2 pi x_e + 0.1 e) for e = 1, 2, 3, read with the
+    product in absolute value: as printed it is negative on about half of any
+    domain, which no SPD solver accepts; the absolute value keeps its
+    contrast (10^6) and its pattern."""
+    e = np.arange(1, 4)
+    return 1.0 + 1e6 * np.abs(np.prod(np.cos(2.0 * np.pi * x + 0.1 * e), -1))
+
+
+def strong_coefficient(n, p, box=(-1.0, 1.0)):
+    """strong_coefficient_field at all cell and face Gauss points of the
+    Cartesian mesh of [box_lo, box_hi]^3."""
+    lo, hi = box
+    a_cell = strong_coefficient_field(lo + (hi - lo) * cell_points(n, p))
+    a_face = strong_coefficient_field(lo + (hi - lo) * face_points(n, p))
+    return a_cell, a_face
+

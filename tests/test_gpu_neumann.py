@@ -172,3 +172,29 @@ def test_gradient_with_neumann_sides(mfp, disc):
     assert rel_err(gc.cpu().numpy(), rc) <= 1e-12
     if disc == "dg":
         assert rel_err(gf.cpu().numpy(), rf) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Strongly varying coefficient (the paper's shell diffusivity on the brick
+# (-1, 1)^3, contrast 10^6; synthetic.strong_coefficient): the GPU hierarchy
+# takes the same V-cycle as the oracle's, so PCG needs the oracle's
+# iteration count, and the solution meets the residual on the oracle's
+# matrix.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("disc,k,n", [("cg", 2, 8), ("dg", 2, 8),
+                                      ("cg", 3, 8), ("dg", 1, 8)])
+def test_strong_coefficient_solve(mfp, disc, k, n):
+    N3 = (n, n, n)
+    a_cell, a_face = synthetic.strong_coefficient(N3, k + 1, box=BOX)
+    op = mfp.Poisson(*N3, k, disc=disc, box=BOX)
+    op.set_coefficient(cuda(a_cell), cuda(a_face))
+    P = fem.Problem(*N3, k, disc=disc, box=BOX, a_cell=a_cell, a_face=a_face)
+    b = op.rhs(0)
+    x, its, _ = op.solve(b, rtol=1e-10, max_it=300)
+    V = mg.VCycle(P)
+    A = V.levels[-1].A
+    bh, xh = b.cpu().numpy(), x.cpu().numpy()
+    assert rel_err(bh, fem.load_vector(P, fem.sine_forcing)) <= 1e-12
+    assert np.linalg.norm(bh - A @ xh) / np.linalg.norm(bh) <= 1.05e-10
+    _, its_oracle = mg.pcg(A, bh, V.apply, rtol=1e-10, max_it=300)[:2]
+    assert its[0] <= its_oracle + 1, (its, its_oracle)
