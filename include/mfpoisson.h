@@ -122,7 +122,9 @@ void mfp_desc_default(mfp_desc* desc);
  * one level and at most 2048 dofs on the coarsest level, that level's
  * operator is also assembled once as a dense matrix (from matrix-free
  * applies to identity columns) for the coarse Chebyshev solve.  Synchronises
- * `stream`.  *out receives an opaque handle owned by the library. */
+ * `stream`.  *out receives an opaque handle owned by the library.  Start
+ * `desc` from mfp_desc_default: a zero-filled one is rejected (box_hi must
+ * exceed box_lo).  Invalid fields return MFP_ERR_ARG before any CUDA call. */
 mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out);
 
 /* Free all device and host memory of the context (synchronises the device
