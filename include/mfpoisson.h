@@ -2,7 +2,8 @@
  * mfpoisson.h - C ABI of the GB300 matrix-free high-order Poisson library.
  *
  * The library evaluates the operator of -div(kappa grad u) = f (Sec. 2,
- * Eq. 1) on a structured hexahedral brick of the unit cube without
+ * Eq. 1) on a structured hexahedral brick of the unit cube (or of a cube
+ * [box_lo, box_hi]^3, optionally curved by an analytic map) without
  * assembling a matrix: cell integrals by sum factorization (Sec. 3, Eq. 12)
  * for continuous Q_k elements (Sec. 2.1, Eq. 4) and for the symmetric
  * interior penalty DG method (Sec. 2.2, Eq. 6, boundary extension Eq. 7),
@@ -23,11 +24,13 @@
  *    frees it in mfp_destroy().
  *
  * Vector layouts (level l of a context; level n_levels-1 is the finest)
- *  - cells c = cx + nx*(cy + ny*cz), cell size 1/nx x 1/ny x 1/nz;
+ *  - cells c = cx + nx*(cy + ny*cz), cell size L/nx x L/ny x L/nz before
+ *    the mapping, L = box_hi - box_lo (1 by default);
  *  - local node / quadrature point a = ax + p*ay + p*p*az, p = k+1, x fastest;
  *  - CG (disc = MFP_CG): one value per node of the (nx k+1)(ny k+1)(nz k+1)
- *    grid, x fastest; boundary nodes are present and carry the identity
- *    rows / columns of the eliminated Dirichlet conditions (Sec. 2.1);
+ *    grid, x fastest; boundary nodes are present, and those on Dirichlet
+ *    sides carry the identity rows / columns of the eliminated Dirichlet
+ *    conditions (Sec. 2.1);
  *  - SIPG (disc = MFP_SIPG): cell-major blocks of p^3 nodal values;
  *  - batched vectors (n_rhs = R > 1): entry (i, r) at [i*R + r];
  *  - cell coefficient / gradient: [ncells][p^3] in local quadrature order;
