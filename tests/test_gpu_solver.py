@@ -86,6 +86,19 @@ def test_vcycle(mfp, disc, mapping, k, n):
     assert rel_err(z, V.apply(r)) <= 1e-9
 
 
+@pytest.mark.parametrize("disc,mapping,k,n", CASES)
+def test_vcycle_float32(mfp, disc, mapping, k, n):
+    # the float V-cycle of a mixed-precision context against the oracle's
+    # float64 V-cycle: float rounding through about 25 operator applications,
+    # the transfers and the coarse solve (the float64 V-cycle meets 1e-9)
+    op, P = pair(mfp, disc, mapping, k, n, prec="fp32")
+    V = mg.VCycle(P)
+    r = synthetic.random_vector(P.n_dofs, seed=3)
+    r[P.constrained()] = 0.0
+    z = op.vcycle(cuda(r)).cpu().numpy()
+    assert rel_err(z, V.apply(r)) <= 1e-4
+
+
 @pytest.mark.parametrize("disc,mapping,k,n,limit", [
     ("cg", "identity", 2, (8, 8, 8), 8),      # 17^3 = 4913 dofs
     ("dg", "identity", 2, (8, 8, 8), 16),

@@ -41,6 +41,24 @@ def test_rhs_noalloc_matches_rhs(mfp, disc, stride):
         assert rel_err(got, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("disc", ["cg", "dg"])
+def test_rhs_noalloc_boundary_data(mfp, disc):
+    # f_kind 2 (Dirichlet and Neumann data of a Gaussian sum) on a box with
+    # Neumann sides; CG rows are atomic sums, equal up to rounding
+    lib = mfp.lib()
+    op = mfp.Poisson(3, 2, 2, 2, disc=disc, n_levels=1, neumann_sides=(0, 3),
+                     box=(-1.0, 1.0))
+    g = np.array([[-0.5, 0.5, 0.25, 0.2, 2.0], [0.5, -0.5, 0.5, 0.3, -1.0]])
+    ref = op.rhs(2, g).cpu().numpy()
+    out = torch.zeros(op.n_dofs(), dtype=torch.float64, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = lib.mfp_rhs_noalloc(op._h, 2, _dp(g), g.shape[0],
+                             ctypes.c_void_p(out.data_ptr()), 1, s)
+    assert st == mfp.MFP_OK, lib.mfp_last_error()
+    torch.cuda.synchronize()
+    assert rel_err(out.cpu().numpy(), ref) <= 1e-14
+
+
 def test_rhs_noalloc_rejects_too_many_terms(mfp):
     lib = mfp.lib()
     op = mfp.Poisson(2, 2, 2, 1, n_levels=1)
