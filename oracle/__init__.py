@@ -26,8 +26,12 @@ Modules
            estimate, transfer, coarse Chebyshev solve, V-cycle, PCG (Sec. 4.1)
   adjoint  assembled coefficient derivative and dL/da (not in the paper)
   rows     sampled rows of the operator for large meshes (Eq. 12)
+  hdg      hybridizable DG blocks, the statically condensed trace solve, the
+           element-by-element post-processing and the mixed HDG operator
+           (Sec. 2.3, Sec. 3 "HDG mixed matrix-free"), pinned against the
+           HDG L2 errors the paper prints
 
-Parity status: every function is pinned by tests in tests/test_oracle_*.py
-except the mixed-precision V-cycle internals, which have no oracle at all
-(parity unpinned; only the final float64 residual is checked).
+Parity status: every function is pinned by tests in tests/test_oracle_*.py.
+The float32 V-cycle of the mixed-precision path has no float32 oracle: it is
+compared with the float64 V-cycle within a float tolerance.
 """
