@@ -192,6 +192,23 @@ mfp_status mfp_rhs_noalloc(mfp_ctx* ctx, int f_kind, const double* params_host,
                            int n_terms, double* b_dev, int64_t stride,
                            void* stream);
 
+/* HDG mixed matrix-free operator (Sec. 3, "HDG mixed matrix-free", on the
+ * hybridizable DG form of Sec. 2.3):
+ *   y = ([A B^T; B D] + [C^T; G^T] H^{-1} [C G]) x
+ * on the finest cells of an SIPG context (same mesh, box and Neumann sides),
+ * with A = (w, kappa^-1 q), B^T = -(div w, u), D = -<v, tau u>,
+ * C^T = <w . n, lambda>, G^T = <v, tau lambda>, H = sum <mu, tau lambda> and
+ * tau = tau_factor kappa (Sec. 5: tau_factor 5).  Dirichlet faces hold data
+ * traces and add no H^{-1} coupling.  x_dev and y_dev hold the cell unknowns
+ * (q_x, q_y, q_z, u) in cell-major blocks of 4 (k+1)^3 nodal values (the
+ * SIPG cell layout per field), 4 ncells (k+1)^3 doubles each, distinct.
+ * Cartesian cells (MFP_MAP_IDENTITY) and the constant coefficient only
+ * (MFP_ERR_ARG otherwise).  The first call allocates the context's trace
+ * buffer (nfaces (k+1)^2 doubles): make it outside a stream capture.
+ * Launches four kernels (traces per face direction, then the cells). */
+mfp_status mfp_hdg_apply(mfp_ctx* ctx, double tau_factor, const double* x_dev,
+                         double* y_dev, void* stream);
+
 /* dst = A src on `level` (Eq. 12, plus the SIPG face terms of Eq. 6/7 and
  * identity rows / columns for CG Dirichlet nodes).  prec MFP_FP64 takes
  * double vectors, MFP_FP32 float vectors (FP32 level data must exist, i.e.

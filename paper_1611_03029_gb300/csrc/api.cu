@@ -445,6 +445,7 @@ void free_ctx(mfp_ctx* c) {
   dfree(c->hist);
   dfree(c->eig_out);
   dfree(c->params);
+  dfree(c->hdg_lam);
   dfree(c->red.part);
   dfree(c->red.cnt);
   dfree(c->mix_r);
@@ -780,6 +781,22 @@ mfp_status mfp_rhs(mfp_ctx* c, int f_kind, const double* params, int nterms,
     MFP_CHECK_CUDA(cudaStreamSynchronize(s));  // host params may go away
   }
   launch_rhs(c->levels.back(), f_kind, c->params, nterms, b, stride, s);
+  API_END
+}
+
+mfp_status mfp_hdg_apply(mfp_ctx* c, double tau_factor, const double* x,
+                         double* y, void* stream) {
+  API_BEGIN
+  MFP_REQUIRE(c && x && y && x != y, "x / y must be distinct non-null");
+  MFP_REQUIRE(c->desc.disc == MFP_SIPG,
+              "the HDG operator uses the cells of an SIPG context");
+  Level& L = c->levels.back();
+  MFP_REQUIRE(!L.curved, "HDG apply: Cartesian cells only");
+  MFP_REQUIRE(!c->has_coef, "HDG apply: constant coefficient only");
+  MFP_REQUIRE(tau_factor > 0 && std::isfinite(tau_factor),
+              "tau_factor must be > 0");
+  if (!c->hdg_lam) c->hdg_lam = dalloc<double>(L.nfaces * L.p * L.p);
+  launch_hdg_apply(L, tau_factor * L.kappa, c->hdg_lam, x, y, st(stream));
   API_END
 }
 

@@ -238,6 +238,7 @@ struct mfp_ctx {
   double* eig_out = nullptr;
   double* params = nullptr; // device copy of forcing parameters
   int params_cap = 0;
+  double* hdg_lam = nullptr;    // HDG traces at the face points [nfaces][p^2]
   mfp::RedScratch red;
   double* host_scal = nullptr;  // pinned [S_COUNT][kMaxRhs]
   float* mix_r = nullptr;       // float V-cycle input / output on the finest
@@ -302,6 +303,9 @@ void launch_coarsen_coefficient(const Level& fine, const Level& coarse,
 void launch_start_vector(const Level& L, double* v, cudaStream_t s);
 void launch_gradient(const Level& L, const double* u, const double* lam,
                      double* gc, double* gf, cudaStream_t s);
+// HDG mixed operator on Cartesian cells (k_hdg.cu); lam: [nfaces][p^2]
+void launch_hdg_apply(const Level& L, double tau, double* lam,
+                      const double* x, double* y, cudaStream_t s);
 
 template <typename T>
 void launch_prolongate(const Level& fine, const Level& coarse, const T* xc,

@@ -71,6 +71,8 @@ def lib():
                                                ctypes.c_int64, vp]),
             "mfp_apply": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp,
                                          vp, ctypes.c_int, vp]),
+            "mfp_hdg_apply": (ctypes.c_int, [vp, ctypes.c_double, vp, vp,
+                                             vp]),
             "mfp_inverse_diagonal": (ctypes.c_int, [vp, ctypes.c_int,
                                                     ctypes.c_int, vp, vp]),
             "mfp_level_info": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, dp,
@@ -221,6 +223,15 @@ class Poisson:
         _check(lib().mfp_apply(self._h, self._lvl(level), prec, _ptr(src),
                                _ptr(dst), n_rhs, _stream(stream)))
         return dst
+
+    def hdg_apply(self, x, y=None, tau_factor=5.0, stream=None):
+        """HDG mixed operator on the cell unknowns (q_x, q_y, q_z, u),
+        cell-major blocks of 4 (k+1)^3 values (SIPG contexts)."""
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().mfp_hdg_apply(self._h, tau_factor, _ptr(x), _ptr(y),
+                                   _stream(stream)))
+        return y
 
     def inverse_diagonal(self, level=None, dtype=torch.float64, stream=None):
         lv = self._lvl(level)
