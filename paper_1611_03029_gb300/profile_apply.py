@@ -25,6 +25,9 @@ def main(argv=None):
     ap.add_argument("--arith", default="df", choices=["df", "native"],
                     help="float64 arithmetic: double-float or DFMA")
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--hdg", action="store_true",
+                    help="the HDG mixed operator on (q, u) (Cartesian, SIPG "
+                         "cells, float64)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--reps", type=int, default=20)
     a = ap.parse_args(argv)
@@ -42,22 +45,34 @@ def main(argv=None):
                    fp64_arith=a.arith)
     dt = torch.float64 if a.prec == "f64" else torch.float32
     N = op.n_dofs()
-    src = torch.randn(N * a.nrhs, dtype=dt, device="cuda")
+    if a.hdg:
+        if a.disc != "dg" or a.curved or a.prec != "f64" or a.nrhs != 1:
+            raise SystemExit("--hdg needs --disc dg, Cartesian cells, f64")
+        src = torch.randn(4 * N, dtype=dt, device="cuda")
+
+        def run(x, y):
+            op.hdg_apply(x, y)
+    else:
+        src = torch.randn(N * a.nrhs, dtype=dt, device="cuda")
+
+        def run(x, y):
+            op.apply(x, y, n_rhs=a.nrhs)
     dst = torch.empty_like(src)
     for _ in range(a.warmup):
-        op.apply(src, dst, n_rhs=a.nrhs)
+        run(src, dst)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
     for _ in range(a.reps):
-        op.apply(src, dst, n_rhs=a.nrhs)
+        run(src, dst)
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / a.reps * 1e-3
     print(json.dumps({"disc": a.disc, "cells": n, "degree": a.degree,
                       "curved": a.curved, "prec": a.prec, "nrhs": a.nrhs,
                       "arith": a.arith if a.prec == "f64" else "f32",
+                      "hdg": a.hdg, "unknowns": src.numel(),
                       "dofs": N, "ms": t * 1e3,
                       "MDoF_s": N * a.nrhs / t / 1e6,
                       "cells_per_block": os.environ.get(
