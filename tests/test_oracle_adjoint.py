@@ -7,8 +7,9 @@ import scipy.sparse.linalg as sla
 from oracle import adjoint, fem
 
 
-@pytest.mark.parametrize("disc", ["cg", "dg"])
-def test_gradient_matches_finite_differences(disc):
+@pytest.mark.parametrize("disc,sides", [("cg", ()), ("dg", ()),
+                                        ("cg", (1, 2)), ("dg", (1, 2))])
+def test_gradient_matches_finite_differences(disc, sides):
     rng = np.random.default_rng(11)
     shape = fem.Problem(2, 2, 1, 2, disc=disc)
     a_c = np.exp(0.3 * rng.standard_normal((shape.ncells, 27)))
@@ -17,7 +18,7 @@ def test_gradient_matches_finite_differences(disc):
 
     def solve(ac, af):
         P = fem.Problem(2, 2, 1, 2, disc=disc, mapping="sine", amp=0.1,
-                        a_cell=ac, a_face=af)
+                        a_cell=ac, a_face=af, neumann_sides=sides)
         A = fem.assemble(P)
         u = sla.spsolve(A.tocsc(), fem.load_vector(P, fem.sine_forcing))
         return P, A, u
@@ -36,3 +37,10 @@ def test_gradient_matches_finite_differences(disc):
         assert abs(fd - an) <= 1e-6 * abs(an)
     if disc == "cg":
         assert np.all(gf == 0)
+    else:
+        # faces on Neumann sides carry no term of the form (Eq. 7)
+        for side in sides:
+            d, s = side // 2, side % 2
+            fid, left, right = fem.face_cells(P, d)
+            bnd = fid[(right < 0) if s else (left < 0)]
+            assert np.all(gf[bnd] == 0)
