@@ -342,3 +342,49 @@ def mixed_rhs(prob, f, u_exact, grad_u, tau=None):
     Fc -= np.einsum("caj,cj->ca", Nc, lamf[fids].reshape(prob.ncells, -1))
     return Fc.reshape(-1)
 
+
+
+def mixed_apply_cells(prob, x, cells, tau=None):
+    """Rows of the mixed operator for the listed cells only (for meshes too
+    large to assemble): y_c = M_c x_c + sum over the non-Dirichlet faces f of
+    c of N_c,f H_f^{-1} sum over the cells c' of f of N_c',f^T x_c'.
+    x is the full cell-major vector; returns [len(cells), 4 p^3]."""
+    F = prob.p ** 2
+    if tau is None:
+        tau = tau_faces(prob)
+    cells = np.asarray(cells)
+    n4 = 4 * prob.p ** 3
+    X = np.asarray(x).reshape(prob.ncells, n4)
+    side = face_sides(prob)
+    dir_face = (side >= 0) & ~np.isin(side, list(prob.neumann))
+    # the listed cells and every cell across one of their faces
+    fids_c = cell_face_ids(prob, cells)
+    need = set(int(c) for c in cells)
+    owners = {}
+    for d in range(3):
+        fid, left, right = fem.face_cells(prob, d)
+        sel = np.isin(fid, fids_c.ravel())
+        for f, L, R in zip(fid[sel], left[sel], right[sel]):
+            owners[int(f)] = [int(c) for c in (L, R) if c >= 0]
+            need.update(owners[int(f)])
+    need = np.array(sorted(need))
+    M, Nc, Hs, fids = local_blocks(prob, need, tau)
+    pos = {int(c): i for i, c in enumerate(need)}
+    out = np.zeros((cells.size, n4))
+    for r, c in enumerate(cells):
+        i = pos[int(c)]
+        y = M[i] @ X[c]
+        for j in range(6):
+            f = int(fids[i, j])
+            if dir_face[f]:
+                continue
+            H = np.zeros((F, F))
+            g = np.zeros(F)
+            for c2 in owners[f]:
+                i2 = pos[c2]
+                j2 = int(np.nonzero(fids[i2] == f)[0][0])
+                H += Hs[i2, j2]
+                g += Nc[i2][:, j2 * F:(j2 + 1) * F].T @ X[c2]
+            y += Nc[i][:, j * F:(j + 1) * F] @ np.linalg.solve(H, g)
+        out[r] = y
+    return out

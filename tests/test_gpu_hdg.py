@@ -34,6 +34,24 @@ def test_hdg_apply_matches_oracle(mfp, k, n, sides, box, kappa):
     assert np.array_equal(y, y2)
 
 
+def test_hdg_apply_full_size_sampled_cells(mfp):
+    # 32^3 cells, Q4, Cartesian: the size bench.py times; the oracle
+    # evaluates the rows of sampled cells (corners, faces, interior) one by
+    # one
+    n, k = 32, 4
+    op = mfp.Poisson(n, n, n, k, disc="dg", n_levels=1)
+    P = fem.Problem(n, n, n, k, disc="dg")
+    x = synthetic.random_vector(4 * op.n_dofs(), seed=81)
+    y = op.hdg_apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    rng = np.random.default_rng(6)
+    cells = np.concatenate([[0, n - 1, n * n - 1, P.ncells - 1,
+                             P.ncells // 2 + n // 2],
+                            rng.choice(P.ncells, 15, replace=False)])
+    ref = hdg.mixed_apply_cells(P, x, cells)
+    got = y.reshape(P.ncells, -1)[cells]
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 def test_hdg_apply_rejects_unsupported(mfp):
     x = torch.zeros(4 * 8 * 8, dtype=torch.float64, device="cuda")
     for kw in (dict(disc="cg"), dict(disc="dg", mapping="sine",

@@ -112,3 +112,19 @@ def test_hdg_converges_at_k_plus_1_and_post_at_k_plus_2():
         post.append(fem.l2_error(P2, ust, fem.sine_solution))
     assert np.log2(errs[0] / errs[1]) > 3 - 0.3, errs
     assert np.log2(post[0] / post[1]) > 4 - 0.3, post
+
+
+@pytest.mark.parametrize("mapping,sides", [("identity", (0, 2, 4)),
+                                           ("sine", (5,))])
+def test_mixed_rows_of_listed_cells(mapping, sides):
+    # the per-cell evaluation used at sizes too large to assemble agrees
+    # with the assembled mixed operator
+    P = fem.Problem(3, 2, 3, 2, disc="dg", mapping=mapping,
+                    amp=0.1 if mapping == "sine" else 0.0, box=(-1.0, 1.0),
+                    neumann_sides=sides)
+    A = hdg.mixed_operator(P)
+    x = np.random.default_rng(5).standard_normal(A.shape[0])
+    ref = (A @ x).reshape(P.ncells, -1)
+    cells = np.array([0, 4, P.ncells - 1, 7])
+    got = hdg.mixed_apply_cells(P, x, cells)
+    assert np.abs(got - ref[cells]).max() <= 1e-13 * np.abs(ref).max()
