@@ -198,3 +198,23 @@ def test_strong_coefficient_solve(mfp, disc, k, n):
     assert np.linalg.norm(bh - A @ xh) / np.linalg.norm(bh) <= 1.05e-10
     _, its_oracle = mg.pcg(A, bh, V.apply, rtol=1e-10, max_it=300)[:2]
     assert its[0] <= its_oracle + 1, (its, its_oracle)
+
+
+@pytest.mark.parametrize("disc", ["cg", "dg"])
+def test_full_size_neumann_sampled_rows(mfp, disc):
+    # 32^3 cells, Q4, curved, the timed size, on (-1, 1)^3 with the Neumann
+    # sides of the paper's example; rows sampled on those sides, on the
+    # Dirichlet sides and inside
+    from oracle import rows
+    n, k, sides = (32, 32, 32), 4, (0, 2, 4)
+    op = mfp.Poisson(*n, k, disc=disc, mapping="sine", map_param=0.1,
+                     n_levels=1, neumann_sides=sides, box=BOX)
+    N = op.n_dofs()
+    u = synthetic.random_vector(N, seed=22)
+    y = op.apply(cuda(u)).cpu().numpy()
+    P = problem(disc, "sine", k, n, sides)
+    rng = np.random.default_rng(7)
+    r = np.concatenate([rng.choice(N, 30, replace=False),
+                        [0, N - 1, N // 2, 1, N - 2]])
+    ref = rows.apply_rows(P, u, r)
+    assert np.abs(y[r] - ref).max() <= 1e-12 * np.abs(ref).max()
