@@ -14,6 +14,7 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -442,6 +443,35 @@ def run_ours(args):
     except Exception as exc:  # reported, never fatal to the contract line
         apply["hdg_f64_cartesian"] = {"error": str(exc)[:200]}
 
+    # --- the paper's smooth example (Sec. 5): three Gaussians on (-1, 1)^3,
+    # Neumann data on x_e = -1, 32^3 cells Q4 (its 32768-cell row) --------
+    paper_cube = {}
+    try:
+        s3 = (1.0 / (0.2 * math.sqrt(2.0 * math.pi))) ** 3
+        gauss = [[-0.5, 0.5, 0.25, 0.2, s3], [-0.6, -0.5, -0.125, 0.2, s3],
+                 [0.5, -0.5, 0.5, 0.2, s3]]
+        for d, pf in (("cg", 1.0), ("dg", 3.0)):
+            opc = M.Poisson(n, n, n, DEGREE, disc=d, neumann_sides=(0, 2, 4),
+                            box=(-1.0, 1.0), penalty_factor=pf)
+            bc = opc.rhs(2, gauss)
+            xc = torch.empty_like(bc)
+            opc.solve(bc, xc, rtol=RTOL, max_it=200)
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+                enable_timing=True)
+            flush.fill_(3.0)
+            c0.record(stream)
+            _, itc, relc = opc.solve(bc, xc, rtol=RTOL, max_it=200)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            tc = c0.elapsed_time(c1)
+            paper_cube[d] = {"ms": tc, "iterations": itc[0],
+                             "relres": relc[0],
+                             "dofs": opc.n_dofs(),
+                             "DoF_s": opc.n_dofs() / (tc * 1e-3)}
+            del opc, bc, xc
+    except Exception as exc:  # reported, never fatal to the contract line
+        paper_cube["error"] = str(exc)[:200]
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -482,6 +512,7 @@ def run_ours(args):
                   "iterations": {d: its_mixed[d][0] for d in its_mixed},
                   "speedup_vs_fp64": ms / mixed_ms},
         "apply": apply,
+        "paper_cube": paper_cube,
         "cells_per_block": tuned,
         "roofline": roof,
         "e2e": {"value": dofs_step / (e2e_ms * 1e-3), "unit": "DoF/s",
