@@ -1,14 +1,19 @@
 """Benchmark of the GB300 matrix-free Poisson multigrid solver.
 
 Workload (default): continuous Q4 and SIPG DG_Q4 on 32^3 cells of the curved
-mesh x -> x + 0.1 sin(pi x) sin(pi y) sin(pi z), float64 throughout,
-manufactured sine right-hand side.  One step = one V-cycle preconditioned
-CG solve to 1e-10 relative residual of each discretization (every stage of
-the hot path: cell and face kernels, Jacobi-Chebyshev smoothing, transfer,
-coarse solve, fused CG updates and reductions).  `value` = dofs solved per
-second over both solves (float64); the JSON line also carries the operator
-apply throughput (MDoF/s) in float64 and float32 and the mixed-precision
-solve rate.
+mesh x -> x + 0.1 sin(pi x) sin(pi y) sin(pi z), manufactured sine
+right-hand side.  One step = one V-cycle preconditioned CG solve to 1e-10
+relative residual of each discretization (every stage of the hot path: cell
+and face kernels, Jacobi-Chebyshev smoothing, transfer, coarse solve, fused
+CG updates and reductions).  `value` = dofs solved per second over both
+solves with float64 vectors and double-float operator arithmetic (key
+"arith"); the line also carries the same solves with a float32 V-cycle
+("mixed") and with IEEE float64 applies ("fp64_native"), every apply's
+throughput with its HBM and pipe fractions, the paper's smooth example, and
+the other workloads ("configs": latency, degree sweep, 16 batched
+right-hand sides, adjoint gradient).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -38,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=N_CELLS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave the other workloads out of the contract line")
     ap.add_argument("--workload", default="solve",
                     choices=["solve", "latency", "sweep", "batched",
                              "gradient"],
@@ -174,13 +181,16 @@ def hdg_flops(k, ncells):
 
 
 def apply_bytes(disc, k, n, curved, word=8):
-    """Compulsory DRAM bytes of one apply: source read, destination written
-    (CG: plus the zero fill), stored geometry (6 words per cell point) and,
-    for curved SIPG, 7 words per face point plus one per face."""
+    """Algorithmic DRAM bytes of one apply: source read once, destination
+    written once, stored geometry (6 words per cell point) and, for curved
+    SIPG, 7 words per face point plus one per face (the per-dof figures of
+    the algorithmic-work table: curved Q4 110 B/dof CG and 98 B/dof SIPG in
+    float64).  Index arrays are not needed (structured brick) and the CG
+    destination's zero fill is an implementation cost, not counted."""
     p = k + 1
     ncells = n ** 3
     ndofs = (n * k + 1) ** 3 if disc == "cg" else ncells * p ** 3
-    b = 2 * ndofs * word + (ndofs * word if disc == "cg" else 0)
+    b = 2 * ndofs * word
     if curved:
         b += 6 * ncells * p ** 3 * word
         if disc == "dg":
@@ -189,11 +199,25 @@ def apply_bytes(disc, k, n, curved, word=8):
     return float(b)
 
 
-# FP64 pipe peak of the GB300 from its unit counts: 152 SMs x 2 DFMA per
-# clock per SM x 2 flop x 2.07 GHz = 1258.6 GFLOP/s (a DFMA-chain probe on
-# this pool measured 1254.6).  FP32: 152 x 128 FFMA x 2 x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # probe measured 73.2
+# Float64 flops per dof of the SIPG apply in the algorithmic-work table of
+# the scope (12 sweeps of p^4 multiply-adds per cell, about 15 flops per
+# point, faces at the Cartesian cost); apply_flops also counts the curved
+# tangential face terms, so the line reports the fraction at both counts.
+SURVEY_DG_FLOPS_PER_DOF = {1: 156, 2: 165, 3: 182, 4: 201, 6: 244, 8: 289}
+
+
+def fp32_pipe_peak_tflops(sm_count, sm_mhz):
+    """FP32-pipe peak from the unit counts: SMs x 128 FFMA per clock x 2 flop
+    x the maximum SM clock (GB300: 152 x 128 x 2 x 2.07 GHz = 80.5 TFLOP/s;
+    an FFMA-chain probe on this GPU measured 73.2)."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp64_pipe_peak_tflops(sm_count, sm_mhz):
+    """FP64-pipe peak: SMs x 2 DFMA per clock x 2 flop x clock (GB300:
+    1.26 TFLOP/s; a DFMA-chain probe measured 1.25)."""
+    return sm_count * 2 * 2 * sm_mhz * 1e6 / 1e12
+
 
 # DRAM traffic (read + write) per launch of the dominant kernel from one ncu
 # capture, keyed by a hash of the sources it was compiled from; a kernel
@@ -251,11 +275,13 @@ def cpu_baseline(n=8):
     dofs, its = oracle_sample_solve(setup)
     t = time.time() - t0
     return {"value": dofs / t, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "host_cpus": os.cpu_count(), "cpu_model": cpu_model(),
             "sample": "oracle assembled-matrix V-cycle PCG to 1e-10, CG and "
                       "SIPG Q4 on the same curved map with %d^3 cells "
                       "(%d dofs, its %s); solve time only (setup %.1f s "
-                      "excluded, as on the GPU); scipy sparse products run "
-                      "on one thread" % (n, dofs, its, t_setup)}
+                      "excluded, as on the GPU); the oracle's scipy sparse "
+                      "products run on one thread of the %s host CPUs"
+                      % (n, dofs, its, t_setup, os.cpu_count())}
 
 
 def run_reference(args):
@@ -282,7 +308,8 @@ def run_reference(args):
                        "8^3-cell bounded sample of the 32^3 workload",
                        "cells": 8, "degree": DEGREE, "rtol": RTOL},
             "cpu_baseline": {"value": v, "unit": "DoF/s", "cores": 1,
-                             "kind": "oracle",
+                             "kind": "oracle", "host_cpus": os.cpu_count(),
+                             "cpu_model": cpu_model(),
                              "sample": "8^3 cells CG+SIPG Q4 curved, "
                                        "solve only"},
             "e2e": {"value": v, "unit": "DoF/s", "h2d_bytes_per_step": 0,
@@ -293,6 +320,98 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def _events():
+    import torch
+    return (torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True))
+
+
+def timed_runs(fn, stream, n, flush=None):
+    """n runs of fn, each between its own pair of CUDA events recorded on
+    `stream` (the stream the library launches on), the L2 flushed by a
+    256 MB write before each run; returns the per-run milliseconds."""
+    out = []
+    for i in range(n):
+        if flush is not None:
+            flush.fill_(float(i))
+        e0, e1 = _events()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def stats(ts):
+    s = sorted(ts)
+    return {"min_ms": s[0], "median_ms": s[len(s) // 2],
+            "mean_ms": sum(s) / len(s), "runs": len(s)}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True,
+                             timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+ARITH = ("double-float: vectors float64 in HBM; the operator applies (cell, "
+         "face, diagonal, gradient kernels) carry every intermediate as an "
+         "unevaluated pair of floats on the FP32 pipes (error-free TwoSum and "
+         "FMA TwoProd, about 2^-46 relative per operation); CG updates, dot "
+         "products, Chebyshev updates and transfers in IEEE float64. "
+         "fp64_native holds the same solve with IEEE float64 (DFMA) applies")
+
+
+def measure_applies(M, ops, native, mixed, N, n, stream, flush, reps,
+                    hbm_gbs, sm_count, sm_mhz):
+    """Per-launch CUDA-event timing of every fine-level apply (L2 flushed
+    before each launch) with its HBM and pipe fractions."""
+    import torch
+    res = {}
+    p32 = fp32_pipe_peak_tflops(sm_count, sm_mhz)
+    p64 = fp64_pipe_peak_tflops(sm_count, sm_mhz)
+    for tag, opset, dt in (("f64", ops, torch.float64),
+                           ("f64_native", native, torch.float64),
+                           ("f32", mixed, torch.float32)):
+        word = 4 if dt == torch.float32 else 8
+        for d in ("cg", "dg"):
+            src = torch.randn(N[d], dtype=dt, device="cuda")
+            dst = torch.empty_like(src)
+            for _ in range(3):
+                opset[d].apply(src, dst)
+            ts = timed_runs(lambda: opset[d].apply(src, dst), stream,
+                            reps, flush)
+            st_ = stats(ts)
+            t = st_["mean_ms"] * 1e-3
+            fl = apply_flops(d, DEGREE, n ** 3, True)
+            by = apply_bytes(d, DEGREE, n, True, word)
+            e = {"launch": stats(ts), "MDoF_s": N[d] / t / 1e6,
+                 "equiv_MDoF_s": n ** 3 * DEGREE ** 3 / t / 1e6,
+                 "GFLOP_s": fl / t / 1e9,
+                 "algorithmic_bytes": by, "GB_s": by / t / 1e9,
+                 "hbm_frac": by / t / 1e9 / hbm_gbs}
+            if tag == "f64":
+                e["fp32_pipe_TFLOP_s"] = DF_FLOPS_PER_FP64_FLOP * fl / t / 1e12
+                e["fp32_pipe_frac"] = e["fp32_pipe_TFLOP_s"] / p32
+            elif tag == "f64_native":
+                e["fp64_pipe_frac"] = fl / t / 1e12 / p64
+            else:
+                e["fp32_pipe_frac"] = fl / t / 1e12 / p32
+            res[tag + "_" + d] = e
+            del src, dst
+    return res
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -311,20 +430,26 @@ def run_ours(args):
 
     n = args.cells
     stream = torch.cuda.current_stream()
-    ops = {}
-    for disc in ("cg", "dg"):
-        ops[disc] = M.Poisson(n, n, n, DEGREE, disc=disc, mapping="sine",
-                              map_param=AMP)
-    mixed = {disc: M.Poisson(n, n, n, DEGREE, disc=disc, mapping="sine",
-                             map_param=AMP, mg_precision="fp32")
-             for disc in ("cg", "dg")}
+    peaks = load_peaks()
+    hbm_gbs = float(peaks.get("hbm_gbs") or 6800.0)
+    sm_mhz = float(peaks.get("sm_max_mhz") or 2070.0)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+
+    def make(disc, **kw):
+        return M.Poisson(n, n, n, DEGREE, disc=disc, mapping="sine",
+                         map_param=AMP, **kw)
+    ops = {d: make(d) for d in ("cg", "dg")}
+    mixed = {d: make(d, mg_precision="fp32") for d in ("cg", "dg")}
+    native = {d: make(d, fp64_arith="native") for d in ("cg", "dg")}
     tuned = {}
     for d in ("cg", "dg"):
         tuned["f64_" + d] = ops[d].autotune(prec="fp64")[0]
+        tuned["f64_native_" + d] = native[d].autotune(prec="fp64")[0]
         tuned["f32_" + d] = mixed[d].autotune(prec="fp32")[0]
     b = {d: ops[d].rhs(0) for d in ops}
     x = {d: torch.empty_like(b[d]) for d in ops}
     N = {d: ops[d].n_dofs() for d in ops}
+    dofs_step = N["cg"] + N["dg"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
                         device="cuda")
 
@@ -345,76 +470,49 @@ def run_ours(args):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        step_ms = []
         for i in range(args.steps):
             flush.fill_(float(i))
             starts[i].record(stream)
-            torch.cuda.nvtx.range_push("timed_step")  # launch-list window
             its = step(ops)
-            torch.cuda.nvtx.range_pop()
             ends[i].record(stream)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-    _, _, l1 = ops["cg"].counters()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    dofs_step = N["cg"] + N["dg"]
-    ms, _, value = aggregate(sum(step_ms) / len(step_ms), dofs_step, dist)
+        _, _, l1 = ops["cg"].counters()
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        ms, _, value = aggregate(sum(step_ms) / len(step_ms), dofs_step, dist)
 
-    # --- mixed-precision solve rate (same workload, float32 V-cycle) -----
-    for _ in range(2):
-        step(mixed)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
-        enable_timing=True)
-    e0.record(stream)
-    its_mixed = step(mixed)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    mixed_ms = e0.elapsed_time(e1)
+        # --- the same solves with a float32 V-cycle (mixed precision) and
+        # with IEEE float64 (DFMA) applies: min of 5 and median of 20 ------
+        for _ in range(3):
+            step(mixed)
+            step(native)
+        its_mixed = step(mixed)
+        mixed_ts = timed_runs(lambda: step(mixed), stream, 20, flush)
+        its_native = step(native)
+        native_ts = timed_runs(lambda: step(native), stream, 5, flush)
 
-    # --- operator apply throughput, per kernel, CUDA events ---------------
-    apply = {}
-    for prec, opset, dt in (("f64", ops, torch.float64),
-                            ("f32", mixed, torch.float32)):
-        for d in ("cg", "dg"):
-            src = torch.randn(N[d], dtype=dt, device="cuda")
-            dst = torch.empty_like(src)
-            for _ in range(3):
-                opset[d].apply(src, dst)
-            reps = 20 if prec == "f64" else 50
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
-                enable_timing=True)
-            flush.fill_(1.0)
-            a0.record(stream)
-            for _ in range(reps):
-                opset[d].apply(src, dst)
-            a1.record(stream)
-            torch.cuda.synchronize()
-            t = a0.elapsed_time(a1) / reps * 1e-3
-            equiv = n ** 3 * DEGREE ** 3
-            apply[prec + "_" + d] = {
-                "ms": t * 1e3, "MDoF_s": N[d] / t / 1e6,
-                "equiv_MDoF_s": equiv / t / 1e6,
-                "GFLOP_s": apply_flops(d, DEGREE, n ** 3, True) / t / 1e9,
-                "fp32_pipe_GFLOP_s": (apply_flops_df(d, DEGREE, n ** 3, True)
-                                      / t / 1e9 if prec == "f64" else None),
-                "GB_s": apply_bytes(d, DEGREE, n, True,
-                                    8 if prec == "f64" else 4) / t / 1e9}
+        # --- operator applies, one event pair per launch -----------------
+        apply = measure_applies(M, ops, native, mixed, N, n, stream, flush,
+                                20, hbm_gbs, sm_count, sm_mhz)
 
-    # --- end to end through the C ABI with host buffers ------------------
-    hb = {d: b[d].cpu().pin_memory() for d in ops}
-    hx = {d: torch.empty(N[d], dtype=torch.float64).pin_memory() for d in ops}
-    db = {d: torch.empty_like(b[d]) for d in ops}
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for d in ("cg", "dg"):
-        db[d].copy_(hb[d], non_blocking=True)
-        ops[d].solve(db[d], x[d], rtol=RTOL, max_it=200)
-        hx[d].copy_(x[d], non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+        # --- end to end through the C ABI with host buffers --------------
+        hb = {d: b[d].cpu().pin_memory() for d in ops}
+        hx = {d: torch.empty(N[d], dtype=torch.float64).pin_memory()
+              for d in ops}
+        db = {d: torch.empty_like(b[d]) for d in ops}
+
+        def e2e_step():
+            for d in ("cg", "dg"):
+                db[d].copy_(hb[d], non_blocking=True)
+                ops[d].solve(db[d], x[d], rtol=RTOL, max_it=200)
+                hx[d].copy_(x[d], non_blocking=True)
+        e2e_step()
+        e2e_ts = timed_runs(e2e_step, stream, 20, flush)
+    mixed_st, native_st, e2e_st = (stats(mixed_ts), stats(native_ts),
+                                   stats(e2e_ts))
+    del native
+    torch.cuda.empty_cache()
 
     # --- HDG mixed operator on (q, u), Cartesian cells, float64 -----------
     try:
@@ -424,21 +522,15 @@ def run_ours(args):
         hdst = torch.empty_like(hsrc)
         for _ in range(3):
             oph.hdg_apply(hsrc, hdst)
-        reps = 10
-        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
-            enable_timing=True)
-        flush.fill_(2.0)
-        h0.record(stream)
-        for _ in range(reps):
-            oph.hdg_apply(hsrc, hdst)
-        h1.record(stream)
-        torch.cuda.synchronize()
-        t = h0.elapsed_time(h1) / reps * 1e-3
+        hst = stats(timed_runs(lambda: oph.hdg_apply(hsrc, hdst), stream, 20,
+                               flush))
+        t = hst["mean_ms"] * 1e-3
         apply["hdg_f64_cartesian"] = {
-            "ms": t * 1e3, "MDoF_s": nu / t / 1e6,
+            "launch": hst, "MDoF_s": nu / t / 1e6,
             "unknowns_per_s": 4 * nu / t,
             "GFLOP_s": hdg_flops(DEGREE, n ** 3) / t / 1e9,
-            "GB_s": 2 * 4 * nu * 8 / t / 1e9}
+            "GB_s": 2 * 4 * nu * 8 / t / 1e9,
+            "hbm_frac": 2 * 4 * nu * 8 / t / 1e9 / hbm_gbs}
         del oph, hsrc, hdst
     except Exception as exc:  # reported, never fatal to the contract line
         apply["hdg_f64_cartesian"] = {"error": str(exc)[:200]}
@@ -455,73 +547,105 @@ def run_ours(args):
                             box=(-1.0, 1.0), penalty_factor=pf)
             bc = opc.rhs(2, gauss)
             xc = torch.empty_like(bc)
-            opc.solve(bc, xc, rtol=RTOL, max_it=200)
-            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
-                enable_timing=True)
-            flush.fill_(3.0)
-            c0.record(stream)
             _, itc, relc = opc.solve(bc, xc, rtol=RTOL, max_it=200)
-            c1.record(stream)
-            torch.cuda.synchronize()
-            tc = c0.elapsed_time(c1)
-            paper_cube[d] = {"ms": tc, "iterations": itc[0],
-                             "relres": relc[0],
-                             "dofs": opc.n_dofs(),
-                             "DoF_s": opc.n_dofs() / (tc * 1e-3)}
+            cst = stats(timed_runs(
+                lambda: opc.solve(bc, xc, rtol=RTOL, max_it=200), stream, 5,
+                flush))
+            paper_cube[d] = {"solve": cst, "iterations": itc[0],
+                             "relres": relc[0], "dofs": opc.n_dofs(),
+                             "DoF_s": opc.n_dofs() / (cst["median_ms"] * 1e-3)}
             del opc, bc, xc
     except Exception as exc:  # reported, never fatal to the contract line
         paper_cube["error"] = str(exc)[:200]
+
+    # --- the other workloads (latency, degree sweep, batched, gradient) ---
+    configs = {}
+    if not args.no_extras:
+        del mixed
+        torch.cuda.empty_cache()
+        for name, fn in (("latency_cg_q2_8", config_latency),
+                         ("sweep_cartesian", config_sweep),
+                         ("batched_16rhs_cg_q3_48", config_batched),
+                         ("gradient_sipg_q3_32", config_gradient)):
+            try:
+                configs[name] = fn(M, stream, flush)
+            except Exception as exc:  # reported, never fatal
+                configs[name] = {"error": str(exc)[:300]}
+            torch.cuda.empty_cache()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    peaks = load_peaks()
     # dominant kernel: the float64 SIPG apply (largest share of the step in
     # the launch list), double-float arithmetic, bound by the FP32 pipe.
     dom = apply["f64_dg"]
-    ach = dom["fp32_pipe_GFLOP_s"] / 1e3
-    roof = {"kernel": "k_apply_df<P=5,DG,curved>", "bound": "alu",
-            "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP32_PEAK_TFLOPS,
+    p32 = fp32_pipe_peak_tflops(sm_count, sm_mhz)
+    t_dom = dom["launch"]["mean_ms"] * 1e-3
+    fl = apply_flops("dg", DEGREE, n ** 3, True)
+    ach = DF_FLOPS_PER_FP64_FLOP * fl / t_dom / 1e12
+    fl_s = SURVEY_DG_FLOPS_PER_DOF[DEGREE] * N["dg"]
+    roof = {"kernel": "k_apply_df<P=5,DG,curved> + k_dg_face_add",
+            "bound": "alu", "achieved": ach, "peak": p32, "unit": "TFLOP/s",
+            "frac": ach / p32,
             "traffic": TRAFFIC.get(kernel_hash()),
-            "algorithmic_bytes": apply_bytes("dg", DEGREE, n, True),
-            "work": "the method's float64 flops (bench.apply_flops) at 14 "
-                    "FP32-pipe flops per double-float multiply-add "
-                    "(bench.apply_flops_df)",
-            "fp64_equivalent_TFLOP_s": dom["GFLOP_s"] / 1e3,
-            "fp64_pipe_peak": FP64_PEAK_TFLOPS,
-            "peak_source": "FP32 pipe from unit counts (152 SMs x 128 FFMA/clk "
-                           "x 2 x 2.07 GHz); FFMA probe measured 73.2 TFLOP/s",
+            "algorithmic_flops_fp64": fl,
+            "flops_per_dof_fp64": fl / N["dg"],
+            "work": "float64 flops of the method as counted in "
+                    "bench.apply_flops (sweeps, quadrature-point operation, "
+                    "each face once with the curved tangential terms) x 7 "
+                    "FP32-pipe flops per float64 flop (one double-float "
+                    "multiply-add: FMUL + 3 FFMA + 8 FADD = 14 flops)",
+            "frac_at_survey_flop_count": (DF_FLOPS_PER_FP64_FLOP * fl_s
+                                          / t_dom / 1e12 / p32),
+            "algorithmic_bytes": dom["algorithmic_bytes"],
+            "hbm_frac": dom["hbm_frac"],
+            "launch_mean_ms": dom["launch"]["mean_ms"],
+            "peak_source": "FP32 pipe from unit counts: %d SMs (device query) "
+                           "x 128 FFMA/clk x 2 flop x %.0f MHz" % (sm_count,
+                                                                  sm_mhz),
             "kernel_source_hash": kernel_hash()}
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": "f64", "arith": ARITH, "data": "synthetic",
         "config": {"workload": "CG Q4 + SIPG DG_Q4 V-cycle PCG solves to "
                    "1e-10, 32^3 cells, curved map amplitude 0.1",
                    "cells": n, "degree": DEGREE, "dofs_cg": N["cg"],
                    "dofs_dg": N["dg"], "rtol": RTOL,
-                   "l2": "flushed (256 MB write) before every timed step",
+                   "l2": "flushed (256 MB write) before every timed step "
+                         "and every timed launch",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
+        "step_ms": stats(step_ms),
         "iterations": {d: its[d][0] for d in its},
-        "solve_ms": None,
-        "mixed": {"ms_per_step": mixed_ms,
-                  "value": dofs_step / (mixed_ms * 1e-3),
+        "mixed": {"solve": mixed_st,
+                  "value": dofs_step / (mixed_st["median_ms"] * 1e-3),
                   "iterations": {d: its_mixed[d][0] for d in its_mixed},
-                  "speedup_vs_fp64": ms / mixed_ms},
+                  "speedup_vs_fp64": stats(step_ms)["median_ms"]
+                  / mixed_st["median_ms"]},
+        "fp64_native": {"solve": native_st,
+                        "value": dofs_step / (native_st["median_ms"] * 1e-3),
+                        "iterations": {d: its_native[d][0]
+                                       for d in its_native},
+                        "arith": "IEEE float64 (DFMA) applies"},
         "apply": apply,
         "paper_cube": paper_cube,
+        "configs": configs,
         "cells_per_block": tuned,
         "roofline": roof,
-        "e2e": {"value": dofs_step / (e2e_ms * 1e-3), "unit": "DoF/s",
+        "e2e": {"value": dofs_step / (e2e_st["median_ms"] * 1e-3),
+                "unit": "DoF/s", "solve": e2e_st,
                 "h2d_bytes_per_step": 8 * dofs_step,
                 "d2h_bytes_per_step": 8 * dofs_step},
         "gpu_launches": int((l1 - l0) // max(args.steps, 1)),
         "gpu_launches_scope": "per timed step",
         "clocks": clk.summary(),
-        "peaks": {"hbm_gbs": peaks.get("hbm_gbs")},
+        "peaks": {"hbm_gbs": hbm_gbs, "sm_count": sm_count,
+                  "sm_max_mhz": sm_mhz,
+                  "fp32_pipe_tflops": p32,
+                  "fp64_pipe_tflops": fp64_pipe_peak_tflops(sm_count,
+                                                            sm_mhz)},
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(8)
@@ -531,51 +655,32 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
-# Further configurations (one JSON line each, not the contract line)
+# The other configurations: each returns a dict that the contract line
+# carries under "configs" (and --workload prints alone)
 # ---------------------------------------------------------------------------
-def _timed(fn, stream):
+def config_latency(M, stream, flush, runs=20):
+    """8^3 cells, continuous Q2 (17^3 = 4913 dofs), Cartesian, FP64, 3
+    levels: time to 1e-10 with the V-cycle replayed from a CUDA graph and
+    eagerly, and the latency of one operator apply."""
     import torch
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    out = fn()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1), out
-
-
-def run_latency(args):
-    """8^3 cells, continuous Q2 (17^3 = 4913 dofs), Cartesian, FP64: time to
-    1e-10 with the V-cycle replayed from a CUDA graph and eagerly, and the
-    latency of one operator apply."""
-    import torch
-    from paper_1611_03029_gb300 import build
-    build.build()
-    from paper_1611_03029_gb300 import mfpoisson as M
-    st = torch.cuda.current_stream()
     op = M.Poisson(8, 8, 8, 2, disc="cg")
     b = op.rhs(0)
     x = torch.empty_like(b)
-    res = {}
+    res = {"dofs": op.n_dofs(), "levels": op.n_levels}
     for mode in ("graph", "eager"):
         os.environ["MFP_CUDA_GRAPHS"] = "1" if mode == "graph" else "0"
-        for _ in range(args.warmup):
-            op.solve(b, x, rtol=RTOL)
-        ts = []
-        for _ in range(args.steps):
-            t, (_, it, rel) = _timed(lambda: op.solve(b, x, rtol=RTOL), st)
-            ts.append(t)
-        res[mode] = {"ms": min(ts), "median_ms": sorted(ts)[len(ts) // 2],
-                     "iterations": it[0], "relres": rel[0]}
+        for _ in range(3):
+            _, it, rel = op.solve(b, x, rtol=RTOL)
+        res[mode] = stats(timed_runs(lambda: op.solve(b, x, rtol=RTOL),
+                                     stream, runs))
+        res[mode].update(iterations=it[0], relres=rel[0])
     os.environ["MFP_CUDA_GRAPHS"] = "1"
     src = torch.randn(op.n_dofs(), dtype=torch.float64, device="cuda")
     dst = torch.empty_like(src)
-    t, _ = _timed(lambda: [op.apply(src, dst) for _ in range(200)], st)
-    print(json.dumps({"workload": "latency: CG Q2 8^3 cells (4913 dofs), "
-                      "Cartesian, FP64, 3 levels", "solve": res,
-                      "apply_us": t / 200 * 1e3,
-                      "dofs": op.n_dofs()}), flush=True)
+    ts = timed_runs(lambda: [op.apply(src, dst) for _ in range(100)], stream,
+                    5)
+    res["apply_us"] = min(ts) / 100 * 1e3
+    return res
 
 
 SWEEP = {  # degree: (cells per axis CG, cells per axis SIPG)
@@ -583,113 +688,119 @@ SWEEP = {  # degree: (cells per axis CG, cells per axis SIPG)
     5: (56, 48), 6: (48, 40), 7: (40, 32), 8: (32, 32)}
 
 
-def run_sweep(args):
-    """Degree sweep on Cartesian meshes of 16-33M dofs: FP64 V-cycle versus
-    FP32 V-cycle inside the float64 CG, time to 1e-10, iterations and the
-    difference of the two solutions."""
+def config_sweep(M, stream, flush, degrees=(2, 4, 8), runs=5):
+    """Degree sweep on Cartesian meshes of 16-33M dofs: time to 1e-10 with
+    the float64 V-cycle and with the float32 V-cycle inside the float64 CG,
+    iterations, and the difference of the two solutions."""
     import torch
-    from paper_1611_03029_gb300 import build
-    build.build()
-    from paper_1611_03029_gb300 import mfpoisson as M
-    st = torch.cuda.current_stream()
-    for k in [int(v) for v in args.degrees.split(",")]:
+    out = {}
+    for k in degrees:
         for disc, n in (("cg", SWEEP[k][0]), ("dg", SWEEP[k][1])):
-            out = {"workload": "sweep", "disc": disc, "degree": k,
-                   "cells": n}
+            e = {"cells": n}
             xs = {}
             for prec in ("fp64", "fp32"):
                 op = M.Poisson(n, n, n, k, disc=disc, mg_precision=prec)
                 b = op.rhs(0)
                 x = torch.empty_like(b)
-                op.solve(b, x, rtol=RTOL, max_it=200)
-                t, (_, it, rel) = _timed(
-                    lambda: op.solve(b, x, rtol=RTOL, max_it=200), st)
-                out["dofs"] = op.n_dofs()
-                out[prec] = {"ms": t, "iterations": it[0], "relres": rel[0],
-                             "dofs_per_s": op.n_dofs() / (t * 1e-3)}
+                _, it, rel = op.solve(b, x, rtol=RTOL, max_it=200)
+                st_ = stats(timed_runs(
+                    lambda: op.solve(b, x, rtol=RTOL, max_it=200), stream,
+                    runs, flush))
+                e["dofs"] = op.n_dofs()
+                st_.update(iterations=it[0], relres=rel[0],
+                           dofs_per_s=op.n_dofs() / (st_["median_ms"] * 1e-3))
+                e[prec] = st_
                 xs[prec] = x.clone()
-                del op
+                del op, b, x
                 torch.cuda.empty_cache()
-            out["mixed_vs_fp64_rel_diff"] = float(
+            e["mixed_vs_fp64_rel_diff"] = float(
                 (xs["fp32"] - xs["fp64"]).norm() / xs["fp64"].norm())
-            out["mixed_speedup"] = out["fp64"]["ms"] / out["fp32"]["ms"]
-            print(json.dumps(out), flush=True)
+            e["mixed_speedup"] = (e["fp64"]["median_ms"]
+                                  / e["fp32"]["median_ms"])
+            out["%s_q%d" % (disc, k)] = e
+            del xs
+    return out
 
 
-def run_batched(args):
+def config_batched(M, stream, flush, runs=5):
     """16 right-hand sides (sums of 8 Gaussians), continuous Q3 on 48^3
-    Cartesian cells (3,048,625 dofs each): one batched mixed-precision solve
-    (one launch per operator apply, graph-captured V-cycle) versus 16
-    sequential float64 solves."""
+    Cartesian cells (3,048,625 dofs each), time to 1e-10 for all 16:
+    batched (one launch per operator apply for all columns, graph-captured
+    V-cycle) and sequential, each with the float32 and the float64 V-cycle,
+    so that batching and precision show separately."""
     import torch
-    from paper_1611_03029_gb300 import build, synthetic
-    build.build()
-    from paper_1611_03029_gb300 import mfpoisson as M
-    st = torch.cuda.current_stream()
+    from paper_1611_03029_gb300 import synthetic
     R, n, k = 16, 48, 3
-    mixed = M.Poisson(n, n, n, k, disc="cg", mg_precision="fp32")
-    fp64 = M.Poisson(n, n, n, k, disc="cg")
-    N = mixed.n_dofs()
+    ctx = {"fp32": M.Poisson(n, n, n, k, disc="cg", mg_precision="fp32"),
+           "fp64": M.Poisson(n, n, n, k, disc="cg")}
+    N = ctx["fp64"].n_dofs()
     B = torch.empty(N * R, dtype=torch.float64, device="cuda")
     for r in range(R):
-        mixed.rhs(1, synthetic.gaussian_terms(1000 + r), out=B[r:], stride=R)
+        ctx["fp64"].rhs(1, synthetic.gaussian_terms(1000 + r), out=B[r:],
+                        stride=R)
     X = torch.empty_like(B)
-    tuned = mixed.autotune(prec="fp64", n_rhs=R)[0]
-    mixed.solve(B, X, n_rhs=R, rtol=RTOL)
-    t_b, (_, its_b, rel_b) = _timed(
-        lambda: mixed.solve(B, X, n_rhs=R, rtol=RTOL), st)
     cols = [B[r::R].contiguous() for r in range(R)]
     x1 = torch.empty(N, dtype=torch.float64, device="cuda")
-    fp64.solve(cols[0], x1, rtol=RTOL)
+    out = {"dofs_per_rhs": N, "rhs": R}
+    for prec, op in ctx.items():
+        vp = "fp32" if prec == "fp32" else "fp64"
+        out["cells_per_block_R16_" + prec] = op.autotune(prec=vp, n_rhs=R)[0]
+        _, its, rel = op.solve(B, X, n_rhs=R, rtol=RTOL)
+        st_ = stats(timed_runs(lambda: op.solve(B, X, n_rhs=R, rtol=RTOL),
+                               stream, runs, flush))
+        st_.update(iterations=its, max_relres=max(rel),
+                   dofs_per_s=N * R / (st_["median_ms"] * 1e-3))
+        out["batched_" + prec] = st_
 
-    def seq():
-        its = []
-        for r in range(R):
-            _, it, _ = fp64.solve(cols[r], x1, rtol=RTOL)
-            its.append(it[0])
-        return its
-    t_s, its_s = _timed(seq, st)
-    print(json.dumps({"workload": "batched: 16 RHS, CG Q3 48^3 Cartesian",
-                      "dofs_per_rhs": N, "batched_mixed_ms": t_b,
-                      "batched_iterations": its_b,
-                      "batched_max_relres": max(rel_b),
-                      "sequential_fp64_ms": t_s,
-                      "sequential_iterations": its_s,
-                      "speedup": t_s / t_b,
-                      "cells_per_block_fp64_R16": tuned,
-                      "dofs_per_s_batched": N * R / (t_b * 1e-3)}),
-          flush=True)
+        def seq():
+            for r in range(R):
+                op.solve(cols[r], x1, rtol=RTOL)
+        seq()
+        st_ = stats(timed_runs(seq, stream, max(2, runs // 2), flush))
+        st_["dofs_per_s"] = N * R / (st_["median_ms"] * 1e-3)
+        out["sequential_" + prec] = st_
+    t = {kk: v["median_ms"] for kk, v in out.items()
+         if isinstance(v, dict) and "median_ms" in v}
+    out["speedup_batched_mixed_vs_sequential_fp64"] = (
+        t["sequential_fp64"] / t["batched_fp32"])
+    out["speedup_batching_fp64"] = t["sequential_fp64"] / t["batched_fp64"]
+    out["speedup_batching_mixed"] = t["sequential_fp32"] / t["batched_fp32"]
+    out["speedup_precision_sequential"] = (t["sequential_fp64"]
+                                           / t["sequential_fp32"])
+    return out
 
 
-def run_gradient(args):
+def config_gradient(M, stream, flush, runs=5):
     """-div(a grad u) = f, a = exp(g) at every quadrature point, SIPG Q3 on
-    32^3 Cartesian cells: forward solve, adjoint solve and the dL/da kernel,
-    with the directional finite-difference check of the gradient."""
+    32^3 Cartesian cells: forward solve, adjoint solve and the dL/da kernel
+    (rtol 1e-13), with the directional fourth-order finite-difference check
+    of the gradient along 3 seeded directions with standard normal entries
+    (every coefficient value moves by about eps = 1e-4 max a)."""
     import numpy as np
     import torch
-    from paper_1611_03029_gb300 import build, synthetic
-    build.build()
-    from paper_1611_03029_gb300 import mfpoisson as M
-    st = torch.cuda.current_stream()
+    from paper_1611_03029_gb300 import synthetic
     n, k = 32, 3
     op = M.Poisson(n, n, n, k, disc="dg")
     a_c, a_f = synthetic.log_coefficient((n, n, n), k + 1, seed=7)
     ac = torch.from_numpy(a_c).cuda()
     af = torch.from_numpy(a_f).cuda()
-    t_set, _ = _timed(lambda: op.set_coefficient(ac, af), st)
+    t_set = stats(timed_runs(lambda: op.set_coefficient(ac, af), stream, 2))
     b = op.rhs(0)
     u, _, _ = op.solve(b, rtol=1e-13, max_it=300)
     ut = torch.from_numpy(
         synthetic.random_vector(op.n_dofs(), 8)).cuda() * u.norm() / \
         np.sqrt(op.n_dofs())
+    res = {}
 
     def fwd_adj_grad():
         u, itf, _ = op.solve(b, rtol=1e-13, max_it=300)
         lam, ita, _ = op.solve((u - ut).contiguous(), rtol=1e-13, max_it=300)
         gc, gf = op.gradient(u, lam)
-        return u, lam, gc, gf, itf[0], ita[0]
-    t, (u, lam, gc, gf, itf, ita) = _timed(fwd_adj_grad, st)
-    t_g, _ = _timed(lambda: op.gradient(u, lam), st)
+        res.update(u=u, lam=lam, gc=gc, gf=gf, itf=itf[0], ita=ita[0])
+    fwd_adj_grad()
+    t_all = stats(timed_runs(fwd_adj_grad, stream, runs, flush))
+    u, lam, gc, gf = res["u"], res["lam"], res["gc"], res["gf"]
+    t_g = stats(timed_runs(lambda: op.gradient(u, lam), stream, 20, flush))
 
     def loss(dc, df, eps):
         op.set_coefficient((ac + eps * dc).contiguous(),
@@ -702,22 +813,35 @@ def run_gradient(args):
     for _ in range(3):
         dc = torch.from_numpy(rng.standard_normal(a_c.shape)).cuda()
         df = torch.from_numpy(rng.standard_normal(a_f.shape)).cuda()
-        dc /= dc.norm()
-        df /= df.norm()
-        # fourth-order central difference
         fd = (8 * (loss(dc, df, eps) - loss(dc, df, -eps))
               - (loss(dc, df, 2 * eps) - loss(dc, df, -2 * eps))) / (12 * eps)
         an = float((gc * dc).sum() + (gf * df).sum())
         checks.append(abs(fd - an) / abs(an))
     op.set_coefficient(ac, af)
-    print(json.dumps({"workload": "gradient: SIPG Q3 32^3, a = exp(g)",
-                      "dofs": op.n_dofs(), "cell_points": a_c.size,
-                      "face_points": a_f.size,
-                      "forward_adjoint_gradient_ms": t,
-                      "gradient_kernel_ms": t_g,
-                      "set_coefficient_ms": t_set,
-                      "iterations": {"forward": itf, "adjoint": ita},
-                      "fd_rel_errors": checks}), flush=True)
+    return {"dofs": op.n_dofs(), "cell_points": a_c.size,
+            "face_points": a_f.size,
+            "forward_adjoint_gradient": t_all, "gradient_kernel": t_g,
+            "set_coefficient": t_set,
+            "iterations": {"forward": res["itf"], "adjoint": res["ita"]},
+            "fd_rel_errors": checks}
+
+
+def run_config(args):
+    import torch
+    from paper_1611_03029_gb300 import build
+    build.build()
+    from paper_1611_03029_gb300 import mfpoisson as M
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
+                        device="cuda")
+    fn = {"latency": config_latency, "sweep": config_sweep,
+          "batched": config_batched, "gradient": config_gradient}[
+        args.workload]
+    kw = {}
+    if args.workload == "sweep":
+        kw["degrees"] = [int(v) for v in args.degrees.split(",")]
+    out = fn(M, stream, flush, **kw)
+    print(json.dumps({"workload": args.workload, **out}), flush=True)
 
 
 def main():
@@ -727,8 +851,7 @@ def main():
     elif args.workload == "solve":
         run_ours(args)
     else:
-        {"latency": run_latency, "sweep": run_sweep, "batched": run_batched,
-         "gradient": run_gradient}[args.workload](args)
+        run_config(args)
 
 
 if __name__ == "__main__":

@@ -179,9 +179,12 @@ mfp_status mfp_rhs(mfp_ctx* ctx, int f_kind, const double* params_host,
  * this entry point copies them into a fixed array compiled into the library
  * instead (160 KiB, held on every device that loads the library until the
  * process exits) and calls no allocating routine.
- *  - n_terms <= 4096 for f_kind 1; larger counts return MFP_ERR_ARG.
- *  - The first call on a device looks up the array's device address; make
- *    that first call before any stream capture.
+ *  - n_terms <= 4096 for f_kind 1 and 2 (the limit of mfp_rhs too); larger
+ *    counts return MFP_ERR_ARG.
+ *  - mfp_create sets this entry point up on its device: it resolves the
+ *    array's device address and loads the array and the load-vector kernels
+ *    there, so that this call makes CUDA load nothing.  Call it with the
+ *    context's device current (MFP_ERR_STATE otherwise).
  *  - All calls share the array, which keeps the last call's parameters.
  *    Calls whose work overlaps on the GPU (different streams without
  *    ordering) race on it; calls on one stream are safe.
@@ -204,7 +207,8 @@ mfp_status mfp_rhs_noalloc(mfp_ctx* ctx, int f_kind, const double* params_host,
  * SIPG cell layout per field), 4 ncells (k+1)^3 doubles each, distinct.
  * Cartesian cells (MFP_MAP_IDENTITY) and the constant coefficient only
  * (MFP_ERR_ARG otherwise).  The first call allocates the context's trace
- * buffer (nfaces (k+1)^2 doubles): make it outside a stream capture.
+ * buffer (nfaces (k+1)^2 doubles): make it outside a stream capture.  Calls
+ * on one context share that buffer: issue them in stream order.
  * Launches four kernels (traces per face direction, then the cells). */
 mfp_status mfp_hdg_apply(mfp_ctx* ctx, double tau_factor, const double* x_dev,
                          double* y_dev, void* stream);

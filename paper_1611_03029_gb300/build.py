@@ -17,8 +17,6 @@ LIB = os.path.join(HERE, "libmfpoisson.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr"]
-# extra nvcc flags (e.g. -DMFP_DF_MIN_BLOCKS=4) for experiments
-FLAGS += os.environ.get("MFP_NVCC_EXTRA", "").split()
 
 
 def _nvcc():

@@ -688,6 +688,7 @@ mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out) {
                                   sizeof(double) * S_COUNT * kMaxRhs));
     ensure_scratch(c, 1);
     build_levels(c, st(stream));
+    noalloc_prepare(c->device, d.degree + 1);
     *out = c;
     return MFP_OK;
   } catch (const Fail& f) {
@@ -769,7 +770,8 @@ mfp_status mfp_rhs(mfp_ctx* c, int f_kind, const double* params, int nterms,
               "f_kind 2 needs the constant coefficient");
   cudaStream_t s = st(stream);
   if (f_kind >= 1) {
-    MFP_REQUIRE(params && nterms >= 1 && nterms <= 4096, "bad Gaussian terms");
+    MFP_REQUIRE(params && nterms >= 1 && nterms <= kMaxGaussTerms,
+                "bad Gaussian terms (1..4096)");
     if (c->params_cap < nterms) {
       dfree(c->params);
       c->params = dalloc<double>(5 * (int64_t)nterms);

@@ -24,11 +24,7 @@
 // most 128 threads for p <= 5, 256 above), measured on 24^3..64^3 meshes
 // for k = 2..8: more resident warps hide the latency of the shared-memory
 // sweeps and the gathers, down to about 73 registers per thread; CG p >= 7
-// keeps its larger line arrays in registers.  MFP_DF_MIN_BLOCKS overrides
-// the table for experiments.
-#ifndef MFP_DF_MIN_BLOCKS
-#define MFP_DF_MIN_BLOCKS 0
-#endif
+// keeps its larger line arrays in registers.
 
 namespace mfp {
 namespace {
@@ -105,25 +101,15 @@ __device__ __forceinline__ void dmtv(const float (&ih)[P],
   }
 }
 
-// Rolled sum-factorization sweeps (MFP_DF_ROLL, p >= 4): a loop over the
+// Rolled sum-factorization sweeps (p >= 4): a loop over the
 // output index with the table entries read by index keeps the double-float
 // code P times shorter than the unrolled matrix-vector product; unrolled,
 // the sweeps and faces of a cell overflow the instruction caches and
 // instruction fetch limits the issue rate (p <= 3 stays unrolled, its code
 // is short and the indexed table reads would cost more than they save).
-#ifndef MFP_DF_ROLL
-#define MFP_DF_ROLL 1
-#endif
-#ifndef MFP_DF_ROLL_BY
-#define MFP_DF_ROLL_BY 1
-#endif
 #define MFP_DF_STR2(x) #x
 #define MFP_DF_STR(x) MFP_DF_STR2(x)
-#if MFP_DF_ROLL
-#define MFP_DF_LOOP _Pragma(MFP_DF_STR(unroll(P >= 4 ? MFP_DF_ROLL_BY : P)))
-#else
-#define MFP_DF_LOOP _Pragma("unroll")
-#endif
+#define MFP_DF_LOOP _Pragma(MFP_DF_STR(unroll(P >= 4 ? 1 : P)))
 
 // Even-odd split of the sweeps (p >= 4, MFP_DF_EO): the mirror symmetry of
 // S and D (tables c_tabeo) halves the multiply-adds of each sweep for the
@@ -559,7 +545,6 @@ template <int P>
 constexpr int df_max_threads() { return P <= 5 ? 128 : 256; }
 template <int P, bool DG>
 constexpr int df_min_blocks() {
-  if (MFP_DF_MIN_BLOCKS > 0) return MFP_DF_MIN_BLOCKS;
   if (DG) return P <= 3 ? 5 : (P <= 5 ? 7 : 2);
   return P <= 5 ? 8 : (P == 6 ? 3 : 1);
 }
@@ -655,7 +640,7 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
     }
     // ---- values at Gauss points: S along z, y, x (one copy of the sweep
     // code for p >= 4: line (base, stride) of the thread per direction)
-    if constexpr (P >= 4 && MFP_DF_ROLL) {
+    if constexpr (P >= 4) {
 #pragma unroll
       for (int j = 0; j < P; ++j)
         A[dx3<P>(ta, tb, j)] = make_float2(rh[j], rl[j]);
@@ -772,7 +757,7 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
       __syncthreads();
     }
     // ---- S^T along x, y (and z for SIPG), one copy of the sweep for p >= 4
-    if constexpr (P >= 4 && MFP_DF_ROLL) {
+    if constexpr (P >= 4) {
 #pragma unroll 1
       for (int d = 0; d < (DG ? 3 : 2); ++d) {
         const int b0 = d == 0   ? dx3<P>(0, ta, tb)

@@ -916,6 +916,20 @@ void launch_rhs(const Level& L, int kind, const double* params_dev,
   });
 }
 
+// Loads the load-vector kernels of degree p - 1 on the current device (a
+// kernel's code is otherwise loaded, and its device memory taken, at its
+// first launch when CUDA loads modules lazily).
+void preload_rhs_kernels(int p) {
+  cudaFuncAttributes fa;
+  MFP_CHECK_CUDA(cudaFuncGetAttributes(&fa, k_zero_strided));
+  dispatch_p(p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
+    MFP_CHECK_CUDA(cudaFuncGetAttributes(&fa, k_rhs<P>));
+    MFP_CHECK_CUDA(cudaFuncGetAttributes(&fa, k_rhs_lift<P>));
+    MFP_CHECK_CUDA(cudaFuncGetAttributes(&fa, k_rhs_face<P>));
+  });
+}
+
 void launch_coarsen_coefficient(const Level& fine, const Level& coarse,
                                 cudaStream_t s) {
   ensure_tables();

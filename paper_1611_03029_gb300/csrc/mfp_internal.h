@@ -119,6 +119,7 @@ enum ScalarSlot {
 };
 constexpr int kMaxRedBlocks = 1024;
 constexpr int kMaxRhs = 256;
+constexpr int kMaxGaussTerms = 4096;  // forcing terms of mfp_rhs (f_kind 1, 2)
 constexpr int kDenseMax = 2048;   // dofs of a coarsest level stored dense
 constexpr int kDenseRows = 128;   // rows per block of k_dense_apply
 constexpr int kDenseSplit = 32;   // column ranges per row block
@@ -300,6 +301,11 @@ void launch_rhs(const Level& L, int kind, const double* params_dev,
                 int nterms, double* b, int64_t stride, cudaStream_t s);
 void launch_coarsen_coefficient(const Level& fine, const Level& coarse,
                                 cudaStream_t s);
+void preload_rhs_kernels(int p);
+// Set-up of mfp_rhs_noalloc on the current device: resolves the device
+// address of its fixed parameter array and loads the load-vector kernels,
+// so that the entry point itself never makes CUDA load code or data.
+void noalloc_prepare(int device, int p);
 void launch_start_vector(const Level& L, double* v, cudaStream_t s);
 void launch_gradient(const Level& L, const double* u, const double* lam,
                      double* gc, double* gf, cudaStream_t s);

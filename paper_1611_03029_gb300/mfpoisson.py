@@ -200,6 +200,8 @@ class Poisson:
     def set_coefficient(self, a_cell, a_face=None, stream=None):
         _check(lib().mfp_set_coefficient(self._h, _ptr(a_cell), _ptr(a_face),
                                          _stream(stream)))
+        # stamp of the coefficient the context now holds
+        self.coef_stamp = getattr(self, "coef_stamp", 0) + 1
 
     def rhs(self, kind=0, params=None, out=None, stride=1, stream=None):
         n = self.n_dofs()
@@ -328,21 +330,33 @@ class MFPSolve(torch.autograd.Function):
     """u = A(a)^{-1} f as a differentiable function of the per-point
     coefficient (a_cell, a_face).  Backward solves A lambda = dL/du with the
     same symmetric operator and returns -lambda^T (dA/da) u from the
-    library's gradient kernel."""
+    library's gradient kernel.  The context holds one coefficient at a time:
+    forward saves its own, and backward sets it again if another forward (or
+    set_coefficient) has replaced it on the same context since."""
 
     @staticmethod
     def forward(ctx, a_cell, a_face, op, b, rtol, max_it):
-        op.set_coefficient(a_cell.contiguous(),
-                           None if a_face is None else a_face.contiguous())
+        a_cell = a_cell.contiguous()
+        a_face = None if a_face is None else a_face.contiguous()
+        op.set_coefficient(a_cell, a_face)
         u, its, rel = op.solve(b, rtol=rtol, max_it=max_it)
         ctx.op, ctx.rtol, ctx.max_it = op, rtol, max_it
-        ctx.save_for_backward(u)
+        ctx.stamp = op.coef_stamp
         ctx.has_face = a_face is not None
+        if a_face is None:
+            ctx.save_for_backward(u, a_cell)
+        else:
+            ctx.save_for_backward(u, a_cell, a_face)
         return u
 
     @staticmethod
     def backward(ctx, grad_u):
-        (u,) = ctx.saved_tensors
+        u, a_cell = ctx.saved_tensors[:2]
+        if ctx.op.coef_stamp != ctx.stamp:
+            a_face = ctx.saved_tensors[2] if ctx.has_face else None
+            ctx.op.set_coefficient(a_cell.detach(), None if a_face is None
+                                   else a_face.detach())
+            ctx.stamp = ctx.op.coef_stamp
         lam, _, _ = ctx.op.solve(grad_u.contiguous(), rtol=ctx.rtol,
                                  max_it=ctx.max_it)
         gc, gf = ctx.op.gradient(u, lam)

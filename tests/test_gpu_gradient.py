@@ -86,3 +86,66 @@ def test_gradient_full_size_sampled(mfp):
     fscale = np.abs(gf).max()
     for f, v in rf.items():
         assert np.abs(gf[f] - v).max() <= 1e-12 * fscale
+
+
+def test_autograd_two_forwards_then_backward(mfp):
+    # the context holds one coefficient: a second forward on the same
+    # context replaces it, and the first loss's backward must still
+    # differentiate at its own coefficient
+    from paper_1611_03029_gb300.mfpoisson import MFPSolve
+    n, k = (4, 4, 4), 2
+    p = k + 1
+    a1c, a1f = synthetic.log_coefficient(n, p, seed=7)
+    a2c, a2f = synthetic.log_coefficient(n, p, seed=9)
+    op = mfp.Poisson(*n, k, disc="dg")
+    b = op.rhs(0)
+
+    def grads(first_only):
+        ac = torch.from_numpy(a1c).cuda().requires_grad_(True)
+        af = torch.from_numpy(a1f).cuda().requires_grad_(True)
+        u1 = MFPSolve.apply(ac, af, op, b, 1e-13, 300)
+        if not first_only:
+            bc = torch.from_numpy(a2c).cuda().requires_grad_(True)
+            bf = torch.from_numpy(a2f).cuda().requires_grad_(True)
+            MFPSolve.apply(bc, bf, op, b, 1e-13, 300)
+        (0.5 * (u1 ** 2).sum()).backward()
+        return ac.grad.cpu().numpy(), af.grad.cpu().numpy()
+
+    rc, rf = grads(True)
+    gc, gf = grads(False)
+    assert rel_err(gc, rc) <= 1e-9
+    assert rel_err(gf, rf) <= 1e-9
+
+
+def test_gradient_fd_full_size(mfp):
+    # the gradient workload at its size: SIPG Q3 on 32^3 cells, a = exp(g)
+    # at every cell and face point; central differences of the loss through
+    # GPU solves at rtol 1e-13 along 3 seeded directions with standard
+    # normal entries, so that every coefficient value moves by about eps
+    n, k = (32, 32, 32), 3
+    a_c, a_f = synthetic.log_coefficient(n, k + 1, seed=7)
+    op = mfp.Poisson(*n, k, disc="dg")
+    ac = torch.from_numpy(a_c).cuda()
+    af = torch.from_numpy(a_f).cuda()
+    op.set_coefficient(ac, af)
+    b = op.rhs(0)
+    u, _, _ = op.solve(b, rtol=1e-13, max_it=300)
+    ut = torch.from_numpy(synthetic.random_vector(op.n_dofs(), 8)).cuda() \
+        * u.norm() / np.sqrt(op.n_dofs())
+    lam, _, _ = op.solve((u - ut).contiguous(), rtol=1e-13, max_it=300)
+    gc, gf = op.gradient(u, lam)
+
+    def loss(dc, df, e):
+        op.set_coefficient((ac + e * dc).contiguous(),
+                           (af + e * df).contiguous())
+        uu, _, _ = op.solve(b, rtol=1e-13, max_it=300)
+        return 0.5 * float(((uu - ut) ** 2).sum())
+    rng = np.random.default_rng(11)
+    eps = 1e-4 * float(ac.abs().max())
+    for _ in range(3):
+        dc = torch.from_numpy(rng.standard_normal(a_c.shape)).cuda()
+        df = torch.from_numpy(rng.standard_normal(a_f.shape)).cuda()
+        fd = (8 * (loss(dc, df, eps) - loss(dc, df, -eps))
+              - (loss(dc, df, 2 * eps) - loss(dc, df, -2 * eps))) / (12 * eps)
+        an = float((gc * dc).sum() + (gf * df).sum())
+        assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)

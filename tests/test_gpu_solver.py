@@ -118,9 +118,12 @@ def test_solve_fp64(mfp, disc, mapping, k, n, limit):
     assert rel_err(xh, xd) <= 1e-7
 
 
-@pytest.mark.parametrize("disc", ["cg", "dg"])
-def test_solve_mixed_precision(mfp, disc):
-    n, k = (8, 8, 8), 3
+@pytest.mark.parametrize("disc,k,n", [
+    ("cg", 1, (8, 8, 8)), ("dg", 1, (8, 8, 8)),
+    ("cg", 3, (8, 8, 8)), ("dg", 3, (8, 8, 8)),
+    ("cg", 4, (8, 8, 8)), ("dg", 4, (4, 4, 4)),
+    ("cg", 8, (4, 4, 4)), ("dg", 8, (4, 4, 4))])
+def test_solve_mixed_precision(mfp, disc, k, n):
     op64, P = pair(mfp, disc, "sine", k, n)
     op32, _ = pair(mfp, disc, "sine", k, n, prec="fp32")
     b = op64.rhs(0)
@@ -152,6 +155,32 @@ def test_batched_solve_matches_single(mfp):
         assert rel_err(Xh[:, r], x1.cpu().numpy()) <= 1e-12
         res = np.linalg.norm(Bh[:, r] - A @ Xh[:, r]) / np.linalg.norm(Bh[:, r])
         assert res <= 1.05e-10
+
+
+@pytest.mark.parametrize("disc,k,n,R", [("cg", 2, (8, 8, 8), 4),
+                                        ("cg", 3, (4, 4, 4), 16),
+                                        ("dg", 2, (4, 4, 4), 16)])
+def test_batched_mixed_solve(mfp, disc, k, n, R):
+    # the batched workload's form: R columns through the float32 V-cycle
+    # (batched transfer, Chebyshev, dense coarse level, graph replay) inside
+    # the float64 CG; every column solves the oracle's system and agrees
+    # with its own single-column solve (float atomics in the CG apply change
+    # the rounding, so to the solver tolerance rather than bit for bit)
+    op, P = pair(mfp, disc, "sine", k, n, prec="fp32")
+    N = op.n_dofs()
+    B = torch.empty(N * R, dtype=torch.float64, device="cuda")
+    for r in range(R):
+        op.rhs(1, synthetic.gaussian_terms(1000 + r), out=B[r:], stride=R)
+    X, its, rel = op.solve(B, n_rhs=R, rtol=1e-10)
+    Xh = X.reshape(N, R).cpu().numpy()
+    Bh = B.reshape(N, R).cpu().numpy()
+    A = fem.assemble(P)
+    for r in range(R):
+        res = np.linalg.norm(Bh[:, r] - A @ Xh[:, r]) / np.linalg.norm(Bh[:, r])
+        assert res <= 1.05e-10, (r, res)
+        x1, it1, _ = op.solve(torch.from_numpy(Bh[:, r].copy()).cuda())
+        assert abs(its[r] - it1[0]) <= 1
+        assert rel_err(Xh[:, r], x1.cpu().numpy()) <= 1e-7
 
 
 def test_apply_counts_per_iteration(mfp):

@@ -69,3 +69,25 @@ def test_rhs_noalloc_rejects_too_many_terms(mfp):
                              ctypes.c_void_p(out.data_ptr()), 1, None)
     assert st == mfp.MFP_ERR_ARG
     assert b"4096" in lib.mfp_last_error()
+
+
+@pytest.mark.parametrize("disc", ["cg", "dg"])
+def test_rhs_noalloc_takes_no_device_memory(mfp, disc):
+    # on a freshly created context: the device's free memory is the same
+    # before and after the first two calls (mfp_create did the set-up)
+    lib = mfp.lib()
+    op = mfp.Poisson(4, 3, 2, 3, disc=disc, n_levels=1)
+    out = torch.zeros(op.n_dofs(), dtype=torch.float64, device="cuda")
+    g = np.ascontiguousarray(synthetic.gaussian_terms(1002))
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        st = lib.mfp_rhs_noalloc(op._h, 1, _dp(g), g.shape[0],
+                                 ctypes.c_void_p(out.data_ptr()), 1, s)
+        assert st == mfp.MFP_OK, lib.mfp_last_error()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    ref = op.rhs(1, g).cpu().numpy()
+    assert rel_err(out.cpu().numpy(), ref) <= 1e-12
