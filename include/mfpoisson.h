@@ -65,7 +65,7 @@ typedef enum {
 
 enum { MFP_CG = 0, MFP_SIPG = 1 };
 enum { MFP_FP64 = 0, MFP_FP32 = 1, MFP_MIXED = 2 };
-enum { MFP_MAP_IDENTITY = 0, MFP_MAP_SINE = 1 };
+enum { MFP_MAP_IDENTITY = 0, MFP_MAP_SINE = 1, MFP_MAP_NODES = 2 };
 enum { MFP_ARITH_DF = 0, MFP_ARITH_NATIVE = 1 };
 
 typedef struct {
@@ -79,7 +79,10 @@ typedef struct {
                             level); MFP_MAP_SINE: x -> x + map_param
                             sin(pi x) sin(pi y) sin(pi z) (1,1,1), degree-k
                             isoparametric interpolation through the
-                            Gauss-Lobatto support points (Sec. 2)           */
+                            Gauss-Lobatto support points (Sec. 2);
+                            MFP_MAP_NODES: the support points are given in
+                            map_nodes (Sec. 2: a degree-k polynomial map
+                            through Gauss-Lobatto support points)          */
   double map_param;      /* amplitude for MFP_MAP_SINE (|amp| < 1/(pi sqrt 3)) */
   double kappa;          /* constant coefficient (> 0) until
                             mfp_set_coefficient is called                   */
@@ -110,7 +113,22 @@ typedef struct {
                             (values 0..62).                                 */
   double box_lo, box_hi; /* domain [box_lo, box_hi]^3: the unit cube mapped
                             by `mapping`, then by x -> box_lo + (box_hi -
-                            box_lo) x (default 0, 1; Sec. 5 uses -1, 1)     */
+                            box_lo) x (default 0, 1; Sec. 5 uses -1, 1);
+                            MFP_MAP_NODES needs the default (the nodes are
+                            physical points)                                */
+  const double* map_nodes; /* MFP_MAP_NODES: HOST array [ncells][(k+1)^3][3]
+                            of the physical support points of every finest
+                            cell (cell and local node order of the vector
+                            layouts above), the images of the cell's
+                            Gauss-Lobatto grid.  Neighbouring cells must
+                            give identical points on their common face (a
+                            conforming mesh).  Copied during mfp_create; the
+                            caller keeps ownership.  Coarse levels take the
+                            finer level's isoparametric map evaluated at
+                            their own Gauss-Lobatto points (a point on the
+                            interface of two children from the upper one).
+                            A map with det J <= 0 at a quadrature point
+                            returns MFP_ERR_ARG.  NULL otherwise.          */
 } mfp_desc;
 
 /* Fill `desc` with the defaults (1 cell, k=1, CG, identity map, kappa 1,

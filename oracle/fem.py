@@ -126,7 +126,11 @@ class Problem:
 
     disc          'cg' (Sec. 2.1) or 'dg' (symmetric interior penalty, Sec. 2.2)
     mapping       'identity' or 'sine': x -> x + amp sin(pi x) sin(pi y)
-                  sin(pi z) (1,1,1), interpolated isoparametrically
+                  sin(pi z) (1,1,1), interpolated isoparametrically; or
+                  'nodes': the support points are given (map_nodes)
+    map_nodes     mapping 'nodes': physical support points [ncells, p^3, 3]
+                  (the images of each cell's Gauss-Lobatto grid, local order
+                  a = ax + p ay + p^2 az); the box is not applied to them
     kappa         constant coefficient, used when a_cell / a_face are None
     a_cell        optional [ncells, p^3] coefficient at cell quadrature points
     a_face        optional [nfaces, p^2] coefficient at face quadrature points
@@ -143,9 +147,12 @@ class Problem:
 
     def __init__(self, nx, ny, nz, k, disc="cg", mapping="identity", amp=0.0,
                  kappa=1.0, a_cell=None, a_face=None, penalty_factor=1.0,
-                 dirichlet=True, box=(0.0, 1.0), neumann_sides=()):
+                 dirichlet=True, box=(0.0, 1.0), neumann_sides=(),
+                 map_nodes=None):
         if disc not in ("cg", "dg"):
             raise ValueError(disc)
+        if mapping not in ("identity", "sine", "nodes"):
+            raise ValueError(mapping)
         self.n = (int(nx), int(ny), int(nz))
         self.k = int(k)
         self.p = self.k + 1
@@ -166,6 +173,12 @@ class Problem:
         self.h = tuple(1.0 / n for n in self.n)
         self.ncells = self.n[0] * self.n[1] * self.n[2]
         self.nodes1 = gll_points(self.k)
+        self.map_nodes = None
+        if mapping == "nodes":
+            X = np.asarray(map_nodes, float)
+            if X.shape != (self.ncells, self.p ** 3, 3):
+                raise ValueError("map_nodes must be [ncells, p^3, 3]")
+            self.map_nodes = X
 
     # ---- sizes -----------------------------------------------------------
     @property
@@ -222,7 +235,9 @@ class Problem:
 
     def support_points(self, cells):
         """Isoparametric support points X[c, a, 3]: the analytic map evaluated
-        at the GLL nodes of each cell (Sec. 2)."""
+        at the GLL nodes of each cell (Sec. 2), or the given nodes."""
+        if self.map_nodes is not None:
+            return self.map_nodes[np.asarray(cells)]
         ref = tensor_points(self.nodes1)
         return self.phi_map(self.logical_points(cells, ref))
 
@@ -597,7 +612,8 @@ def manufactured_rhs(prob, f, u, grad_u):
         return b + sipg_dirichlet_vector(prob, u)
     full = Problem(*prob.n, prob.k, disc="cg", mapping=prob.mapping,
                    amp=prob.amp, kappa=prob.kappa, a_cell=prob.a_cell,
-                   a_face=prob.a_face, dirichlet=False, box=prob.box)
+                   a_face=prob.a_face, dirichlet=False, box=prob.box,
+                   map_nodes=prob.map_nodes)
     dmask = prob.constrained()
     g = np.zeros(prob.n_dofs)
     g[dmask] = u(prob.node_points()[dmask])

@@ -46,11 +46,34 @@ def coarsen_problem(prob):
     a_cell = a_face = None
     if prob.a_cell is not None:
         a_cell, a_face = coarsen_coefficient(prob, nc)
+    nodes = coarsen_nodes(prob, nc) if prob.map_nodes is not None else None
     return fem.Problem(*nc, prob.k, disc=prob.disc, mapping=prob.mapping,
                        amp=prob.amp, kappa=prob.kappa, a_cell=a_cell,
                        a_face=a_face, penalty_factor=prob.penalty_factor,
                        dirichlet=prob.dirichlet, box=prob.box,
-                       neumann_sides=tuple(prob.neumann))
+                       neumann_sides=tuple(prob.neumann), map_nodes=nodes)
+
+
+def coarsen_nodes(prob, nc):
+    """Support points of the coarse cells of a mesh given by its nodes: the
+    fine isoparametric map evaluated at the coarse cells' Gauss-Lobatto
+    points (a coarse point on the interface of two children is taken from
+    the upper child)."""
+    p = prob.p
+    r = prob.nodes1                       # coarse GLL nodes on [-1, 1]
+    off = np.minimum(np.floor(r + 1.0), 1).astype(int)   # child per axis
+    eta = 2.0 * (r + 1.0 - off) - 1.0     # its reference coordinate
+    ncc = nc[0] * nc[1] * nc[2]
+    C = np.arange(ncc)
+    cx, cy, cz = C % nc[0], (C // nc[0]) % nc[1], C // (nc[0] * nc[1])
+    out = np.empty((ncc, p ** 3, 3))
+    for a in range(p ** 3):
+        ax, ay, az = a % p, (a // p) % p, a // (p * p)
+        child = prob.cell_index(2 * cx + off[ax], 2 * cy + off[ay],
+                                2 * cz + off[az])
+        val, _ = fem.basis3d(prob.k, np.array([[eta[ax], eta[ay], eta[az]]]))
+        out[:, a] = np.einsum("cbd,b->cd", prob.support_points(child), val[0])
+    return out
 
 
 def coarsen_coefficient(prob, nc):

@@ -424,6 +424,7 @@ void free_level(Level& L) {
                     &L.ddf.sgl})
     dfree(*p);
   dfree(L.vol);
+  dfree(L.nodes);
   dfree(L.t_res);
   dfree(L.t_d);
   dfree(L.t_x);
@@ -593,8 +594,15 @@ mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out) {
     MFP_REQUIRE(d.nx >= 1 && d.ny >= 1 && d.nz >= 1, "cell counts must be >= 1");
     MFP_REQUIRE(d.degree >= 1 && d.degree <= 8, "degree must be in 1..8");
     MFP_REQUIRE(d.disc == MFP_CG || d.disc == MFP_SIPG, "unknown disc");
-    MFP_REQUIRE(d.mapping == MFP_MAP_IDENTITY || d.mapping == MFP_MAP_SINE,
+    MFP_REQUIRE(d.mapping == MFP_MAP_IDENTITY || d.mapping == MFP_MAP_SINE ||
+                    d.mapping == MFP_MAP_NODES,
                 "unknown mapping");
+    MFP_REQUIRE(d.mapping != MFP_MAP_NODES || d.map_nodes,
+                "MFP_MAP_NODES needs map_nodes");
+    MFP_REQUIRE(d.mapping != MFP_MAP_NODES ||
+                    (d.box_lo == 0.0 && d.box_hi == 1.0),
+                "MFP_MAP_NODES: the nodes are physical points, leave the box "
+                "at [0, 1]");
     MFP_REQUIRE(d.mapping != MFP_MAP_SINE ||
                     std::fabs(d.map_param) * 3.14159265358979 * std::sqrt(3.0) < 1.0,
                 "map_param too large: the mapping would fold");
@@ -653,8 +661,9 @@ mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out) {
       L.k = d.degree;
       L.p = d.degree + 1;
       L.disc = d.disc;
-      L.curved = d.mapping == MFP_MAP_SINE && d.map_param != 0.0;
-      L.map_amp = L.curved ? d.map_param : 0.0;
+      L.curved = (d.mapping == MFP_MAP_SINE && d.map_param != 0.0) ||
+                 d.mapping == MFP_MAP_NODES;
+      L.map_amp = d.mapping == MFP_MAP_SINE ? d.map_param : 0.0;
       L.kappa = d.kappa;
       L.penalty = d.penalty_factor;
       L.ncells = (int64_t)L.n[0] * L.n[1] * L.n[2];
@@ -687,6 +696,21 @@ mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out) {
     MFP_CHECK_CUDA(cudaMallocHost(&c->host_scal,
                                   sizeof(double) * S_COUNT * kMaxRhs));
     ensure_scratch(c, 1);
+    if (d.mapping == MFP_MAP_NODES) {
+      // the given support points on the finest level, re-interpolated on
+      // the coarser ones
+      Level& F = c->levels.back();
+      const int64_t n = F.ncells * p3 * 3;
+      F.nodes = dalloc<double>(n);
+      MFP_CHECK_CUDA(cudaMemcpyAsync(F.nodes, d.map_nodes, n * sizeof(double),
+                                     cudaMemcpyHostToDevice, st(stream)));
+      for (int l = nl - 2; l >= 0; --l) {
+        Level& C = c->levels[l];
+        C.nodes = dalloc<double>(C.ncells * p3 * 3);
+        launch_coarsen_nodes(c->levels[l + 1], C, st(stream));
+      }
+      MFP_CHECK_CUDA(cudaStreamSynchronize(st(stream)));
+    }
     build_levels(c, st(stream));
     noalloc_prepare(c->device, d.degree + 1);
     *out = c;

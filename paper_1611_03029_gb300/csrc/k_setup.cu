@@ -14,6 +14,7 @@ struct GeoArgs {
   double h[3];  // cell size on the unit cube (1 / n)
   double amp;
   double lo, len;  // then x -> lo + len x onto the box [lo, lo + len]^3
+  const double* nodes;  // given support points [ncells][p^3][3], or null
 };
 
 // All tables of degree P-1 in shared memory.
@@ -49,10 +50,18 @@ __device__ __forceinline__ void phi_map(double amp, double& x, double& y,
   }
 }
 
-// Support points (images of the GLL nodes) of cell (cx,cy,cz) into X[p^3][3].
+// Support points (images of the GLL nodes) of cell (cx,cy,cz) into X[p^3][3]:
+// the given nodes, or the analytic map at the cell's GLL grid.
 template <int P>
 __device__ void support_points(const GeoArgs& g, const ShTab<P>& t, int cx,
                                int cy, int cz, double* X) {
+  if (g.nodes) {
+    const size_t cell = cx + (size_t)g.n[0] * (cy + (size_t)g.n[1] * cz);
+    const double* src = g.nodes + cell * 3 * P * P * P;
+    for (int i = threadIdx.x; i < 3 * P * P * P; i += blockDim.x)
+      X[i] = src[i];
+    return;
+  }
   for (int a = threadIdx.x; a < P * P * P; a += blockDim.x) {
     const int ax = a % P, ay = (a / P) % P, az = a / (P * P);
     double x = (cx + t.x[ax]) * g.h[0];
@@ -779,6 +788,51 @@ __global__ void k_coarsen_faces(const double* fine, double* coarse, int D,
     coarse[((size_t)coarse_off + F) * P2 + q] = acc;
 }
 
+// Support points of the coarse cells of a mesh given by its nodes: the fine
+// isoparametric map evaluated at each coarse cell's Gauss-Lobatto points.
+// Coarse point a lies, per axis, in child offset o = min(floor(2 x_a), 1) at
+// the child's unit coordinate 2 x_a - o (x_a the GLL node on [0, 1]); a point
+// on the interface of two children is taken from the upper one.  One block
+// per coarse cell, one thread per point.
+template <int P>
+__global__ void k_coarsen_nodes(const double* fine, double* coarse, int nf0,
+                                int nf1, int nc0, int nc1) {
+  constexpr int P3 = P * P * P;
+  __shared__ double gx[P];
+  if (threadIdx.x < P) gx[threadIdx.x] = c_tab64[P - 2].x[threadIdx.x];
+  __syncthreads();
+  const int C = blockIdx.x;
+  const int c3[3] = {C % nc0, (C / nc0) % nc1, C / (nc0 * nc1)};
+  for (int a = threadIdx.x; a < P3; a += blockDim.x) {
+    const int ai[3] = {a % P, (a / P) % P, a / (P * P)};
+    double L[3][P];
+    int f3[3];
+    for (int e = 0; e < 3; ++e) {
+      const double u = 2.0 * gx[ai[e]];
+      const int o = u >= 1.0 ? 1 : 0;
+      f3[e] = 2 * c3[e] + o;
+      const double xi = u - o;
+      for (int b = 0; b < P; ++b) {  // Lagrange basis of the GLL nodes at xi
+        double v = 1.0;
+        for (int m = 0; m < P; ++m)
+          if (m != b) v *= (xi - gx[m]) / (gx[b] - gx[m]);
+        L[e][b] = v;
+      }
+    }
+    const size_t fc = f3[0] + (size_t)nf0 * (f3[1] + (size_t)nf1 * f3[2]);
+    const double* X = fine + fc * 3 * P3;
+    double y[3] = {0, 0, 0};
+    for (int bz = 0; bz < P; ++bz)
+      for (int by = 0; by < P; ++by)
+        for (int bx = 0; bx < P; ++bx) {
+          const double w = L[0][bx] * L[1][by] * L[2][bz];
+          const int b = bx + P * (by + P * bz);
+          for (int d = 0; d < 3; ++d) y[d] += w * X[3 * b + d];
+        }
+    for (int d = 0; d < 3; ++d) coarse[((size_t)C * P3 + a) * 3 + d] = y[d];
+  }
+}
+
 GeoArgs geo_args(const Level& L) {
   GeoArgs g;
   for (int d = 0; d < 3; ++d) {
@@ -789,6 +843,7 @@ GeoArgs geo_args(const Level& L) {
   g.amp = L.map_amp;
   g.lo = L.box_lo;
   g.len = L.box_len;
+  g.nodes = L.nodes;
   return g;
 }
 
@@ -814,6 +869,19 @@ void launch_curved_cell_geometry(Level& L, cudaStream_t s) {
   MFP_CHECK_CUDA(cudaStreamSynchronize(s));
   cudaFreeAsync(bad, s);
   MFP_REQUIRE(!hbad, "mapping is not invertible (det J <= 0)");
+}
+
+void launch_coarsen_nodes(const Level& fine, Level& coarse, cudaStream_t s) {
+  ensure_tables();
+  dispatch_p(fine.p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
+    const int thr = P * P * P < 256 ? ((P * P * P + 31) / 32) * 32 : 256;
+    k_coarsen_nodes<P><<<(int)coarse.ncells, thr, 0, s>>>(
+        fine.nodes, coarse.nodes, fine.n[0], fine.n[1], coarse.n[0],
+        coarse.n[1]);
+  });
+  MFP_CHECK_CUDA(cudaGetLastError());
+  note_launch();
 }
 
 void launch_curved_face_geometry(Level& L, cudaStream_t s) {

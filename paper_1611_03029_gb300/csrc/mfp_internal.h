@@ -185,6 +185,7 @@ struct Level {
   double kappa = 1.0;
   double penalty = 1.0;
   double map_amp = 0.0;
+  double* nodes = nullptr;    // given support points [ncells][p^3][3]
   double* vol = nullptr;      // curved: cell volumes [ncells]
   LevelData<double> d64;
   LevelData<float> d32;
@@ -295,6 +296,8 @@ void launch_split(const double* a, float* hi, float* lo, int64_t n,
                   cudaStream_t s);
 
 void launch_curved_cell_geometry(Level& L, cudaStream_t s);
+// support points of `coarse` from the isoparametric map of `fine`
+void launch_coarsen_nodes(const Level& fine, Level& coarse, cudaStream_t s);
 void launch_curved_face_geometry(Level& L, cudaStream_t s);
 void launch_diagonal(const Level& L, double* diag, cudaStream_t s);
 void launch_rhs(const Level& L, int kind, const double* params_dev,

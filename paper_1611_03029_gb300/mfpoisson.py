@@ -17,7 +17,7 @@ MFP_OK, MFP_ERR_ARG, MFP_ERR_CUDA, MFP_ERR_OOM = 0, -1, -2, -3
 MFP_ERR_NOT_CONVERGED, MFP_ERR_STATE = -4, -6
 MFP_CG, MFP_SIPG = 0, 1
 MFP_FP64, MFP_FP32, MFP_MIXED = 0, 1, 2
-MFP_MAP_IDENTITY, MFP_MAP_SINE = 0, 1
+MFP_MAP_IDENTITY, MFP_MAP_SINE, MFP_MAP_NODES = 0, 1, 2
 MFP_ARITH_DF, MFP_ARITH_NATIVE = 0, 1
 
 
@@ -33,7 +33,8 @@ class MfpDesc(ctypes.Structure):
                 ("eig_cg_iters", ctypes.c_int),
                 ("fp64_arith", ctypes.c_int),
                 ("neumann_sides", ctypes.c_int),
-                ("box_lo", ctypes.c_double), ("box_hi", ctypes.c_double)]
+                ("box_lo", ctypes.c_double), ("box_hi", ctypes.c_double),
+                ("map_nodes", ctypes.POINTER(ctypes.c_double))]
 
 
 class MfpError(RuntimeError):
@@ -141,14 +142,24 @@ class Poisson:
                  mapping="identity", map_param=0.0, kappa=1.0,
                  penalty_factor=1.0, mg_precision="fp64", cheb_degree=5,
                  eig_cg_iters=15, fp64_arith="df", neumann_sides=(),
-                 box=(0.0, 1.0), stream=None):
+                 box=(0.0, 1.0), map_nodes=None, stream=None):
         L = lib()
         d = MfpDesc()
         L.mfp_desc_default(ctypes.byref(d))
         d.nx, d.ny, d.nz, d.degree = nx, ny, nz, degree
         d.disc = {"cg": MFP_CG, "dg": MFP_SIPG, "sipg": MFP_SIPG}[disc]
         d.n_levels = n_levels
-        d.mapping = {"identity": MFP_MAP_IDENTITY, "sine": MFP_MAP_SINE}[mapping]
+        d.mapping = {"identity": MFP_MAP_IDENTITY, "sine": MFP_MAP_SINE,
+                     "nodes": MFP_MAP_NODES}[mapping]
+        nodes = None
+        if mapping == "nodes":
+            import numpy as np
+            # host array [ncells][(k+1)^3][3], copied by mfp_create
+            nodes = np.ascontiguousarray(map_nodes, dtype=np.float64)
+            if nodes.size != nx * ny * nz * (degree + 1) ** 3 * 3:
+                raise ValueError("map_nodes must be [ncells, (k+1)^3, 3]")
+            d.map_nodes = nodes.ctypes.data_as(
+                ctypes.POINTER(ctypes.c_double))
         d.map_param = map_param
         d.kappa = kappa
         d.penalty_factor = penalty_factor

@@ -132,3 +132,33 @@ def strong_coefficient(n, p, box=(-1.0, 1.0)):
     a_face = strong_coefficient_field(lo + (hi - lo) * face_points(n, p))
     return a_cell, a_face
 
+
+
+def perturbed_lattice_nodes(n, k, seed, amp=0.05):
+    """Support points [ncells, (k+1)^3, 3] of a conforming mesh of the unit
+    cube: the equispaced lattice of (n_e k + 1) points per axis, every
+    interior lattice point moved by amp / (n_e k) times a uniform draw in
+    [-1, 1]^3 (boundary points stay, so the domain is still the unit cube),
+    then handed to each cell as its local nodes a = ax + p ay + p^2 az
+    (neighbours share the points of their common face)."""
+    rng = np.random.default_rng(seed)
+    p = k + 1
+    g = [m * k + 1 for m in n]
+    iz, iy, ix = np.meshgrid(np.arange(g[2]), np.arange(g[1]),
+                             np.arange(g[0]), indexing="ij")
+    idx = [ix.reshape(-1), iy.reshape(-1), iz.reshape(-1)]
+    pts = np.stack([idx[e] / (g[e] - 1.0) for e in range(3)], -1)
+    noise = rng.uniform(-1.0, 1.0, pts.shape)
+    interior = np.ones(pts.shape[0], bool)
+    for e in range(3):
+        interior &= (idx[e] > 0) & (idx[e] < g[e] - 1)
+    for e in range(3):
+        pts[:, e] += np.where(interior, amp / (g[e] - 1.0) * noise[:, e], 0)
+    nc = n[0] * n[1] * n[2]
+    c = np.arange(nc)
+    cx, cy, cz = c % n[0], (c // n[0]) % n[1], c // (n[0] * n[1])
+    a = np.arange(p ** 3)
+    ax, ay, az = a % p, (a // p) % p, a // (p * p)
+    gi = ((cx[:, None] * k + ax) + g[0] * ((cy[:, None] * k + ay)
+                                          + g[1] * (cz[:, None] * k + az)))
+    return pts[gi]

@@ -32,6 +32,7 @@ def test_desc_defaults_land_in_their_fields(mfp):
     assert d.fp64_arith == mfp.MFP_ARITH_DF
     assert d.neumann_sides == 0
     assert (d.box_lo, d.box_hi) == (0.0, 1.0)
+    assert not d.map_nodes
 
 
 @pytest.mark.parametrize("field,value,msg", [
@@ -50,6 +51,21 @@ def test_create_rejects_bad_descriptions(mfp, field, value, msg):
     assert st == mfp.MFP_ERR_ARG
     assert not h.value
     assert msg in mfp.lib().mfp_last_error().decode()
+
+
+def test_create_rejects_node_mapping_without_nodes_or_with_box(mfp):
+    d = default_desc(mfp)
+    d.mapping = mfp.MFP_MAP_NODES
+    h = ctypes.c_void_p()
+    st = mfp.lib().mfp_create(ctypes.byref(d), None, ctypes.byref(h))
+    assert st == mfp.MFP_ERR_ARG and not h.value
+    assert "map_nodes" in mfp.lib().mfp_last_error().decode()
+    nodes = (ctypes.c_double * 24)()
+    d.map_nodes = ctypes.cast(nodes, ctypes.POINTER(ctypes.c_double))
+    d.box_lo = -1.0
+    st = mfp.lib().mfp_create(ctypes.byref(d), None, ctypes.byref(h))
+    assert st == mfp.MFP_ERR_ARG and not h.value
+    assert "box" in mfp.lib().mfp_last_error().decode()
 
 
 def test_neumann_mask(mfp):

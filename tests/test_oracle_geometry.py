@@ -72,3 +72,64 @@ def test_coarsened_linear_coefficient_is_centroid_value(k):
     fcent = synthetic.face_points(nc, p).mean(axis=1)
     assert c_face.shape == (fcent.shape[0], p * p)
     assert np.abs(c_face - _linear(fcent)[:, None]).max() <= 1e-14
+
+
+@pytest.mark.parametrize("disc", ["cg", "dg"])
+@pytest.mark.parametrize("mapping", ["identity", "sine"])
+def test_given_nodes_reproduce_the_mapping(disc, mapping):
+    # support points handed over as nodes give the same operator
+    n, k = (2, 3, 2), 2
+    P = fem.Problem(*n, k, disc=disc, mapping=mapping, amp=0.1)
+    Q = fem.Problem(*n, k, disc=disc, mapping="nodes",
+                    map_nodes=P.support_points(np.arange(P.ncells)))
+    A, B = fem.assemble(P), fem.assemble(Q)
+    assert abs(A - B).max() <= 1e-14 * abs(A).max()
+
+
+def _quadratic_map(x):
+    y = x.copy()
+    for d in range(3):
+        e = (d + 1) % 3
+        y[..., d] += 0.05 * x[..., e] * (1.0 - x[..., e])
+    return y
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_coarse_nodes_reproduce_a_polynomial_map(k):
+    # the fine isoparametric map of a degree-2 map is the map itself, so the
+    # coarse nodes (the fine map at the coarse Gauss-Lobatto points) are the
+    # map's values there; this checks the child and the reference point
+    n = (4, 2, 6)
+    I = fem.Problem(*n, k)
+    nodes = _quadratic_map(I.support_points(np.arange(I.ncells)))
+    P = fem.Problem(*n, k, mapping="nodes", map_nodes=nodes)
+    nc = (2, 1, 3)
+    Ic = fem.Problem(*nc, k)
+    got = mg.coarsen_nodes(P, nc)
+    ref = _quadratic_map(Ic.support_points(np.arange(Ic.ncells)))
+    assert np.abs(got - ref).max() <= 1e-14
+
+
+@pytest.mark.parametrize("disc", ["cg", "dg"])
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_perturbed_lattice_mesh_is_valid(disc, k):
+    # the generator's meshes are conforming and invertible, and their
+    # operator is symmetric positive definite (P1) on every level
+    n = (4, 4, 2)
+    nodes = synthetic.perturbed_lattice_nodes(n, k, seed=3)
+    P = fem.Problem(*n, k, disc=disc, mapping="nodes", map_nodes=nodes)
+    for Q in mg.hierarchy(P, 2):
+        A = fem.assemble(Q).toarray()
+        assert np.abs(A - A.T).max() <= 1e-13 * np.abs(A).max()
+        np.linalg.cholesky(A)
+    # the boundary points stay on the cube's faces, so the cells fill it;
+    # det J has degree 3k - 1 per axis, which the (k+1)-point Gauss rule
+    # integrates exactly for k <= 2 only
+    vol = fem.cell_volumes(P, np.arange(P.ncells))
+    assert abs(vol.sum() - 1.0) <= (1e-13 if k <= 2 else 1e-5)
+    # neighbours share their face nodes: the CG node positions agree
+    Q = fem.Problem(*n, k, mapping="nodes", map_nodes=nodes)
+    dm = Q.dof_map()
+    X = np.zeros((Q.n_dofs, 3))
+    X[dm.ravel()] = nodes.reshape(-1, 3)
+    assert np.abs(X[dm] - nodes).max() == 0.0
