@@ -82,9 +82,26 @@ void ensure_fbuf(mfp_ctx* c, Level& L, int R, cudaStream_t s) {
   L.fbuf_rhs = R;
 }
 
+// The update `epi` on the finished result (see Epi): fused into the face-add
+// kernel of a matrix-free SIPG apply, else a vector kernel after the apply.
+template <typename T>
+void epi_after(const Level& L, const T* y, T* dst, int R, const Epi<T>* epi,
+               cudaStream_t s) {
+  if (!epi || epi->mode == EPI_STORE) return;
+  const int64_t n = L.ndofs;
+  if (epi->mode == EPI_RESIDUAL)
+    launch_residual<T>(epi->b, y, dst, n * R, s);
+  else if (epi->mode == EPI_CHEB_FIRST)
+    launch_cheb_first<T>(epi->b, epi->dinv, epi->d, epi->x, y, epi->c1, n, R,
+                         s);
+  else
+    launch_cheb_step<T>(epi->b, epi->dinv, epi->d, epi->x, y, epi->c1,
+                        epi->c2, n, R, s);
+}
+
 template <typename T>
 void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
-                 cudaStream_t s) {
+                 cudaStream_t s, const Epi<T>* epi = nullptr) {
   LevelData<T>& D = level_data<T>(L);
   MFP_REQUIRE(D.valid, "level data of this precision was not built "
                        "(mg_precision must be MFP_FP32 for float applies)");
@@ -97,6 +114,7 @@ void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
     launch_dense_apply<T>(dense, src, dst, (int)L.ndofs, R, L.dpart, L.dcnt,
                           s);
     L.applies += R;
+    epi_after<T>(L, dst, dst, R, epi, s);
     return;
   }
   if (L.disc == MFP_CG)
@@ -110,21 +128,27 @@ void apply_level(mfp_ctx* c, Level& L, const T* src, T* dst, int R,
       const double* sd = reinterpret_cast<const double*>(src);
       double* dd = reinterpret_cast<double*>(dst);
       bool ok;
-      if (L.disc == MFP_CG)
+      const Epi<double>* e = reinterpret_cast<const Epi<double>*>(epi);
+      if (L.disc == MFP_CG) {
         ok = apply_cg_df_lo(L, sd, dd, R, cells, s) ||
              apply_cg_df_hi(L, sd, dd, R, cells, s);
-      else
-        ok = apply_dg_df_lo(L, sd, dd, R, cells, s) ||
-             apply_dg_df_hi(L, sd, dd, R, cells, s);
-      MFP_REQUIRE(ok, "degree out of range");
+        MFP_REQUIRE(ok, "degree out of range");
+        epi_after<T>(L, dst, dst, R, epi, s);
+      } else {
+        ok = apply_dg_df_lo(L, sd, dd, R, cells, s, e) ||
+             apply_dg_df_hi(L, sd, dd, R, cells, s, e);
+        MFP_REQUIRE(ok, "degree out of range");
+      }
       L.applies += R;
       return;
     }
   }
-  if (L.disc == MFP_CG)
+  if (L.disc == MFP_CG) {
     launch_apply_cg(L, D, src, dst, R, cells, s);
-  else
-    launch_apply_dg(L, D, src, dst, R, cells, s);
+    epi_after<T>(L, dst, dst, R, epi, s);
+  } else {
+    launch_apply_dg(L, D, src, dst, R, cells, s, epi);
+  }
   L.applies += R;
 }
 
@@ -133,30 +157,43 @@ void cheb_coeffs_first(const Level& L, double& c) {
   c = 1.0 / theta;
 }
 
-// Chebyshev smoother / coarse solve on level l (Sec. 4.1).
+// Chebyshev smoother / coarse solve on level l (Sec. 4.1).  From a zero
+// start on a coarsest level that stores it, the coarse solve is one product
+// with the matrix of the same Chebyshev iteration (assemble_coarse_solve).
 template <typename T>
 void smooth(mfp_ctx* c, int l, const T* b, T* x, bool zero, int R,
             cudaStream_t s) {
   Level& L = c->levels[l];
   LevelData<T>& D = level_data<T>(L);
+  if (l == 0 && zero) {
+    const T* M = nullptr;
+    if constexpr (sizeof(T) == 8)
+      M = reinterpret_cast<const T*>(L.csolve64);
+    else
+      M = reinterpret_cast<const T*>(L.csolve32);
+    if (M) {
+      launch_dense_apply<T>(M, b, x, (int)L.ndofs, R, L.dpart, L.dcnt, s);
+      return;
+    }
+  }
   T* res = static_cast<T*>(L.t_res);
   T* d = static_cast<T*>(L.t_d);
   const double theta = 0.5 * (L.cheb_hi + L.cheb_lo);
   const double delta = 0.5 * (L.cheb_hi - L.cheb_lo);
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
-  if (zero) {
+  Epi<T> e{EPI_CHEB_FIRST, b, D.dinv, d, x, 1.0 / theta, 0.0};
+  if (zero)
     launch_cheb_first<T>(b, D.dinv, d, x, nullptr, 1.0 / theta, L.ndofs, R,
                          s);
-  } else {
-    apply_level<T>(c, L, x, res, R, s);
-    launch_cheb_first<T>(b, D.dinv, d, x, res, 1.0 / theta, L.ndofs, R, s);
-  }
+  else
+    apply_level<T>(c, L, x, res, R, s, &e);
   for (int i = 1; i < L.cheb_degree; ++i) {
-    apply_level<T>(c, L, x, res, R, s);
     const double rho1 = 1.0 / (2.0 * sigma - rho);
-    launch_cheb_step<T>(b, D.dinv, d, x, res, rho1 * rho, 2.0 * rho1 / delta,
-                        L.ndofs, R, s);
+    e.mode = EPI_CHEB_STEP;
+    e.c1 = rho1 * rho;
+    e.c2 = 2.0 * rho1 / delta;
+    apply_level<T>(c, L, x, res, R, s, &e);
     rho = rho1;
   }
 }
@@ -183,8 +220,8 @@ void vcycle_level(mfp_ctx* c, int l, const T* b, T* x, int R,
   Level& C = c->levels[l - 1];
   T* res = static_cast<T*>(L.t_res);
   smooth<T>(c, l, b, x, true, R, s);
-  apply_level<T>(c, L, x, res, R, s);
-  launch_residual<T>(b, res, res, L.ndofs * R, s);
+  const Epi<T> e{EPI_RESIDUAL, b, nullptr, nullptr, nullptr, 0.0, 0.0};
+  apply_level<T>(c, L, x, res, R, s, &e);  // res = b - A x
   restrict_<T>(c, l, res, static_cast<T*>(C.t_b), R, s);
   vcycle_level<T>(c, l - 1, static_cast<const T*>(C.t_b),
                   static_cast<T*>(C.t_x), R, s);
@@ -370,8 +407,49 @@ void to_float_array(const double* a, float*& b, int64_t n, cudaStream_t s);
 void free_dense(Level& L) {
   dfree(L.dense64);
   dfree(L.dense32);
+  dfree(L.csolve64);
+  dfree(L.csolve32);
   dfree(L.dpart);
   dfree(L.dcnt);
+}
+
+// The coarse solve of Sec. 4.1 (Chebyshev from a zero start with the degree
+// and interval fixed at set-up) is a fixed polynomial in D^{-1} A applied to
+// D^{-1} b, so it is one linear operator: its matrix is found once by running
+// that iteration on blocks of identity columns, and each V-cycle then applies
+// it with one dense product instead of its degree's worth of operator
+// applications and vector updates.  Only the evaluation order (rounding)
+// differs from running the iteration.
+void assemble_coarse_solve(mfp_ctx* c, Level& L, cudaStream_t s) {
+  const int64_t n = L.ndofs;
+  const int blk = kMaxRhs;
+  double* M = dalloc<double>(n * n);
+  double* E = dalloc<double>(n * blk);
+  double* X = dalloc<double>(n * blk);
+  double* tres = dalloc<double>(n * blk);
+  double* td = dalloc<double>(n * blk);
+  void* keep_res = L.t_res;
+  void* keep_d = L.t_d;
+  L.t_res = tres;
+  L.t_d = td;
+  const int64_t keep_applies = L.applies;
+  for (int64_t c0 = 0; c0 < n; c0 += blk) {
+    const int R = (int)(n - c0 < blk ? n - c0 : blk);
+    launch_identity_block(E, n, c0, R, s);
+    smooth<double>(c, 0, E, X, true, R, s);
+    launch_store_columns(X, M, n, c0, R, s);
+  }
+  MFP_CHECK_CUDA(cudaStreamSynchronize(s));
+  L.t_res = keep_res;
+  L.t_d = keep_d;
+  L.applies = keep_applies;
+  dfree(E);
+  dfree(X);
+  dfree(tres);
+  dfree(td);
+  if (c->vprec == MFP_FP32) to_float_array(M, L.csolve32, n * n, s);
+  L.csolve64 = M;
+  MFP_CHECK_CUDA(cudaStreamSynchronize(s));
 }
 
 // Assembles the operator of a coarsest level with at most kDenseMax dofs as a
@@ -402,6 +480,7 @@ void assemble_dense(mfp_ctx* c, Level& L, cudaStream_t s) {
   L.dense64 = A;
   L.applies = 0;
   MFP_CHECK_CUDA(cudaStreamSynchronize(s));
+  assemble_coarse_solve(c, L, s);
 }
 
 void free_level(Level& L) {

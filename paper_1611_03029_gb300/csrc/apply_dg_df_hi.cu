@@ -5,11 +5,13 @@
 namespace mfp {
 
 bool apply_dg_df_hi(const Level& L, const double* src, double* dst,
-                     int nrhs, int cells, cudaStream_t s) {
+                     int nrhs, int cells, cudaStream_t s,
+                     const Epi<double>* epi) {
   if (L.p < 6) return false;
   ensure_tables();
   ApplyArgsDF a = make_apply_args_df(L, src, dst);
   a.stride = nrhs;
+  if (epi) a.epi = *epi;
   switch (L.p) {
     case 6:
       if (L.curved)

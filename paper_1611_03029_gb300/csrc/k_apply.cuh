@@ -45,6 +45,7 @@ struct ApplyArgs {
   int col;     // first column of this launch
   int cpb;     // cells per block
   int ncols;   // columns per block
+  Epi<T> epi;  // SIPG: update fused into k_dg_face_add_t
 };
 
 template <int P>
@@ -318,13 +319,15 @@ __global__ void __launch_bounds__(256) k_dg_face_add_t(const ApplyArgs<T> a) {
     const T gz = fb[(size_t)(5 * P2 + xy) * R];
     const T vz = fb[(size_t)(4 * P2 + xy) * R];
     const T wx = tv<T, P, T_DPHI0>(x), wy = tv<T, P, T_DPHI0>(y);
+    const size_t dof = cell * P3 + xy;
 #pragma unroll
     for (int z = 0; z < P; ++z) {
       T s = u[z];
       if (cx > 0) s += fma(wx, gx[z], vx[z]);
       if (cy > 0) s += fma(wy, gy[z], vy[z]);
       if (cz > 0) s += fma(tv<T, P, T_DPHI0>(z), gz, z == 0 ? vz : T(0));
-      out[(size_t)z * P2 * R] = s;
+      epi_finish(a.epi, a.dst, (dof + (size_t)z * P2) * R + col,
+                 dof + (size_t)z * P2, s);
     }
   }
 }

@@ -48,6 +48,7 @@ struct ApplyArgsDF {
   bool kappa_one;            // constant coefficient exactly 1
   df gs[3], ns[3], fa[3], sg[3];
   int stride, col, cpb, ncols;
+  Epi<double> epi;           // SIPG: update fused into k_dg_face_add
 };
 
 __device__ __forceinline__ df f2df(float2 v) { return df_make(v.x, v.y); }
@@ -878,9 +879,11 @@ __global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
         if (z == 0) acc_add(s[z], df_make(vz.x, vz.y));
       }
     }
+    const size_t dof = cell * P3 + xy;
 #pragma unroll
     for (int z = 0; z < P; ++z)
-      out[(size_t)z * P2 * R] = df_to_double(acc_get(s[z]));
+      epi_finish(a.epi, a.dst, (dof + (size_t)z * P2) * R + col,
+                 dof + (size_t)z * P2, df_to_double(acc_get(s[z])));
   }
 }
 

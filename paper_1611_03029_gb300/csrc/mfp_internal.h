@@ -136,6 +136,45 @@ struct RedScratch {
 // SIPG: bit 2d + s of `neumann` drops the operator terms of the faces on
 // side (d, s) (the extension of Eq. 7 leaves only data there).
 // ---------------------------------------------------------------------------
+// Vector update fused into the last kernel of an SIPG apply (the face-add
+// kernel, which completes y = (A src)_i of every dof), so that y itself is
+// never written and read back (Sec. 4.1 smoother and V-cycle residual):
+//   EPI_STORE       dst = y
+//   EPI_RESIDUAL    dst = b - y
+//   EPI_CHEB_FIRST  e = c1 dinv (b - y);        d = e; x += e  (dst unused)
+//   EPI_CHEB_STEP   e = c1 d + c2 dinv (b - y); d = e; x += e  (dst unused)
+// Vectors in the batched layout; dinv has one entry per dof.
+enum { EPI_STORE = 0, EPI_RESIDUAL = 1, EPI_CHEB_FIRST = 2, EPI_CHEB_STEP = 3 };
+template <typename T>
+struct Epi {
+  int mode;
+  const T* b;
+  const T* dinv;
+  T* d;
+  T* x;
+  double c1, c2;
+};
+
+// Applies the update of `e` to the finished value y of entry gi (dof `dof`).
+template <typename T, typename Y>
+__device__ __forceinline__ void epi_finish(const Epi<T>& e, T* dst, size_t gi,
+                                           size_t dof, Y y) {
+  if (e.mode == EPI_STORE) {
+    dst[gi] = (T)y;
+    return;
+  }
+  const Y r = (Y)e.b[gi] - y;
+  if (e.mode == EPI_RESIDUAL) {
+    dst[gi] = (T)r;
+    return;
+  }
+  const Y dr = (Y)e.c2 * ((Y)e.dinv[dof] * r);
+  const Y v = e.mode == EPI_CHEB_FIRST ? (Y)e.c1 * ((Y)e.dinv[dof] * r)
+                                       : (Y)e.c1 * (Y)e.d[gi] + dr;
+  e.d[gi] = (T)v;
+  e.x[gi] = (T)((Y)e.x[gi] + v);
+}
+
 struct Bc {
   int lo[3] = {0, 0, 0};
   int hi[3] = {0, 0, 0};
@@ -211,6 +250,10 @@ struct Level {
   // cells the cell kernels are latency-bound (about 30 us per apply).
   double* dense64 = nullptr;
   float* dense32 = nullptr;
+  // the coarse solve (zero-start Chebyshev of the bound-derived degree) as
+  // its dense matrix p(D^{-1} A) D^{-1}, column-major [ndofs][ndofs]
+  double* csolve64 = nullptr;
+  float* csolve32 = nullptr;
   double* dpart = nullptr;   // partial sums [kDenseSplit][kMaxRhs][ndofs]
   unsigned* dcnt = nullptr;  // arrival counters [row blocks][kMaxRhs]
 };
@@ -274,12 +317,13 @@ void launch_apply_cg(const Level& L, const LevelData<double>& D,
 void launch_apply_cg(const Level& L, const LevelData<float>& D,
                      const float* src, float* dst, int nrhs, int cells,
                      cudaStream_t s);
+// SIPG: `epi` (may be null = EPI_STORE) is applied by the face-add kernel
 void launch_apply_dg(const Level& L, const LevelData<double>& D,
                      const double* src, double* dst, int nrhs, int cells,
-                     cudaStream_t s);
+                     cudaStream_t s, const Epi<double>* epi);
 void launch_apply_dg(const Level& L, const LevelData<float>& D,
                      const float* src, float* dst, int nrhs, int cells,
-                     cudaStream_t s);
+                     cudaStream_t s, const Epi<float>* epi);
 
 // dst = A src in float64 I/O with double-float arithmetic on the FP32 pipes
 // (one translation unit per degree range; false if p is not in its range)
@@ -288,9 +332,9 @@ bool apply_cg_df_lo(const Level& L, const double* src, double* dst, int nrhs,
 bool apply_cg_df_hi(const Level& L, const double* src, double* dst, int nrhs,
                     int cells, cudaStream_t s);
 bool apply_dg_df_lo(const Level& L, const double* src, double* dst, int nrhs,
-                    int cells, cudaStream_t s);
+                    int cells, cudaStream_t s, const Epi<double>* epi);
 bool apply_dg_df_hi(const Level& L, const double* src, double* dst, int nrhs,
-                    int cells, cudaStream_t s);
+                    int cells, cudaStream_t s, const Epi<double>* epi);
 // hi / lo split of a float64 array
 void launch_split(const double* a, float* hi, float* lo, int64_t n,
                   cudaStream_t s);
