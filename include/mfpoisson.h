@@ -219,14 +219,17 @@ mfp_status mfp_rhs_noalloc(mfp_ctx* ctx, int f_kind, const double* params_host,
  * on the finest cells of an SIPG context (same mesh, box and Neumann sides),
  * with A = (w, kappa^-1 q), B^T = -(div w, u), D = -<v, tau u>,
  * C^T = <w . n, lambda>, G^T = <v, tau lambda>, H = sum <mu, tau lambda> and
- * tau = tau_factor kappa (Sec. 5: tau_factor 5).  Dirichlet faces hold data
- * traces and add no H^{-1} coupling.  x_dev and y_dev hold the cell unknowns
- * (q_x, q_y, q_z, u) in cell-major blocks of 4 (k+1)^3 nodal values (the
- * SIPG cell layout per field), 4 ncells (k+1)^3 doubles each, distinct.
- * Cartesian cells (MFP_MAP_IDENTITY) and the constant coefficient only
- * (MFP_ERR_ARG otherwise).  The first call allocates the context's trace
- * buffer (nfaces (k+1)^2 doubles): make it outside a stream capture.  Calls
- * on one context share that buffer: issue them in stream order.
+ * tau = tau_factor times the largest coefficient value on the face (Sec. 5:
+ * tau_factor 5).  Dirichlet faces hold data traces and add no H^{-1}
+ * coupling.  x_dev and y_dev hold the cell unknowns (q_x, q_y, q_z, u) in
+ * cell-major blocks of 4 (k+1)^3 nodal values (the SIPG cell layout per
+ * field), 4 ncells (k+1)^3 doubles each, distinct.  Any mapping; the
+ * coefficient is the constant one or the per-point values of
+ * mfp_set_coefficient (cell and face values both needed).  The first call
+ * allocates the context's trace buffer (nfaces (k+1)^2 doubles) and, on
+ * curved cells, per-point geometry (10 doubles per cell point, 4 per face
+ * point): make it outside a stream capture.  Calls on one context share
+ * those buffers: issue them in stream order.
  * Launches four kernels (traces per face direction, then the cells). */
 mfp_status mfp_hdg_apply(mfp_ctx* ctx, double tau_factor, const double* x_dev,
                          double* y_dev, void* stream);

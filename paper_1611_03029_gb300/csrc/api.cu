@@ -526,8 +526,11 @@ void free_ctx(mfp_ctx* c) {
   dfree(c->eig_out);
   dfree(c->params);
   dfree(c->hdg_lam);
+  dfree(c->hdg_cell);
+  dfree(c->hdg_face);
   dfree(c->red.part);
   dfree(c->red.cnt);
+  dfree(c->dev_err);
   dfree(c->mix_r);
   dfree(c->mix_z);
   if (c->host_scal) cudaFreeHost(c->host_scal);
@@ -570,7 +573,9 @@ void build_levels(mfp_ctx* c, cudaStream_t s) {
     const int64_t P3 = (int64_t)L.p * L.p * L.p, P2 = (int64_t)L.p * L.p;
     if (L.curved) {
       if (!L.d64.G) L.d64.G = dalloc<double>(L.ncells * 6 * P3);
-      if (f32 && !L.d32.G) L.d32.G = dalloc<float>(L.ncells * 6 * P3);
+      // one spare cell: the staged float kernel's last bulk copy is rounded
+      // up to 16 bytes
+      if (f32 && !L.d32.G) L.d32.G = dalloc<float>((L.ncells + 1) * 6 * P3);
       if (!L.vol) L.vol = dalloc<double>(L.ncells);
       launch_curved_cell_geometry(L, s);
       if (L.disc == MFP_SIPG) {
@@ -771,6 +776,9 @@ mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out) {
     c->eig_out = dalloc<double>(2);
     c->red.part = dalloc<double>((int64_t)kMaxRedBlocks * kMaxRhs);
     c->red.cnt = dalloc<unsigned>(1);
+    c->dev_err = dalloc<int>(1);
+    MFP_CHECK_CUDA(cudaMemsetAsync(c->dev_err, 0, sizeof(int), st(stream)));
+    for (auto& L : c->levels) L.err = c->dev_err;
     MFP_CHECK_CUDA(cudaMemsetAsync(c->red.cnt, 0, sizeof(unsigned), st(stream)));
     MFP_CHECK_CUDA(cudaMallocHost(&c->host_scal,
                                   sizeof(double) * S_COUNT * kMaxRhs));
@@ -896,12 +904,21 @@ mfp_status mfp_hdg_apply(mfp_ctx* c, double tau_factor, const double* x,
   MFP_REQUIRE(c->desc.disc == MFP_SIPG,
               "the HDG operator uses the cells of an SIPG context");
   Level& L = c->levels.back();
-  MFP_REQUIRE(!L.curved, "HDG apply: Cartesian cells only");
-  MFP_REQUIRE(!c->has_coef, "HDG apply: constant coefficient only");
   MFP_REQUIRE(tau_factor > 0 && std::isfinite(tau_factor),
               "tau_factor must be > 0");
-  if (!c->hdg_lam) c->hdg_lam = dalloc<double>(L.nfaces * L.p * L.p);
-  launch_hdg_apply(L, tau_factor * L.kappa, c->hdg_lam, x, y, st(stream));
+  MFP_REQUIRE(!c->has_coef || L.d64.kface,
+              "HDG apply: a per-point coefficient needs its face values");
+  const int64_t P3 = (int64_t)L.p * L.p * L.p, P2 = (int64_t)L.p * L.p;
+  if (!c->hdg_lam) c->hdg_lam = dalloc<double>(L.nfaces * P2);
+  if (L.curved && !c->hdg_cell) {
+    // w det J, J^{-1} per cell point and dA, the normal per face point
+    c->hdg_cell = dalloc<double>(L.ncells * 10 * P3);
+    c->hdg_face = dalloc<double>(L.nfaces * 4 * P2);
+    launch_curved_cell_geometry(L, st(stream), c->hdg_cell);
+    launch_curved_face_geometry(L, st(stream), c->hdg_face);
+  }
+  launch_hdg_apply(L, tau_factor, c->hdg_lam, c->hdg_cell, c->hdg_face, x, y,
+                   st(stream));
   API_END
 }
 
@@ -1084,6 +1101,17 @@ mfp_status mfp_solve(mfp_ctx* c, const double* b, double* x, int R,
     launch_cg_p(c->cg_p, c->cg_z, n, R, c->scal, s);
   }
   MFP_CHECK_CUDA(cudaStreamSynchronize(s));
+  {
+    int herr = 0;  // a staged kernel gave up waiting for its copies
+    MFP_CHECK_CUDA(cudaMemcpy(&herr, c->dev_err, sizeof(int),
+                              cudaMemcpyDeviceToHost));
+    if (herr) {
+      MFP_CHECK_CUDA(cudaMemset(c->dev_err, 0, sizeof(int)));
+      set_error("a kernel's shared-memory copy wait timed out; the result "
+                "is invalid");
+      return MFP_ERR_CUDA;
+    }
+  }
   if (iters_out)
     for (int r = 0; r < R; ++r) iters_out[r] = its[r];
   if (relres_out)

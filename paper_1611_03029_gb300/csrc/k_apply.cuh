@@ -15,6 +15,9 @@
 // the upper neighbour's share in a face buffer that k_dg_face_add_t adds.
 #pragma once
 
+#include <cstdlib>
+
+#include "bulk_copy.cuh"
 #include "dev_tables.cuh"
 
 namespace mfp {
@@ -46,6 +49,7 @@ struct ApplyArgs {
   int cpb;     // cells per block
   int ncols;   // columns per block
   Epi<T> epi;  // SIPG: update fused into k_dg_face_add_t
+  int* err;    // set to 1 by a staged kernel whose copy wait timed out
 };
 
 template <int P>
@@ -332,6 +336,21 @@ __global__ void __launch_bounds__(256) k_dg_face_add_t(const ApplyArgs<T> a) {
   }
 }
 
+// Stored geometry staging of the float curved kernel (STAGE): the G block of
+// a group of cells ([cell][6][p^3], contiguous) arrives in shared memory by
+// one bulk copy, double-buffered, so that the copy of the next group runs
+// while the current one is computed.  Bytes of one buffer:
+template <int P, typename T>
+__host__ __device__ constexpr size_t stage_g_bytes(int cpb) {
+  return (size_t)cpb * 6 * P * P * P * sizeof(T);
+}
+// offset of the staging buffers in the dynamic shared memory (16-aligned)
+template <int P, typename T, bool DG>
+__host__ __device__ constexpr size_t stage_offset(int cpb, int ncols) {
+  return (((size_t)(cpb * ncols + 1) * cell_smem_elems<T, P, DG>() +
+           table_smem_elems<P>()) * sizeof(T) + 15) / 16 * 16;
+}
+
 // Work decomposition: a block owns `cpb` cells and `ncols` right-hand-side
 // columns; each (cell, column) pair is a virtual cell worked on by p*p
 // threads (thread = one line of each sweep).  The block is padded to whole
@@ -339,12 +358,18 @@ __global__ void __launch_bounds__(256) k_dg_face_add_t(const ApplyArgs<T> a) {
 // global memory.  Columns of one cell are adjacent threads, so batched
 // vectors [N][R] are read coalesced and the geometry of a cell is loaded
 // once per point for all its columns (same address across the warp).
-template <int P, typename T, bool DG, bool CURVED>
+// STAGE (float, curved, one column): the cells' stored geometry is staged
+// through shared memory by bulk copies (see stage_g_bytes) instead of
+// per-thread loads; a block's successive cell groups alternate between two
+// buffers, each completed on its own mbarrier.
+template <int P, typename T, bool DG, bool CURVED, bool STAGE = false>
 __global__ void k_apply(const ApplyArgs<T> a) {
   constexpr int P2 = P * P, P3 = P2 * P;
   // float geometry is prefetched into registers during the gather (the float
-  // apply is latency-bound); float64 is bound by the FP64 pipe instead
-  constexpr bool PREFETCH = CURVED && sizeof(T) == 4 && P <= 7;
+  // apply is latency-bound) unless it is staged; float64 is bound by the
+  // FP64 pipe instead
+  constexpr bool PREFETCH = !STAGE && CURVED && sizeof(T) == 4 && P <= 7;
+  static_assert(!STAGE || CURVED, "staging is for stored geometry");
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const int cpb = a.cpb, nc = a.ncols;
@@ -369,13 +394,48 @@ __global__ void k_apply(const ApplyArgs<T> a) {
   T* s0 = tabs + 3 * P2;
   T* s1 = s0 + P;
   T* sw = s1 + P;
+  T* gbuf = nullptr;
+  uint64_t* bars = nullptr;
+  const int gstep = gridDim.x * cpb;
+  // thread 0 copies the stored geometry of the group at cell c0 into buffer
+  // slot; the last group's copy is rounded up to 16 bytes (the geometry
+  // array is allocated with one spare cell)
+  auto issue = [&](int c0, int slot) {
+    const int cnt = a.ncells - c0 < cpb ? a.ncells - c0 : cpb;
+    const uint32_t bytes =
+        (uint32_t)((stage_g_bytes<P, T>(cnt) + 15) / 16 * 16);
+    fence_proxy_async_smem();
+    bulk_load(gbuf + (size_t)slot * cpb * 6 * P3,
+              a.G + (size_t)c0 * 6 * P3, bytes, &bars[slot]);
+  };
+  if constexpr (STAGE) {
+    const size_t off = stage_offset<P, T, DG>(cpb, nc);
+    gbuf = reinterpret_cast<T*>(smraw + off);
+    bars = reinterpret_cast<uint64_t*>(smraw + off +
+                                       2 * stage_g_bytes<P, T>(cpb));
+    if (tid == 0) {
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      mbar_init_fence();
+    }
+  }
   load_tables_shared<T, P>(sS, sD, sDphi, s0, s1, sw);
   __syncthreads();
+  if constexpr (STAGE) {
+    if (tid == 0 && blockIdx.x * cpb < a.ncells) issue(blockIdx.x * cpb, 0);
+  }
   const int gx0 = a.g[0], gy0 = a.g[1];
   const int col = a.col + rr;
 
+  int it = 0;
   for (int cbase = blockIdx.x * cpb; cbase < a.ncells;
-       cbase += gridDim.x * cpb) {
+       cbase += gstep, ++it) {
+    if constexpr (STAGE) {
+      // the other buffer was last read by the previous group, which ended
+      // with a barrier
+      if (tid == 0 && cbase + gstep < a.ncells)
+        issue(cbase + gstep, (it + 1) & 1);
+    }
     const int cell = cbase + lc;
     const bool active = item_ok && cell < a.ncells;
     const int cc = active ? cell : 0;
@@ -448,6 +508,11 @@ __global__ void k_apply(const ApplyArgs<T> a) {
     __syncthreads();
     // ---- quadrature-point operation t = G_q grad u (Eq. 12)
     {
+      const T* Gs = nullptr;
+      if constexpr (STAGE) {
+        mbar_wait(&bars[it & 1], (uint32_t)((it >> 1) & 1), a.err);
+        Gs = gbuf + ((size_t)(it & 1) * cpb + lc) * 6 * P3;
+      }
       const T wab = sw[ta] * sw[tb];
 #pragma unroll
       for (int qz = 0; qz < P; ++qz) {
@@ -457,7 +522,10 @@ __global__ void k_apply(const ApplyArgs<T> a) {
         T tx, ty, tz;
         if constexpr (CURVED) {
           T g0, g1, g2, g3, g4, g5;
-          if constexpr (PREFETCH) {
+          if constexpr (STAGE) {
+            g0 = Gs[q]; g1 = Gs[P3 + q]; g2 = Gs[2 * P3 + q];
+            g3 = Gs[3 * P3 + q]; g4 = Gs[4 * P3 + q]; g5 = Gs[5 * P3 + q];
+          } else if constexpr (PREFETCH) {
             g0 = gp[0][qz]; g1 = gp[1][qz]; g2 = gp[2][qz];
             g3 = gp[3][qz]; g4 = gp[4][qz]; g5 = gp[5][qz];
           } else {
@@ -561,6 +629,16 @@ __global__ void k_apply(const ApplyArgs<T> a) {
   }
 }
 
+// Bulk-copy staging of the float curved geometry (on unless the environment
+// variable MFP_STAGE is 0).
+inline bool stage_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("MFP_STAGE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 // Cells per block for one column: the block (padded to whole warps) keeps
 // at least 97 % of its lanes busy: p^2 * cpb close to 128 or 256.
 inline int default_cpb(int p) {
@@ -576,21 +654,24 @@ inline int default_cpb(int p) {
   }
 }
 
-template <int P, typename T, bool DG>
+template <int P, typename T, bool DG, bool STAGE = false>
 size_t apply_smem_bytes(int cpb, int ncols) {
+  if constexpr (STAGE)
+    return stage_offset<P, T, DG>(cpb, ncols) + 2 * stage_g_bytes<P, T>(cpb) +
+           2 * sizeof(uint64_t);
   return ((size_t)(cpb * ncols + 1) * cell_smem_elems<T, P, DG>() +
           table_smem_elems<P>()) *
          sizeof(T);
 }
 
 // Resident blocks per SM of a launch shape (cached per shape).
-template <int P, typename T, bool DG, bool CURVED>
+template <int P, typename T, bool DG, bool CURVED, bool STAGE = false>
 int apply_blocks_per_sm(int cpb, int ncols) {
   static std::mutex mu;
   static int cache[64][4] = {};
   constexpr int P2 = P * P;
   const int threads = ((cpb * ncols * P2 + 31) / 32) * 32;
-  const size_t smem = apply_smem_bytes<P, T, DG>(cpb, ncols);
+  const size_t smem = apply_smem_bytes<P, T, DG, STAGE>(cpb, ncols);
   const bool cacheable = ncols == 1 && cpb < 64;
   int dev = 0;
   MFP_CHECK_CUDA(cudaGetDevice(&dev));
@@ -598,7 +679,7 @@ int apply_blocks_per_sm(int cpb, int ncols) {
     std::lock_guard<std::mutex> lk(mu);
     if (cacheable && dev < 4 && cache[cpb][dev]) return cache[cpb][dev];
   }
-  auto kern = k_apply<P, T, DG, CURVED>;
+  auto kern = k_apply<P, T, DG, CURVED, STAGE>;
   if (smem > 48 * 1024)
     MFP_CHECK_CUDA(cudaFuncSetAttribute(
         kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -612,15 +693,15 @@ int apply_blocks_per_sm(int cpb, int ncols) {
   return per_sm;
 }
 
-template <int P, typename T, bool DG, bool CURVED>
+template <int P, typename T, bool DG, bool CURVED, bool STAGE = false>
 void run_apply(ApplyArgs<T> a, int cpb, int ncols, cudaStream_t s) {
   constexpr int P2 = P * P;
   a.cpb = cpb;
   a.ncols = ncols;
   const int threads = ((cpb * ncols * P2 + 31) / 32) * 32;
-  const size_t smem = apply_smem_bytes<P, T, DG>(cpb, ncols);
-  auto kern = k_apply<P, T, DG, CURVED>;
-  const int per_sm = apply_blocks_per_sm<P, T, DG, CURVED>(cpb, ncols);
+  const size_t smem = apply_smem_bytes<P, T, DG, STAGE>(cpb, ncols);
+  auto kern = k_apply<P, T, DG, CURVED, STAGE>;
+  const int per_sm = apply_blocks_per_sm<P, T, DG, CURVED, STAGE>(cpb, ncols);
   if (smem > 48 * 1024)
     MFP_CHECK_CUDA(cudaFuncSetAttribute(
         kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -655,7 +736,15 @@ void run_apply_cols(const ApplyArgs<T>& a0, int R, int cells_req,
     while (cells > 1 && cells * nc * P2 > maxthr) --cells;
     ApplyArgs<T> a = a0;
     a.col = c0;
-    run_apply<P, T, DG, CURVED>(a, cells, nc, s);
+    // float curved geometry staged by bulk copies when a group's block of
+    // it starts on a 16-byte boundary (one column, even cells per block or
+    // an even p^3)
+    constexpr bool can_stage = CURVED && sizeof(T) == 4;
+    if (can_stage && nc == 1 && ((P % 2 == 0) || cells % 2 == 0) &&
+        stage_enabled())
+      run_apply<P, T, DG, CURVED, can_stage>(a, cells, nc, s);
+    else
+      run_apply<P, T, DG, CURVED>(a, cells, nc, s);
   }
   if constexpr (DG) {
     MFP_REQUIRE(a0.fb, "SIPG face buffer missing");
@@ -705,6 +794,7 @@ ApplyArgs<T> make_apply_args(const Level& L, const LevelData<T>& D,
   a.col = 0;
   a.cpb = 1;
   a.ncols = 1;
+  a.err = L.err;
   return a;
 }
 

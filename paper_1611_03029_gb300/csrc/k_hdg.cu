@@ -1,5 +1,5 @@
 // HDG mixed matrix-free operator (Sec. 3, "HDG mixed matrix-free", on the
-// hybridizable DG form of Sec. 2.3) on Cartesian cells:
+// hybridizable DG form of Sec. 2.3):
 //   y = ([A B^T; B D] + [C^T; G^T] H^{-1} [C G]) x
 // with the cell unknowns (q_x, q_y, q_z, u) in cell-major blocks of 4 p^3
 // nodal values (Lagrange in the Gauss-Lobatto points), where
@@ -8,13 +8,17 @@
 // The trace is never an unknown: H^{-1} [C G] x is the face trace
 //   lambda = sum_sides (q . n + tau u) / sum_sides tau
 // at the face Gauss points (H is tau times the face mass in a basis as large
-// as the Gauss rule, so its inverse acts point by point); it is zero on
-// Dirichlet faces, whose traces are data.  k_hdg_trace (one block per face)
-// forms lambda, k_hdg_cell (one block per cell) adds the cell integrals by
-// sum factorization (values at the Gauss points by S, derivatives by the
-// Gauss collocation matrix D) and the six faces' terms
+// as the Gauss rule, so its inverse acts point by point; on a curved face
+// both sides see the same area element); it is zero on Dirichlet faces,
+// whose traces are data.  k_hdg_trace (one block per face) forms lambda,
+// k_hdg_cell (one block per cell) adds the cell integrals by sum
+// factorization (values at the Gauss points by S, reference derivatives by
+// the Gauss collocation matrix D, mapped by J^{-1}) and the six faces' terms
 // -<v, tau u> + <w . n, lambda> + <v, tau lambda> on the face-layer nodes.
-// Plain float64 arithmetic.
+// tau = tau_factor times the largest coefficient on the face (Sec. 5).
+// Cartesian cells use their constant Jacobian; curved ones read w det J and
+// J^{-1} per cell point and dA and the unit normal per face point.  Plain
+// float64 arithmetic.
 #include "dev_tables.cuh"
 
 namespace mfp {
@@ -27,10 +31,23 @@ struct HdgArgs {
   int n[3];
   int face_off[3];
   int neumann;  // bit 2d + s: side (d, s) has Neumann data
-  double h[3];  // physical cell size
-  double kinv;  // 1 / kappa
-  double tau;
+  double h[3];  // physical cell size (Cartesian cells)
+  double kappa;  // constant coefficient (when kcell / kface are null)
+  double tau_factor;
+  const double* __restrict__ kcell;  // [cell][p^3] or null
+  const double* __restrict__ kface;  // [face][p^2] or null
+  const double* __restrict__ gc;     // curved: [cell][10][p^3] or null
+  const double* __restrict__ gf;     // curved: [face][4][p^2] or null
 };
+
+// tau of face f: tau_factor times the largest coefficient on the face
+template <int P>
+__device__ __forceinline__ double face_tau(const HdgArgs& a, size_t f) {
+  if (!a.kface) return a.tau_factor * a.kappa;
+  double m = a.kface[f * P * P];
+  for (int q = 1; q < P * P; ++q) m = fmax(m, a.kface[f * P * P + q]);
+  return a.tau_factor * m;
+}
 
 // out = M (or M^T) applied along `axis` of nf fields of p^3 values
 template <int P>
@@ -76,12 +93,16 @@ __device__ __forceinline__ int layer_node(int D, int s, int ja, int jb) {
   return ii[0] + P * (ii[1] + P * ii[2]);
 }
 
-// One block per face of direction D: lambda at the face Gauss points.
+
+// One block per face of direction D: lambda at the face Gauss points,
+//   lambda = sum_sides (q . n_out + tau u) / (tau * number of sides),
+// n_out the side's outward unit normal (+n for the cell below the face, -n
+// for the one above; n = e_D on Cartesian cells).
 template <int P>
 __global__ void k_hdg_trace(HdgArgs a, int D) {
   constexpr int F = P * P, N = P * P * P;
   __shared__ double sS[P * P];
-  __shared__ double lay[4 * F], tmp[4 * F];  // [side][field q_D, u][F]
+  __shared__ double lay[8 * F], tmp[8 * F];  // [side][q_x, q_y, q_z, u][F]
   int m[3] = {a.n[0], a.n[1], a.n[2]};
   m[D] += 1;
   const int fl = blockIdx.x;
@@ -99,39 +120,75 @@ __global__ void k_hdg_trace(HdgArgs a, int D) {
   const int cellR = hasR ? fc[0] + a.n[0] * (fc[1] + a.n[1] * fc[2]) : 0;
   for (int i = threadIdx.x; i < P * P; i += blockDim.x)
     sS[i] = c_tab64[P - 2].S[i];
-  for (int t = threadIdx.x; t < 2 * F; t += blockDim.x) {
-    const int s = t / F, j = t % F;  // s = 0: lower cell, 1: upper cell
+  for (int t = threadIdx.x; t < 8 * F; t += blockDim.x) {
+    const int sf = t / F, j = t % F;  // side 0: lower cell, 1: upper cell
+    const int s = sf / 4, fld = sf % 4;
     const bool has = s == 0 ? hasL : hasR;
     const int loc = layer_node<P>(D, s == 0 ? 1 : 0, j % P, j / P);
     const double* xc = a.x + (size_t)(s == 0 ? cellL : cellR) * 4 * N;
-    lay[(2 * s) * F + j] = has ? xc[D * N + loc] : 0.0;      // q_D
-    lay[(2 * s + 1) * F + j] = has ? xc[3 * N + loc] : 0.0;  // u
+    lay[t] = has ? xc[fld * N + loc] : 0.0;
   }
   __syncthreads();
-  sweep2<P>(sS, false, 0, lay, tmp, 4);
+  sweep2<P>(sS, false, 0, lay, tmp, 8);
   __syncthreads();
-  sweep2<P>(sS, false, 1, tmp, lay, 4);
+  sweep2<P>(sS, false, 1, tmp, lay, 8);
   __syncthreads();
+  const double tau = face_tau<P>(a, f);
   for (int q = threadIdx.x; q < F; q += blockDim.x) {
-    double num = 0, den = 0;
-    if (hasL) {  // outward normal +e_D
-      num += lay[q] + a.tau * lay[F + q];
-      den += a.tau;
+    double nv[3] = {0.0, 0.0, 0.0};
+    if (a.gf) {
+      for (int e = 0; e < 3; ++e) nv[e] = a.gf[(f * 4 + 1 + e) * F + q];
+    } else {
+      nv[D] = 1.0;
     }
-    if (hasR) {  // outward normal -e_D
-      num += -lay[2 * F + q] + a.tau * lay[3 * F + q];
-      den += a.tau;
+    double num = 0, den = 0;
+    for (int s = 0; s < 2; ++s) {
+      if (!(s == 0 ? hasL : hasR)) continue;
+      const double* L = lay + 4 * s * F;
+      const double qn = nv[0] * L[q] + nv[1] * L[F + q] + nv[2] * L[2 * F + q];
+      num += (s == 0 ? qn : -qn) + tau * L[3 * F + q];
+      den += tau;
     }
     a.lam[f * F + q] = num / den;
   }
 }
 
-// One block per cell: cell integrals and the terms of its six faces.
+template <int P>
+constexpr size_t hdg_cell_smem() {
+  return (size_t)(8 * P * P * P + 10 * P * P) * sizeof(double);
+}
+
+// Geometry of cell point t: w det J and J^{-1}[e][d] (row e, column d).
+template <int P>
+__device__ __forceinline__ void point_geo(const HdgArgs& a, int cell, int t,
+                                          const double* sw, double& wdet,
+                                          double (&Ji)[3][3]) {
+  constexpr int N = P * P * P;
+  if (a.gc) {
+    const double* g = a.gc + (size_t)cell * 10 * N + t;
+    wdet = g[0];
+    for (int e = 0; e < 3; ++e)
+      for (int d = 0; d < 3; ++d) Ji[e][d] = g[(1 + 3 * e + d) * N];
+  } else {
+    wdet = sw[t % P] * sw[(t / P) % P] * sw[t / (P * P)] * a.h[0] * a.h[1] *
+           a.h[2];
+    for (int e = 0; e < 3; ++e)
+      for (int d = 0; d < 3; ++d) Ji[e][d] = e == d ? 1.0 / a.h[d] : 0.0;
+  }
+}
+
+// One block per cell: cell integrals and the terms of its six faces.  At the
+// Gauss points (w det = w_q det J, J^{-1} = dxi/dx):
+//   q_d rows: w det kappa^-1 q_d - sum_e D_e^T (w det J^{-1}[e][d] u)
+//   u rows:   -w det sum_{d,e} J^{-1}[e][d] D_e q_d
 template <int P>
 __global__ void k_hdg_cell(HdgArgs a) {
   constexpr int F = P * P, N = P * P * P;
   __shared__ double sS[P * P], sD[P * P], sw[P];
-  __shared__ double A[4 * N], B[4 * N];
+  extern __shared__ __align__(16) double hsm[];
+  double* A = hsm;
+  double* B = hsm + 4 * N;
+  double* FS = hsm + 8 * N;
   const int cell = blockIdx.x;
   const int c3[3] = {cell % a.n[0], (cell / a.n[0]) % a.n[1],
                      cell / (a.n[0] * a.n[1])};
@@ -150,42 +207,62 @@ __global__ void k_hdg_cell(HdgArgs a) {
   __syncthreads();
   sweep3<P>(sS, false, 2, A, B, 4);
   __syncthreads();
-  // integrands at the Gauss points (w det = w_x w_y w_z h_x h_y h_z):
-  //   q_d rows: w det kappa^-1 q_d - (1/h_d) D^T_d (w det u)
-  //   u rows:   -w det sum_d (1/h_d) D_d q_d
-  const double vol = a.h[0] * a.h[1] * a.h[2];
+  const int st[3] = {1, P, P * P};
+  // u rows and the mass part of the q rows
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     const int ii[3] = {t % P, (t / P) % P, t / (P * P)};
-    const int st[3] = {1, P, P * P};
-    const double wq = sw[ii[0]] * sw[ii[1]] * sw[ii[2]] * vol;
+    double wdet, Ji[3][3];
+    point_geo<P>(a, cell, t, sw, wdet, Ji);
+    const double kinv =
+        1.0 / (a.kcell ? a.kcell[(size_t)cell * N + t] : a.kappa);
     double dv = 0;
     for (int d = 0; d < 3; ++d) {
-      const int base = t - ii[d] * st[d];
-      double s1 = 0, s2 = 0;
-      for (int j = 0; j < P; ++j) {
-        const int tj = base + j * st[d];
-        const int jj[3] = {tj % P, (tj / P) % P, tj / (P * P)};
-        const double wj = sw[jj[0]] * sw[jj[1]] * sw[jj[2]] * vol;
-        s1 += sD[ii[d] * P + j] * B[d * N + tj];
-        s2 += sD[j * P + ii[d]] * wj * B[3 * N + tj];
+      for (int e = 0; e < 3; ++e) {
+        if (!a.gc && e != d) continue;
+        const int base = t - ii[e] * st[e];
+        double s1 = 0;
+        for (int j = 0; j < P; ++j)
+          s1 += sD[ii[e] * P + j] * B[d * N + base + j * st[e]];
+        dv += Ji[e][d] * s1;
       }
-      dv += s1 / a.h[d];
-      A[d * N + t] = wq * a.kinv * B[d * N + t] - s2 / a.h[d];
+      A[d * N + t] = wdet * kinv * B[d * N + t];
     }
-    A[3 * N + t] = -wq * dv;
+    A[3 * N + t] = -wdet * dv;
   }
   __syncthreads();
+  // -sum_e D_e^T (w det J^{-1}[e][d] u) into the q_d rows, one d at a time
+  // (the q values at the points in B are no longer needed)
+  for (int d = 0; d < 3; ++d) {
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+      double wdet, Ji[3][3];
+      point_geo<P>(a, cell, t, sw, wdet, Ji);
+      for (int e = 0; e < 3; ++e) B[e * N + t] = wdet * Ji[e][d] * B[3 * N + t];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+      const int ii[3] = {t % P, (t / P) % P, t / (P * P)};
+      double s2 = 0;
+      for (int e = 0; e < 3; ++e) {
+        if (!a.gc && e != d) continue;
+        const int base = t - ii[e] * st[e];
+        for (int j = 0; j < P; ++j)
+          s2 += sD[j * P + ii[e]] * B[e * N + base + j * st[e]];
+      }
+      A[d * N + t] -= s2;
+    }
+    __syncthreads();
+  }
   sweep3<P>(sS, true, 2, A, B, 4);
   __syncthreads();
   sweep3<P>(sS, true, 1, B, A, 4);
   __syncthreads();
   sweep3<P>(sS, true, 0, A, B, 4);
   __syncthreads();
-  // faces: scratch in A (5 p^2 values)
-  double* ul = A;          // u layer, then u at the face points
-  double* ut = A + F;      // sweep temporary
-  double* gc = A + F;      // [cq, cu] at the face points (after ut is free)
-  double* gt = A + 3 * F;  // sweep temporary for the two fields
+  // faces: scratch FS (10 p^2 values)
+  double* ul = FS;           // u layer, then u at the face points
+  double* ut = FS + F;       // sweep temporary
+  double* gcf = FS + 2 * F;  // [w_x, w_y, w_z, v] terms at the face points
+  double* gt = FS + 6 * F;   // sweep temporary for the four fields
   for (int D = 0; D < 3; ++D) {
     const int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
     int m[3] = {a.n[0], a.n[1], a.n[2]};
@@ -202,22 +279,30 @@ __global__ void k_hdg_cell(HdgArgs a) {
       __syncthreads();
       sweep2<P>(sS, false, 1, ut, ul, 1);
       __syncthreads();
-      const double nD = s ? 1.0 : -1.0;
+      const double tau = face_tau<P>(a, f);
+      const double so = s ? 1.0 : -1.0;  // outward: +n on the upper face
       for (int q = threadIdx.x; q < F; q += blockDim.x) {
-        const double dA = sw[q % P] * sw[q / P] * a.h[T1] * a.h[T2];
+        double dA, nv[3] = {0.0, 0.0, 0.0};
+        if (a.gf) {
+          dA = a.gf[(f * 4) * F + q];
+          for (int e = 0; e < 3; ++e) nv[e] = a.gf[(f * 4 + 1 + e) * F + q];
+        } else {
+          dA = sw[q % P] * sw[q / P] * a.h[T1] * a.h[T2];
+          nv[D] = 1.0;
+        }
         const double lq = a.lam[f * F + q];
-        gc[q] = dA * nD * lq;                       // <w . n, lambda>
-        gc[F + q] = dA * a.tau * (lq - ul[q]);      // <v, tau (lambda - u)>
+        for (int e = 0; e < 3; ++e)
+          gcf[e * F + q] = dA * so * nv[e] * lq;       // <w . n, lambda>
+        gcf[3 * F + q] = dA * tau * (lq - ul[q]);      // <v, tau (lambda - u)>
       }
       __syncthreads();
-      sweep2<P>(sS, true, 1, gc, gt, 2);
+      sweep2<P>(sS, true, 1, gcf, gt, 4);
       __syncthreads();
-      sweep2<P>(sS, true, 0, gt, gc, 2);
+      sweep2<P>(sS, true, 0, gt, gcf, 4);
       __syncthreads();
       for (int j = threadIdx.x; j < F; j += blockDim.x) {
         const int loc = layer_node<P>(D, s, j % P, j / P);
-        B[D * N + loc] += gc[j];
-        B[3 * N + loc] += gc[F + j];
+        for (int e = 0; e < 4; ++e) B[e * N + loc] += gcf[e * F + j];
       }
       __syncthreads();
     }
@@ -228,7 +313,8 @@ __global__ void k_hdg_cell(HdgArgs a) {
 
 }  // namespace
 
-void launch_hdg_apply(const Level& L, double tau, double* lam,
+void launch_hdg_apply(const Level& L, double tau_factor, double* lam,
+                      const double* hdg_cell, const double* hdg_face,
                       const double* x, double* y, cudaStream_t s) {
   ensure_tables();
   HdgArgs a{};
@@ -241,8 +327,12 @@ void launch_hdg_apply(const Level& L, double tau, double* lam,
     a.h[d] = L.h[d];
   }
   a.neumann = L.bc.neumann;
-  a.kinv = 1.0 / L.kappa;
-  a.tau = tau;
+  a.kappa = L.kappa;
+  a.tau_factor = tau_factor;
+  a.kcell = L.d64.kcell;
+  a.kface = L.d64.kface;
+  a.gc = hdg_cell;
+  a.gf = hdg_face;
   dispatch_p(L.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;
     for (int D = 0; D < 3; ++D) {
@@ -252,7 +342,12 @@ void launch_hdg_apply(const Level& L, double tau, double* lam,
       MFP_CHECK_CUDA(cudaGetLastError());
       note_launch();
     }
-    k_hdg_cell<P><<<(int)L.ncells, 128, 0, s>>>(a);
+    constexpr size_t smem = hdg_cell_smem<P>();
+    if (smem > 48 * 1024)
+      MFP_CHECK_CUDA(cudaFuncSetAttribute(
+          k_hdg_cell<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          (int)smem));
+    k_hdg_cell<P><<<(int)L.ncells, 128, smem, s>>>(a);
     MFP_CHECK_CUDA(cudaGetLastError());
     note_launch();
   });

@@ -139,7 +139,7 @@ __device__ double block_sum(double v, double* red) {
 // ---------------------------------------------------------------------------
 template <int P>
 __global__ void k_cell_geometry(GeoArgs g, double* G, float* G32,
-                                double* vol, int* bad) {
+                                double* vol, int* bad, double* hdg) {
   constexpr int P3 = P * P * P;
   __shared__ ShTab<P> t;
   __shared__ double X[3 * P3];
@@ -178,6 +178,12 @@ __global__ void k_cell_geometry(GeoArgs g, double* G, float* G32,
       G[((size_t)cell * 6 + c2) * P3 + q] = Gm[c2];
       if (G32) G32[((size_t)cell * 6 + c2) * P3 + q] = (float)Gm[c2];
     }
+    if (hdg) {  // HDG mixed operator: w det J and J^{-1} [e][d] per point
+      double* o = hdg + (size_t)cell * 10 * P3 + q;
+      o[0] = w;
+      for (int e = 0; e < 3; ++e)
+        for (int d = 0; d < 3; ++d) o[(1 + 3 * e + d) * P3] = I[e][d];
+    }
   }
   const double sum = block_sum(wdet, red);
   if (threadIdx.x == 0) vol[cell] = sum;
@@ -193,7 +199,7 @@ template <int P>
 __global__ void k_face_geometry(GeoArgs g, int D, int face_off,
                                 double penalty, const double* vol,
                                 double* fdata, float* fdata32, double* sigma,
-                                float* sigma32) {
+                                float* sigma32, double* hdg) {
   constexpr int P2 = P * P, P3 = P2 * P;
   __shared__ ShTab<P> t;
   __shared__ double XL[3 * P3], XR[3 * P3];
@@ -250,6 +256,10 @@ __global__ void k_face_geometry(GeoArgs g, int D, int face_off,
     for (int c = 0; c < 7; ++c) {
       fdata[(f * 7 + c) * P2 + q] = out[c];
       if (fdata32) fdata32[(f * 7 + c) * P2 + q] = (float)out[c];
+    }
+    if (hdg) {  // HDG: area element and the unit normal along +e_D
+      hdg[(f * 4 + 0) * P2 + q] = dA;
+      for (int e = 0; e < 3; ++e) hdg[(f * 4 + 1 + e) * P2 + q] = n[e];
     }
   }
   const double A = block_sum(area, red);
@@ -849,7 +859,8 @@ GeoArgs geo_args(const Level& L) {
 
 }  // namespace
 
-void launch_curved_cell_geometry(Level& L, cudaStream_t s) {
+void launch_curved_cell_geometry(Level& L, cudaStream_t s,
+                                 double* hdg_cell) {
   ensure_tables();
   int* bad = nullptr;
   MFP_CHECK_CUDA(cudaMallocAsync(&bad, sizeof(int), s));
@@ -859,7 +870,7 @@ void launch_curved_cell_geometry(Level& L, cudaStream_t s) {
     constexpr int P = decltype(pc)::value;
     const int thr = P * P * P < 256 ? ((P * P * P + 31) / 32) * 32 : 256;
     k_cell_geometry<P><<<(int)L.ncells, thr, 0, s>>>(g, L.d64.G, L.d32.G,
-                                                      L.vol, bad);
+                                                      L.vol, bad, hdg_cell);
   });
   MFP_CHECK_CUDA(cudaGetLastError());
   note_launch();
@@ -884,7 +895,8 @@ void launch_coarsen_nodes(const Level& fine, Level& coarse, cudaStream_t s) {
   note_launch();
 }
 
-void launch_curved_face_geometry(Level& L, cudaStream_t s) {
+void launch_curved_face_geometry(Level& L, cudaStream_t s,
+                                 double* hdg_face) {
   ensure_tables();
   GeoArgs g = geo_args(L);
   for (int D = 0; D < 3; ++D) {
@@ -896,7 +908,7 @@ void launch_curved_face_geometry(Level& L, cudaStream_t s) {
       const int thr = ((P * P + 31) / 32) * 32;
       k_face_geometry<P><<<nf, thr, 0, s>>>(
           g, D, L.face_off[D], L.penalty, L.vol, L.d64.fdata, L.d32.fdata,
-          L.d64.sigma, L.d32.sigma);
+          L.d64.sigma, L.d32.sigma, hdg_face);
     });
     MFP_CHECK_CUDA(cudaGetLastError());
   note_launch();

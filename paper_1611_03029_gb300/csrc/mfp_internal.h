@@ -225,6 +225,7 @@ struct Level {
   double penalty = 1.0;
   double map_amp = 0.0;
   double* nodes = nullptr;    // given support points [ncells][p^3][3]
+  int* err = nullptr;         // the context's kernel error word (device)
   double* vol = nullptr;      // curved: cell volumes [ncells]
   LevelData<double> d64;
   LevelData<float> d32;
@@ -284,12 +285,15 @@ struct mfp_ctx {
   double* params = nullptr; // device copy of forcing parameters
   int params_cap = 0;
   double* hdg_lam = nullptr;    // HDG traces at the face points [nfaces][p^2]
+  double* hdg_cell = nullptr;   // curved HDG: [cell][10][p^3] (w det J, J^-1)
+  double* hdg_face = nullptr;   // curved HDG: [face][4][p^2] (dA, normal)
   mfp::RedScratch red;
   double* host_scal = nullptr;  // pinned [S_COUNT][kMaxRhs]
   float* mix_r = nullptr;       // float V-cycle input / output on the finest
   float* mix_z = nullptr;
   int cg_rhs = 0;
   int64_t vcycles = 0;
+  int* dev_err = nullptr;       // kernel error word: 1 = a copy wait timed out
   // V-cycles of mfp_solve captured as CUDA graphs, one per column count;
   // replays add the captured counter increments
   struct VGraph {
@@ -339,10 +343,15 @@ bool apply_dg_df_hi(const Level& L, const double* src, double* dst, int nrhs,
 void launch_split(const double* a, float* hi, float* lo, int64_t n,
                   cudaStream_t s);
 
-void launch_curved_cell_geometry(Level& L, cudaStream_t s);
+// curved geometry; hdg_cell / hdg_face (may be null) also receive the HDG
+// mixed operator's data: [cell][10][p^3] (w det J, J^{-1}[e][d]) and
+// [face][4][p^2] (dA, unit normal along +e_D)
+void launch_curved_cell_geometry(Level& L, cudaStream_t s,
+                                 double* hdg_cell = nullptr);
 // support points of `coarse` from the isoparametric map of `fine`
 void launch_coarsen_nodes(const Level& fine, Level& coarse, cudaStream_t s);
-void launch_curved_face_geometry(Level& L, cudaStream_t s);
+void launch_curved_face_geometry(Level& L, cudaStream_t s,
+                                 double* hdg_face = nullptr);
 void launch_diagonal(const Level& L, double* diag, cudaStream_t s);
 void launch_rhs(const Level& L, int kind, const double* params_dev,
                 int nterms, double* b, int64_t stride, cudaStream_t s);
@@ -358,6 +367,7 @@ void launch_gradient(const Level& L, const double* u, const double* lam,
                      double* gc, double* gf, cudaStream_t s);
 // HDG mixed operator on Cartesian cells (k_hdg.cu); lam: [nfaces][p^2]
 void launch_hdg_apply(const Level& L, double tau, double* lam,
+                      const double* hdg_cell, const double* hdg_face,
                       const double* x, double* y, cudaStream_t s);
 
 template <typename T>

@@ -14,7 +14,8 @@ the contexts' set-up:
   SIPG context: one gradient (k_grad_cells, k_grad_faces);
   SIPG context on Cartesian cells: one HDG mixed apply (k_hdg_trace per
                 face direction, k_hdg_cell).
-Prints one JSON line with the wall time of each step.
+Each step runs inside the NVTX range "profile".  Prints one JSON line with
+the wall time of each step.
 """
 import argparse
 import json
@@ -43,9 +44,13 @@ def main(argv=None):
     out = {}
 
     def step(name, fn):
+        # each step inside the NVTX range "profile" (ncu --nvtx-include), so
+        # that a capture skips the contexts' set-up launches
         t0 = time.time()
+        torch.cuda.nvtx.range_push("profile")
         fn()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         out[name] = time.time() - t0
 
     top = cg.n_levels - 1

@@ -52,10 +52,53 @@ def test_hdg_apply_full_size_sampled_cells(mfp):
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("k,n,sides,mapping", [
+    (1, (3, 2, 2), (), "sine"),
+    (2, (2, 3, 2), (0, 2, 4), "sine"),
+    (3, (2, 2, 3), (1,), "nodes"),
+    (4, (2, 2, 2), (0, 3), "sine"),
+    (5, (2, 1, 2), (), "nodes")])
+def test_hdg_apply_curved_variable_coefficient(mfp, k, n, sides, mapping):
+    # curved cells (w det J and J^{-1} per point, dA and the normal per face
+    # point) with a per-point coefficient a = exp(g) on cells and faces (tau
+    # from the largest face value)
+    kw = {}
+    if mapping == "nodes":
+        kw["map_nodes"] = synthetic.perturbed_lattice_nodes(n, k, seed=9)
+    else:
+        kw["amp"] = 0.1
+    a_c, a_f = synthetic.log_coefficient(n, k + 1, seed=7)
+    op = mfp.Poisson(*n, k, disc="dg", n_levels=1, neumann_sides=sides,
+                     mapping=mapping, map_param=kw.get("amp", 0.0),
+                     map_nodes=kw.get("map_nodes"))
+    op.set_coefficient(torch.from_numpy(a_c).cuda(),
+                       torch.from_numpy(a_f).cuda())
+    P = fem.Problem(*n, k, disc="dg", neumann_sides=sides, mapping=mapping,
+                    a_cell=a_c, a_face=a_f, **kw)
+    A = hdg.mixed_operator(P)
+    x = synthetic.random_vector(A.shape[0], seed=70 + k)
+    y = op.hdg_apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel_err(y, A @ x) <= 1e-12
+
+
+def test_hdg_apply_curved_full_size_sampled_cells(mfp):
+    # 32^3 cells Q4 on the curved map: sampled cells' rows by the oracle
+    n, k = 32, 4
+    op = mfp.Poisson(n, n, n, k, disc="dg", n_levels=1, mapping="sine",
+                     map_param=0.1)
+    P = fem.Problem(n, n, n, k, disc="dg", mapping="sine", amp=0.1)
+    x = synthetic.random_vector(4 * op.n_dofs(), seed=82)
+    y = op.hdg_apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    rng = np.random.default_rng(7)
+    cells = np.concatenate([[0, n - 1, P.ncells - 1],
+                            rng.choice(P.ncells, 9, replace=False)])
+    ref = hdg.mixed_apply_cells(P, x, cells)
+    got = y.reshape(P.ncells, -1)[cells]
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 def test_hdg_apply_rejects_unsupported(mfp):
     x = torch.zeros(4 * 8 * 8, dtype=torch.float64, device="cuda")
-    for kw in (dict(disc="cg"), dict(disc="dg", mapping="sine",
-                                     map_param=0.1)):
-        op = mfp.Poisson(2, 2, 2, 1, n_levels=1, **kw)
-        with pytest.raises(mfp.MfpError):
-            op.hdg_apply(x)
+    op = mfp.Poisson(2, 2, 2, 1, n_levels=1, disc="cg")
+    with pytest.raises(mfp.MfpError):
+        op.hdg_apply(x)
