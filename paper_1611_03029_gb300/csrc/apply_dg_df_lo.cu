@@ -11,7 +11,11 @@ bool apply_dg_df_lo(const Level& L, const double* src, double* dst,
   ensure_tables();
   ApplyArgsDF a = make_apply_args_df(L, src, dst);
   a.stride = nrhs;
-  if (epi) a.epi = *epi;
+  if (epi) {
+    a.epi = *epi;
+    a.epi_c1 = host_df(epi->c1);
+    a.epi_c2 = host_df(epi->c2);
+  }
   switch (L.p) {
     case 2:
       if (L.curved)

@@ -731,15 +731,18 @@ void run_apply_cols(const ApplyArgs<T>& a0, int R, int cells_req,
   const int maxcols = maxthr / P2 > 0 ? maxthr / P2 : 1;
   for (int c0 = 0; c0 < R; c0 += maxcols) {
     const int nc = R - c0 < maxcols ? R - c0 : maxcols;
+    // float curved geometry staged by bulk copies when a group's block of
+    // it starts on a 16-byte boundary (one column, even cells per block or
+    // an even p^3); the default shape is made even for it
+    constexpr bool can_stage = CURVED && sizeof(T) == 4;
     int cells = cells_req > 0 ? cells_req : default_cpb(P) / nc;
+    if (can_stage && nc == 1 && cells_req <= 0 && P % 2 == 1 &&
+        cells % 2 == 1 && stage_enabled())
+      ++cells;
     if (cells < 1) cells = 1;
     while (cells > 1 && cells * nc * P2 > maxthr) --cells;
     ApplyArgs<T> a = a0;
     a.col = c0;
-    // float curved geometry staged by bulk copies when a group's block of
-    // it starts on a 16-byte boundary (one column, even cells per block or
-    // an even p^3)
-    constexpr bool can_stage = CURVED && sizeof(T) == 4;
     if (can_stage && nc == 1 && ((P % 2 == 0) || cells % 2 == 0) &&
         stage_enabled())
       run_apply<P, T, DG, CURVED, can_stage>(a, cells, nc, s);

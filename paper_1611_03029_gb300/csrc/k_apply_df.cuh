@@ -49,7 +49,33 @@ struct ApplyArgsDF {
   df gs[3], ns[3], fa[3], sg[3];
   int stride, col, cpb, ncols;
   Epi<double> epi;           // SIPG: update fused into k_dg_face_add
+  df epi_c1, epi_c2;         // its coefficients as double-float pairs
 };
+
+// The fused update of Epi in double-float arithmetic on the FP32 pipes: the
+// float64 inputs are split with integer operations and only the float64
+// results take one FP64 addition each (the FP64 pipe, about 1/60 of the
+// FP32 rate on GB300, would otherwise bound the kernel).
+__device__ __forceinline__ void epi_finish_df(const ApplyArgsDF& a, size_t gi,
+                                              size_t dof, df y) {
+  const Epi<double>& e = a.epi;
+  if (e.mode == EPI_STORE) {
+    a.dst[gi] = df_to_double(y);
+    return;
+  }
+  const df r = df_from_double(e.b[gi]) - y;
+  if (e.mode == EPI_RESIDUAL) {
+    a.dst[gi] = df_to_double(r);
+    return;
+  }
+  df v = a.epi_c2 * (df_from_double(e.dinv[dof]) * r);
+  if (e.mode == EPI_CHEB_FIRST)
+    v = a.epi_c1 * (df_from_double(e.dinv[dof]) * r);
+  else
+    v = a.epi_c1 * df_from_double(e.d[gi]) + v;
+  e.d[gi] = df_to_double(v);
+  e.x[gi] = df_to_double(df_from_double(e.x[gi]) + v);
+}
 
 __device__ __forceinline__ df f2df(float2 v) { return df_make(v.x, v.y); }
 __device__ __forceinline__ float2 df2f(df v) { return make_float2(v.h, v.l); }
@@ -882,8 +908,8 @@ __global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
     const size_t dof = cell * P3 + xy;
 #pragma unroll
     for (int z = 0; z < P; ++z)
-      epi_finish(a.epi, a.dst, (dof + (size_t)z * P2) * R + col,
-                 dof + (size_t)z * P2, df_to_double(acc_get(s[z])));
+      epi_finish_df(a, (dof + (size_t)z * P2) * R + col, dof + (size_t)z * P2,
+                    acc_get(s[z]));
   }
 }
 

@@ -457,7 +457,7 @@ __global__ void k_rhs(RhsArgs a, double* b) {
             cz = cell / (g.n[0] * g.n[1]);
   load_shtab<P>(t);
   __syncthreads();
-  const bool curved = g.amp != 0.0;
+  const bool curved = g.amp != 0.0 || g.nodes != nullptr;
   if (curved) support_points<P>(g, t, cx, cy, cz, X);
   __syncthreads();
   for (int q = threadIdx.x; q < P3; q += blockDim.x) {
@@ -529,7 +529,7 @@ __global__ void k_rhs_lift(RhsArgs a, double* b) {
   if (!touch) return;
   load_shtab<P>(t);
   __syncthreads();
-  const bool curved = g.amp != 0.0;
+  const bool curved = g.amp != 0.0 || g.nodes != nullptr;
   if (curved) support_points<P>(g, t, c3[0], c3[1], c3[2], X);
   __syncthreads();
   for (int i = threadIdx.x; i < P3; i += blockDim.x) {
@@ -642,7 +642,7 @@ __global__ void k_rhs_face(RhsArgs a, int side, double* b) {
       a.face_off[D] + fc[0] + (int64_t)m[0] * (fc[1] + (int64_t)m[1] * fc[2]);
   load_shtab<P>(t);
   __syncthreads();
-  const bool curved = g.amp != 0.0;
+  const bool curved = g.amp != 0.0 || g.nodes != nullptr;
   if (curved) support_points<P>(g, t, c3[0], c3[1], c3[2], X);
   __syncthreads();
   const double* dS = s ? t.d1 : t.d0;  // GLL basis slopes at the cell end
