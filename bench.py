@@ -537,7 +537,7 @@ def run_ours(args):
     except Exception as exc:  # reported, never fatal to the contract line
         apply["hdg_f64_cartesian"] = {"error": str(exc)[:200]}
 
-    # --- the paper's smooth example (Sec. 5): three Gaussians on (-1, 1)^3,
+    # --- the paper's smooth example (Sec. 4.3): three Gaussians on (-1, 1)^3,
     # Neumann data on x_e = -1, 32^3 cells Q4 (its 32768-cell row) --------
     paper_cube = {}
     try:

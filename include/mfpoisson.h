@@ -113,7 +113,7 @@ typedef struct {
                             (values 0..62).                                 */
   double box_lo, box_hi; /* domain [box_lo, box_hi]^3: the unit cube mapped
                             by `mapping`, then by x -> box_lo + (box_hi -
-                            box_lo) x (default 0, 1; Sec. 5 uses -1, 1);
+                            box_lo) x (default 0, 1; Sec. 4.3 uses -1, 1);
                             MFP_MAP_NODES needs the default (the nodes are
                             physical points)                                */
   const double* map_nodes; /* MFP_MAP_NODES: HOST array [ncells][(k+1)^3][3]
@@ -178,7 +178,7 @@ mfp_status mfp_set_coefficient(mfp_ctx* ctx, const double* a_cell_dev,
  *  - f_kind 1: f = sum_j A_j exp(-|x - c_j|^2 / w_j^2) with params_host =
  *    n_terms blocks (c_x, c_y, c_z, w, A), homogeneous boundary data.
  *  - f_kind 2: the problem whose exact solution is u = sum_j A_j exp(-|x -
- *    c_j|^2 / w_j^2) (same params; Sec. 5 uses three such terms on
+ *    c_j|^2 / w_j^2) (same params; Sec. 4.3 uses three such terms on
  *    (-1, 1)^3): f = -kappa Laplace u, Dirichlet data u on the Dirichlet
  *    sides and Neumann data kappa grad u . n on the Neumann sides.  CG: a
  *    constrained dof holds u at its node and the free rows have the lifted
@@ -219,7 +219,7 @@ mfp_status mfp_rhs_noalloc(mfp_ctx* ctx, int f_kind, const double* params_host,
  * on the finest cells of an SIPG context (same mesh, box and Neumann sides),
  * with A = (w, kappa^-1 q), B^T = -(div w, u), D = -<v, tau u>,
  * C^T = <w . n, lambda>, G^T = <v, tau lambda>, H = sum <mu, tau lambda> and
- * tau = tau_factor times the largest coefficient value on the face (Sec. 5:
+ * tau = tau_factor times the largest coefficient value on the face (Sec. 4.2:
  * tau_factor 5).  Dirichlet faces hold data traces and add no H^{-1}
  * coupling.  x_dev and y_dev hold the cell unknowns (q_x, q_y, q_z, u) in
  * cell-major blocks of 4 (k+1)^3 nodal values (the SIPG cell layout per

@@ -20,7 +20,7 @@ Modules
            load vector, L2 error, Neumann / inhomogeneous Dirichlet data and
            a direct solve for manufactured solutions (Sec. 2, 2.1, 2.2;
            Eq. 4, 6, 7, 12)
-  cube     the paper's three-Gaussian example on (-1, 1)^3 (Sec. 5), pinned
+  cube     the paper's three-Gaussian example on (-1, 1)^3 (Sec. 4.3), pinned
            against the L2 errors it prints
   mg       Jacobi diagonal, Chebyshev smoother, CG-Lanczos eigenvalue
            estimate, transfer, coarse Chebyshev solve, V-cycle, PCG (Sec. 4.1)

@@ -1,4 +1,4 @@
-"""The paper's three-dimensional example with a smooth solution (Sec. 5,
+"""The paper's three-dimensional example with a smooth solution (Sec. 4.3,
 "Three-dimensional example with smooth solution"): u is a sum of three
 Gaussians of width alpha = 1/5 on the cube (-1, 1)^3, with Neumann data on
 the sides x_e = -1 and Dirichlet data on the sides x_e = +1, kappa = 1.

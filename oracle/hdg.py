@@ -2,7 +2,7 @@
 -div(kappa grad u) = f (Sec. 2.3, Eq. hdg and its matrix form): the flux
 q = -kappa grad u and u in the discontinuous Q_k space of each cell, the
 trace lambda in Q_k of each face, the numerical flux
-q^ . n = q . n + tau (u - lambda), tau = 5 max kappa on the face (Sec. 5).
+q^ . n = q . n + tau (u - lambda), tau = 5 max kappa on the face (Sec. 4.2).
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Written from the paper's
 weak form, not from the CUDA library.  Used to pin the HDG blocks against
@@ -73,7 +73,7 @@ def face_sides(prob):
 
 
 def tau_faces(prob):
-    """tau = TAU_FACTOR max kappa over the points of each face (Sec. 5)."""
+    """tau = TAU_FACTOR max kappa over the points of each face (Sec. 4.2)."""
     return TAU_FACTOR * prob.kappa_face(np.arange(prob.n_faces)).max(1)
 
 

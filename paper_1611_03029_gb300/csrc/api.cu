@@ -760,6 +760,7 @@ mfp_status mfp_create(const mfp_desc* desc, void* stream, mfp_ctx** out) {
         L.bc.hi[e] = (d.neumann_sides >> (2 * e + 1)) & 1 ? -1 : L.gdim[e] - 1;
       }
       L.bc.neumann = d.neumann_sides;
+      L.df_arith = d.fp64_arith == MFP_ARITH_DF;
       L.ndofs = d.disc == MFP_CG ? (int64_t)L.gdim[0] * L.gdim[1] * L.gdim[2]
                                  : L.ncells * L.p * L.p * L.p;
       int64_t off = 0;

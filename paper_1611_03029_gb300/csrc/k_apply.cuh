@@ -323,15 +323,26 @@ __global__ void __launch_bounds__(256) k_dg_face_add_t(const ApplyArgs<T> a) {
     const T gz = fb[(size_t)(5 * P2 + xy) * R];
     const T vz = fb[(size_t)(4 * P2 + xy) * R];
     const T wx = tv<T, P, T_DPHI0>(x), wy = tv<T, P, T_DPHI0>(y);
+    // the fused update's inputs, loaded with the rest
     const size_t dof = cell * P3 + xy;
+    const int mode = a.epi.mode;
+    T eb[P], edi[P], ed[P], ex[P];
+#pragma unroll
+    for (int z = 0; z < P; ++z) {
+      const size_t gi = (dof + (size_t)z * P2) * R + col;
+      eb[z] = mode != EPI_STORE ? a.epi.b[gi] : T(0);
+      edi[z] = mode >= EPI_CHEB_FIRST ? a.epi.dinv[dof + (size_t)z * P2] : T(0);
+      ex[z] = mode >= EPI_CHEB_FIRST ? a.epi.x[gi] : T(0);
+      ed[z] = mode == EPI_CHEB_STEP ? a.epi.d[gi] : T(0);
+    }
 #pragma unroll
     for (int z = 0; z < P; ++z) {
       T s = u[z];
       if (cx > 0) s += fma(wx, gx[z], vx[z]);
       if (cy > 0) s += fma(wy, gy[z], vy[z]);
       if (cz > 0) s += fma(tv<T, P, T_DPHI0>(z), gz, z == 0 ? vz : T(0));
-      epi_finish(a.epi, a.dst, (dof + (size_t)z * P2) * R + col,
-                 dof + (size_t)z * P2, s);
+      epi_finish(a.epi, a.dst, (dof + (size_t)z * P2) * R + col, s, eb[z],
+                 edi[z], ed[z], ex[z]);
     }
   }
 }

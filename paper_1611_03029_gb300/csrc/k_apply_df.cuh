@@ -53,28 +53,28 @@ struct ApplyArgsDF {
 };
 
 // The fused update of Epi in double-float arithmetic on the FP32 pipes: the
-// float64 inputs are split with integer operations and only the float64
-// results take one FP64 addition each (the FP64 pipe, about 1/60 of the
-// FP32 rate on GB300, would otherwise bound the kernel).
+// float64 inputs (loaded by the caller ahead of its arithmetic: b, dinv, d,
+// x as the mode needs them) are split with integer operations and only the
+// float64 results take one FP64 addition each.
 __device__ __forceinline__ void epi_finish_df(const ApplyArgsDF& a, size_t gi,
-                                              size_t dof, df y) {
+                                              df y, double b, double dinv,
+                                              double d, double x) {
   const Epi<double>& e = a.epi;
   if (e.mode == EPI_STORE) {
     a.dst[gi] = df_to_double(y);
     return;
   }
-  const df r = df_from_double(e.b[gi]) - y;
+  const df r = df_from_double(b) - y;
   if (e.mode == EPI_RESIDUAL) {
     a.dst[gi] = df_to_double(r);
     return;
   }
-  df v = a.epi_c2 * (df_from_double(e.dinv[dof]) * r);
-  if (e.mode == EPI_CHEB_FIRST)
-    v = a.epi_c1 * (df_from_double(e.dinv[dof]) * r);
-  else
-    v = a.epi_c1 * df_from_double(e.d[gi]) + v;
+  const df dr = df_from_double(dinv) * r;
+  const df v = e.mode == EPI_CHEB_FIRST
+                   ? a.epi_c1 * dr
+                   : a.epi_c1 * df_from_double(d) + a.epi_c2 * dr;
   e.d[gi] = df_to_double(v);
-  e.x[gi] = df_to_double(df_from_double(e.x[gi]) + v);
+  e.x[gi] = df_to_double(df_from_double(x) + v);
 }
 
 __device__ __forceinline__ df f2df(float2 v) { return df_make(v.x, v.y); }
@@ -883,6 +883,19 @@ __global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
     }
     const float2 gz = fb[(size_t)(5 * P2 + xy) * R];
     const float2 vz = fb[(size_t)(4 * P2 + xy) * R];
+    // the fused update's inputs, loaded with the rest (no store comes
+    // before them, so they are all in flight together)
+    const size_t dof = cell * P3 + xy;
+    const int mode = a.epi.mode;
+    double eb[P], edi[P], ed[P], ex[P];
+#pragma unroll
+    for (int z = 0; z < P; ++z) {
+      const size_t gi = (dof + (size_t)z * P2) * R + col;
+      eb[z] = mode != EPI_STORE ? a.epi.b[gi] : 0.0;
+      edi[z] = mode >= EPI_CHEB_FIRST ? a.epi.dinv[dof + (size_t)z * P2] : 0.0;
+      ex[z] = mode >= EPI_CHEB_FIRST ? a.epi.x[gi] : 0.0;
+      ed[z] = mode == EPI_CHEB_STEP ? a.epi.d[gi] : 0.0;
+    }
     // lower faces inside the mesh: the slope part on every layer along the
     // face normal (weight dphi_l(0)), the value part on layer 0
     const float wxh = d0h[x], wxl = d0l[x], wyh = d0h[y], wyl = d0l[y];
@@ -905,11 +918,10 @@ __global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
         if (z == 0) acc_add(s[z], df_make(vz.x, vz.y));
       }
     }
-    const size_t dof = cell * P3 + xy;
 #pragma unroll
     for (int z = 0; z < P; ++z)
-      epi_finish_df(a, (dof + (size_t)z * P2) * R + col, dof + (size_t)z * P2,
-                    acc_get(s[z]));
+      epi_finish_df(a, (dof + (size_t)z * P2) * R + col, acc_get(s[z]), eb[z],
+                    edi[z], ed[z], ex[z]);
   }
 }
 

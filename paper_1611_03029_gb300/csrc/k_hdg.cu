@@ -15,7 +15,7 @@
 // factorization (values at the Gauss points by S, reference derivatives by
 // the Gauss collocation matrix D, mapped by J^{-1}) and the six faces' terms
 // -<v, tau u> + <w . n, lambda> + <v, tau lambda> on the face-layer nodes.
-// tau = tau_factor times the largest coefficient on the face (Sec. 5).
+// tau = tau_factor times the largest coefficient on the face (Sec. 4.2).
 // Cartesian cells use their constant Jacobian; curved ones read w det J and
 // J^{-1} per cell point and dA and the unit normal per face point.  Plain
 // float64 arithmetic.

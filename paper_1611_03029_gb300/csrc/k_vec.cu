@@ -2,6 +2,7 @@
 // transfer by the tensorial geometric embedding, fused CG updates with
 // deterministic two-stage reductions finished on the device, and the
 // bisection for the extreme eigenvalues of the Lanczos tridiagonal.
+#include "df.cuh"
 #include "dev_tables.cuh"
 
 namespace mfp {
@@ -122,34 +123,81 @@ __device__ __forceinline__ T emb(int o, int r, int j) {
     return o ? c_tab32[P - 2].E1[r * P + j] : c_tab32[P - 2].E0[r * P + j];
 }
 
-template <typename T, int P>
-__device__ void load_embedding(T* E, int dg) {
+// Arithmetic of the transfer sweeps: plain T, or (DF, float64 vectors of a
+// double-float context) pairs of floats in shared memory accumulated with
+// TwoSum / FMA TwoProd on the FP32 pipes; on GB300 the FP64 pipe would bound
+// these sweeps (p multiply-adds per output) well below the memory rate.
+template <typename T, bool DF>
+struct XArith {
+  using S = T;  // shared-memory element
+  struct Acc {
+    T v;
+  };
+  static __device__ __forceinline__ S load(T x) { return x; }
+  static __device__ __forceinline__ Acc zero() { return Acc{T(0)}; }
+  static __device__ __forceinline__ void mac(Acc& a, S e, S u) { a.v += e * u; }
+  static __device__ __forceinline__ S get(const Acc& a) { return a.v; }
+  static __device__ __forceinline__ T out(const Acc& a) { return a.v; }
+};
+template <>
+struct XArith<double, true> {
+  using S = float2;
+  struct Acc {
+    dacc d;
+  };
+  static __device__ __forceinline__ S load(double x) {
+    const df v = df_from_double(x);
+    return make_float2(v.h, v.l);
+  }
+  static __device__ __forceinline__ Acc zero() {
+    Acc a;
+    a.d.h = 0.f;
+    a.d.l = 0.f;
+    return a;
+  }
+  static __device__ __forceinline__ void mac(Acc& a, S e, S u) {
+    acc_mac(a.d, e.x, e.y, u.x, u.y);
+  }
+  static __device__ __forceinline__ S get(const Acc& a) {
+    const df v = acc_get(a.d);
+    return make_float2(v.h, v.l);
+  }
+  static __device__ __forceinline__ double out(const Acc& a) {
+    return df_to_double(acc_get(a.d));
+  }
+};
+
+template <typename T, int P, bool DF>
+__device__ void load_embedding(typename XArith<T, DF>::S* E, int dg) {
+  using A = XArith<T, DF>;
   constexpr int K = P - 1;
   const int M = dg ? 2 * P : 2 * K + 1;
   for (int i = threadIdx.x; i < M * P; i += blockDim.x) {
     const int r = i / P, j = i % P;
     if (dg)
-      E[i] = r < P ? emb<T, P>(0, r, j) : emb<T, P>(1, r - P, j);
+      E[i] = A::load(r < P ? emb<T, P>(0, r, j) : emb<T, P>(1, r - P, j));
     else
-      E[i] = r <= K ? emb<T, P>(0, r, j) : emb<T, P>(1, r - K, j);
+      E[i] = A::load(r <= K ? emb<T, P>(0, r, j) : emb<T, P>(1, r - K, j));
   }
 }
 
-template <typename T, int P>
+template <typename T, int P, bool DF>
 __global__ void k_prolongate(XferArgs a, const T* __restrict__ xc,
                              T* __restrict__ xf) {
+  using A = XArith<T, DF>;
+  using S = typename A::S;
   constexpr int K = P - 1;
   const int M = a.dg ? 2 * P : 2 * K + 1;
   extern __shared__ __align__(16) unsigned char xsm[];
-  T* E = reinterpret_cast<T*>(xsm);
-  T* u = E + M * P;
-  T* t1 = u + P * P * P;
-  T* t2 = t1 + P * P * M;
+  S* E = reinterpret_cast<S*>(xsm);
+  S* u = E + M * P;
+  S* t1 = u + P * P * P;
+  S* t2 = t1 + P * P * M;
   const int C = blockIdx.x;
   a.col = blockIdx.y;  // one column of the batch per grid row
   const int cx = C % a.nc[0], cy = (C / a.nc[0]) % a.nc[1],
             cz = C / (a.nc[0] * a.nc[1]);
-  load_embedding<T, P>(E, a.dg);
+  load_embedding<T, P, DF>(E, a.dg);
   for (int i = threadIdx.x; i < P * P * P; i += blockDim.x) {
     const int ix = i % P, iy = (i / P) % P, iz = i / (P * P);
     T v;
@@ -163,27 +211,30 @@ __global__ void k_prolongate(XferArgs a, const T* __restrict__ xc,
                        a.stride +
                    a.col];
     }
-    u[i] = v;
+    u[i] = A::load(v);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < P * P * M; i += blockDim.x) {  // x
     const int fx = i % M, r = i / M;                            // r = iy + P iz
-    T s = T(0);
-    for (int j = 0; j < P; ++j) s += E[fx * P + j] * u[r * P + j];
-    t1[r * M + fx] = s;
+    auto s = A::zero();
+    for (int j = 0; j < P; ++j) A::mac(s, E[fx * P + j], u[r * P + j]);
+    t1[r * M + fx] = A::get(s);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < P * M * M; i += blockDim.x) {  // y
     const int fx = i % M, fy = (i / M) % M, iz = i / (M * M);
-    T s = T(0);
-    for (int j = 0; j < P; ++j) s += E[fy * P + j] * t1[(iz * P + j) * M + fx];
-    t2[i] = s;
+    auto s = A::zero();
+    for (int j = 0; j < P; ++j)
+      A::mac(s, E[fy * P + j], t1[(iz * P + j) * M + fx]);
+    t2[i] = A::get(s);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < M * M * M; i += blockDim.x) {  // z
     const int fx = i % M, fy = (i / M) % M, fz = i / (M * M);
-    T s = T(0);
-    for (int j = 0; j < P; ++j) s += E[fz * P + j] * t2[(j * M + fy) * M + fx];
+    auto acc = A::zero();
+    for (int j = 0; j < P; ++j)
+      A::mac(acc, E[fz * P + j], t2[(j * M + fy) * M + fx]);
+    const T s = A::out(acc);
     if (a.dg) {
       const int ox = fx / P, oy = fy / P, oz = fz / P;
       const int F = (2 * cx + ox) + a.nf[0] * ((2 * cy + oy) + a.nf[1] * (2 * cz + oz));
@@ -202,21 +253,23 @@ __global__ void k_prolongate(XferArgs a, const T* __restrict__ xc,
   }
 }
 
-template <typename T, int P>
+template <typename T, int P, bool DF>
 __global__ void k_restrict(XferArgs a, const T* __restrict__ xf,
                            T* __restrict__ xc) {
+  using A = XArith<T, DF>;
+  using S = typename A::S;
   constexpr int K = P - 1;
   const int M = a.dg ? 2 * P : 2 * K + 1;
   extern __shared__ __align__(16) unsigned char xsm[];
-  T* E = reinterpret_cast<T*>(xsm);
-  T* u = E + M * P;
-  T* t1 = u + M * M * M;
-  T* t2 = t1 + M * M * P;
+  S* E = reinterpret_cast<S*>(xsm);
+  S* u = E + M * P;
+  S* t1 = u + M * M * M;
+  S* t2 = t1 + M * M * P;
   const int C = blockIdx.x;
   a.col = blockIdx.y;  // one column of the batch per grid row
   const int cx = C % a.nc[0], cy = (C / a.nc[0]) % a.nc[1],
             cz = C / (a.nc[0] * a.nc[1]);
-  load_embedding<T, P>(E, a.dg);
+  load_embedding<T, P, DF>(E, a.dg);
   for (int i = threadIdx.x; i < M * M * M; i += blockDim.x) {
     const int fx = i % M, fy = (i / M) % M, fz = i / (M * M);
     T v;
@@ -237,27 +290,30 @@ __global__ void k_restrict(XferArgs a, const T* __restrict__ xf,
                        a.stride +
                    a.col];
     }
-    u[i] = v;
+    u[i] = A::load(v);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < M * M * P; i += blockDim.x) {  // x
     const int ix = i % P, r = i / P;                            // r = fy + M fz
-    T s = T(0);
-    for (int f = 0; f < M; ++f) s += E[f * P + ix] * u[r * M + f];
-    t1[i] = s;
+    auto s = A::zero();
+    for (int f = 0; f < M; ++f) A::mac(s, E[f * P + ix], u[r * M + f]);
+    t1[i] = A::get(s);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < M * P * P; i += blockDim.x) {  // y
     const int ix = i % P, iy = (i / P) % P, fz = i / (P * P);
-    T s = T(0);
-    for (int f = 0; f < M; ++f) s += E[f * P + iy] * t1[(f + M * fz) * P + ix];
-    t2[i] = s;
+    auto s = A::zero();
+    for (int f = 0; f < M; ++f)
+      A::mac(s, E[f * P + iy], t1[(f + M * fz) * P + ix]);
+    t2[i] = A::get(s);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < P * P * P; i += blockDim.x) {  // z
     const int ix = i % P, iy = (i / P) % P, iz = i / (P * P);
-    T s = T(0);
-    for (int f = 0; f < M; ++f) s += E[f * P + iz] * t2[(f * P + iy) * P + ix];
+    auto acc = A::zero();
+    for (int f = 0; f < M; ++f)
+      A::mac(acc, E[f * P + iz], t2[(f * P + iy) * P + ix]);
+    const T s = A::out(acc);
     if (a.dg) {
       xc[((size_t)C * P * P * P + i) * a.stride + a.col] = s;
     } else {
@@ -593,7 +649,9 @@ void launch_prolongate(const Level& fine, const Level& coarse, const T* xc,
     const int M = a.dg ? 2 * P : 2 * P - 1;
     const size_t smem = (size_t)(M * P + P * P * P + P * P * M + P * M * M) *
                         sizeof(T);
-    auto kern = k_prolongate<T, P>;
+    auto kern = std::is_same<T, double>::value && fine.df_arith
+                    ? k_prolongate<T, P, std::is_same<T, double>::value>
+                    : k_prolongate<T, P, false>;
     if (smem > 48 * 1024)
       MFP_CHECK_CUDA(cudaFuncSetAttribute(
           kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -615,7 +673,9 @@ void launch_restrict(const Level& fine, const Level& coarse, const T* xf,
     const int M = a.dg ? 2 * P : 2 * P - 1;
     const size_t smem = (size_t)(M * P + M * M * M + M * M * P + M * P * P) *
                         sizeof(T);
-    auto kern = k_restrict<T, P>;
+    auto kern = std::is_same<T, double>::value && fine.df_arith
+                    ? k_restrict<T, P, std::is_same<T, double>::value>
+                    : k_restrict<T, P, false>;
     if (smem > 48 * 1024)
       MFP_CHECK_CUDA(cudaFuncSetAttribute(
           kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -155,24 +155,26 @@ struct Epi {
   double c1, c2;
 };
 
-// Applies the update of `e` to the finished value y of entry gi (dof `dof`).
+// Applies the update of `e` to the finished value y of entry gi, given the
+// inputs b, dinv, d, x of that entry (loaded by the caller as the mode needs
+// them, ahead of its arithmetic).
 template <typename T, typename Y>
 __device__ __forceinline__ void epi_finish(const Epi<T>& e, T* dst, size_t gi,
-                                           size_t dof, Y y) {
+                                           Y y, T b, T dinv, T d, T x) {
   if (e.mode == EPI_STORE) {
     dst[gi] = (T)y;
     return;
   }
-  const Y r = (Y)e.b[gi] - y;
+  const Y r = (Y)b - y;
   if (e.mode == EPI_RESIDUAL) {
     dst[gi] = (T)r;
     return;
   }
-  const Y dr = (Y)e.c2 * ((Y)e.dinv[dof] * r);
-  const Y v = e.mode == EPI_CHEB_FIRST ? (Y)e.c1 * ((Y)e.dinv[dof] * r)
-                                       : (Y)e.c1 * (Y)e.d[gi] + dr;
+  const Y dr = (Y)e.c2 * ((Y)dinv * r);
+  const Y v = e.mode == EPI_CHEB_FIRST ? (Y)e.c1 * ((Y)dinv * r)
+                                       : (Y)e.c1 * (Y)d + dr;
   e.d[gi] = (T)v;
-  e.x[gi] = (T)((Y)e.x[gi] + v);
+  e.x[gi] = (T)((Y)x + v);
 }
 
 struct Bc {
@@ -226,6 +228,7 @@ struct Level {
   double map_amp = 0.0;
   double* nodes = nullptr;    // given support points [ncells][p^3][3]
   int* err = nullptr;         // the context's kernel error word (device)
+  bool df_arith = false;      // float64 applies in double-float arithmetic
   double* vol = nullptr;      // curved: cell volumes [ncells]
   LevelData<double> d64;
   LevelData<float> d32;

@@ -115,7 +115,7 @@ def log_coefficient(n, p, seed):
 
 
 def strong_coefficient_field(x):
-    """The strongly varying diffusivity of the paper's shell example (Sec. 5),
+    """The strongly varying diffusivity of the paper's shell example (Sec. 4.3),
     1 + 10^6 prod_e cos(2 pi x_e + 0.1 e) for e = 1, 2, 3, read with the
     product in absolute value: as printed it is negative on about half of any
     domain, which no SPD solver accepts; the absolute value keeps its

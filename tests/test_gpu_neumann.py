@@ -1,6 +1,6 @@
 """Neumann sides, the box domain and the boundary-data right-hand side
 (f_kind 2) against the oracle, and the paper's smooth three-dimensional
-example (Sec. 5: three Gaussians on (-1, 1)^3, Neumann data on x_e = -1,
+example (Sec. 4.3: three Gaussians on (-1, 1)^3, Neumann data on x_e = -1,
 Dirichlet data on x_e = +1) solved on the GPU against the L2 errors the
 paper prints.
 

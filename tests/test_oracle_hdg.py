@@ -101,7 +101,7 @@ def _sine_grad(x):
 
 
 def test_hdg_converges_at_k_plus_1_and_post_at_k_plus_2():
-    # optimal rates (Sec. 5: k+1 for u_h, k+2 after post-processing), Q2 on
+    # optimal rates (Sec. 4.3: k+1 for u_h, k+2 after post-processing), Q2 on
     # 2^3 and 4^3 affine cells
     errs, post = [], []
     for n in (2, 4):

@@ -1,5 +1,5 @@
 """Pins of the oracle against values the paper prints: the L2 errors of its
-three-dimensional example with a smooth solution (Sec. 5; three Gaussians on
+three-dimensional example with a smooth solution (Sec. 4.3; three Gaussians on
 (-1, 1)^3 with Neumann data on x_e = -1 and Dirichlet data on x_e = +1).
 
 These check the oracle's cell integrals under the isoparametric map, the
