@@ -15,8 +15,6 @@
 // the upper neighbour's share in a face buffer that k_dg_face_add_t adds.
 #pragma once
 
-#include <cstdlib>
-
 #include "bulk_copy.cuh"
 #include "dev_tables.cuh"
 
@@ -294,56 +292,39 @@ __device__ __noinline__ void face_lower_gp(const ApplyArgs<T>& a, int col,
 
 // Adds the terms that the cell below each interior face left for the cell
 // above it (face buffer slots 2D: value part on the face layer, 2D + 1:
-// normal-slope part on every layer with the weight dphi_l(0)); one thread
-// per node line along z of a row of cells (blockIdx.y: cy, cz; blockIdx.z:
-// column).
+// normal-slope part on every layer with the weight dphi_l(0)) and applies the
+// fused update; one thread per node (cell, x, y, z) of column blockIdx.y.
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_dg_face_add_t(const ApplyArgs<T> a) {
   constexpr int P2 = P * P, P3 = P2 * P;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n[0] * P2) return;
-  const int R = a.stride, col = blockIdx.z;
-  const int cx = i / P2, xy = i - cx * P2;
-  const int x = xy % P, y = xy / P;
-  const int rows = a.n[1] * a.n[2];
-  for (int row = blockIdx.y; row < rows; row += gridDim.y) {
-    const int cy = row % a.n[1], cz = row / a.n[1];
-    const size_t cell = (size_t)row * a.n[0] + cx;
+  const int R = a.stride, col = blockIdx.y;
+  const size_t total = (size_t)a.ncells * P3;
+  const int mode = a.epi.mode;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t cell = i / P3;
+    const int loc = (int)(i - cell * P3);
+    const int x = loc % P, y = (loc / P) % P, z = loc / P2;
+    const int cx = (int)(cell % a.n[0]), cy = (int)((cell / a.n[0]) % a.n[1]),
+              cz = (int)(cell / ((size_t)a.n[0] * a.n[1]));
     const T* fb = a.fb + cell * 6 * P2 * R + col;
-    T* out = a.dst + (cell * P3 + xy) * R + col;
-    T u[P], gx[P], vx[P], gy[P], vy[P];
-#pragma unroll
-    for (int z = 0; z < P; ++z) {
-      u[z] = out[(size_t)z * P2 * R];
-      gx[z] = fb[(size_t)(1 * P2 + y + P * z) * R];
-      vx[z] = x == 0 ? fb[(size_t)(0 * P2 + y + P * z) * R] : T(0);
-      gy[z] = fb[(size_t)(3 * P2 + x + P * z) * R];
-      vy[z] = y == 0 ? fb[(size_t)(2 * P2 + x + P * z) * R] : T(0);
-    }
-    const T gz = fb[(size_t)(5 * P2 + xy) * R];
-    const T vz = fb[(size_t)(4 * P2 + xy) * R];
-    const T wx = tv<T, P, T_DPHI0>(x), wy = tv<T, P, T_DPHI0>(y);
-    // the fused update's inputs, loaded with the rest
-    const size_t dof = cell * P3 + xy;
-    const int mode = a.epi.mode;
-    T eb[P], edi[P], ed[P], ex[P];
-#pragma unroll
-    for (int z = 0; z < P; ++z) {
-      const size_t gi = (dof + (size_t)z * P2) * R + col;
-      eb[z] = mode != EPI_STORE ? a.epi.b[gi] : T(0);
-      edi[z] = mode >= EPI_CHEB_FIRST ? a.epi.dinv[dof + (size_t)z * P2] : T(0);
-      ex[z] = mode >= EPI_CHEB_FIRST ? a.epi.x[gi] : T(0);
-      ed[z] = mode == EPI_CHEB_STEP ? a.epi.d[gi] : T(0);
-    }
-#pragma unroll
-    for (int z = 0; z < P; ++z) {
-      T s = u[z];
-      if (cx > 0) s += fma(wx, gx[z], vx[z]);
-      if (cy > 0) s += fma(wy, gy[z], vy[z]);
-      if (cz > 0) s += fma(tv<T, P, T_DPHI0>(z), gz, z == 0 ? vz : T(0));
-      epi_finish(a.epi, a.dst, (dof + (size_t)z * P2) * R + col, s, eb[z],
-                 edi[z], ed[z], ex[z]);
-    }
+    const size_t gi = i * R + col;
+    const T u = a.dst[gi];
+    const T gx = cx > 0 ? fb[(size_t)(1 * P2 + y + P * z) * R] : T(0);
+    const T vx = cx > 0 && x == 0 ? fb[(size_t)(0 * P2 + y + P * z) * R] : T(0);
+    const T gy = cy > 0 ? fb[(size_t)(3 * P2 + x + P * z) * R] : T(0);
+    const T vy = cy > 0 && y == 0 ? fb[(size_t)(2 * P2 + x + P * z) * R] : T(0);
+    const T gz = cz > 0 ? fb[(size_t)(5 * P2 + x + P * y) * R] : T(0);
+    const T vz = cz > 0 && z == 0 ? fb[(size_t)(4 * P2 + x + P * y) * R] : T(0);
+    const T eb = mode != EPI_STORE ? a.epi.b[gi] : T(0);
+    const T edi = mode >= EPI_CHEB_FIRST ? a.epi.dinv[i] : T(0);
+    const T ex = mode >= EPI_CHEB_FIRST ? a.epi.x[gi] : T(0);
+    const T ed = mode == EPI_CHEB_STEP ? a.epi.d[gi] : T(0);
+    T s = u;
+    if (cx > 0) s += fma(tv<T, P, T_DPHI0>(x), gx, vx);
+    if (cy > 0) s += fma(tv<T, P, T_DPHI0>(y), gy, vy);
+    if (cz > 0) s += fma(tv<T, P, T_DPHI0>(z), gz, vz);
+    epi_finish(a.epi, a.dst, gi, s, eb, edi, ed, ex);
   }
 }
 
@@ -640,16 +621,6 @@ __global__ void k_apply(const ApplyArgs<T> a) {
   }
 }
 
-// Bulk-copy staging of the float curved geometry (on unless the environment
-// variable MFP_STAGE is 0).
-inline bool stage_enabled() {
-  static const bool on = [] {
-    const char* e = std::getenv("MFP_STAGE");
-    return !(e && e[0] == '0');
-  }();
-  return on;
-}
-
 // Cells per block for one column: the block (padded to whole warps) keeps
 // at least 97 % of its lanes busy: p^2 * cpb close to 128 or 256.
 inline int default_cpb(int p) {
@@ -742,20 +713,18 @@ void run_apply_cols(const ApplyArgs<T>& a0, int R, int cells_req,
   const int maxcols = maxthr / P2 > 0 ? maxthr / P2 : 1;
   for (int c0 = 0; c0 < R; c0 += maxcols) {
     const int nc = R - c0 < maxcols ? R - c0 : maxcols;
-    // float curved geometry staged by bulk copies when a group's block of
-    // it starts on a 16-byte boundary (one column, even cells per block or
-    // an even p^3); the default shape is made even for it
+    // float curved geometry staged by bulk copies (one column, an even
+    // number of cells per block, so that every group's block of it starts on
+    // a 16-byte boundary); the autotuner's choice of cells per block decides
+    // between the variants (at 32^3 Q4 the default, odd shape with the
+    // register prefetch measured 7 % faster)
     constexpr bool can_stage = CURVED && sizeof(T) == 4;
     int cells = cells_req > 0 ? cells_req : default_cpb(P) / nc;
-    if (can_stage && nc == 1 && cells_req <= 0 && P % 2 == 1 &&
-        cells % 2 == 1 && stage_enabled())
-      ++cells;
     if (cells < 1) cells = 1;
     while (cells > 1 && cells * nc * P2 > maxthr) --cells;
     ApplyArgs<T> a = a0;
     a.col = c0;
-    if (can_stage && nc == 1 && ((P % 2 == 0) || cells % 2 == 0) &&
-        stage_enabled())
+    if (can_stage && nc == 1 && cells % 2 == 0)
       run_apply<P, T, DG, CURVED, can_stage>(a, cells, nc, s);
     else
       run_apply<P, T, DG, CURVED>(a, cells, nc, s);
@@ -763,11 +732,11 @@ void run_apply_cols(const ApplyArgs<T>& a0, int R, int cells_req,
   if constexpr (DG) {
     MFP_REQUIRE(a0.fb, "SIPG face buffer missing");
     const int threads = 256;
-    const int bx = (a0.n[0] * P2 + threads - 1) / threads;
-    const int rows = a0.n[1] * a0.n[2];
-    const int by = rows < 65535 ? rows : 65535;
+    const int64_t total = (int64_t)a0.ncells * P2 * P;
+    const int64_t want = (total + threads - 1) / threads;
+    const int bx = (int)(want < (1 << 30) ? want : (1 << 30));
     if (a0.ncells > 0) {
-      k_dg_face_add_t<P, T><<<dim3(bx, by, R), threads, 0, s>>>(a0);
+      k_dg_face_add_t<P, T><<<dim3(bx, R), threads, 0, s>>>(a0);
       MFP_CHECK_CUDA(cudaGetLastError());
       note_launch();
     }

@@ -853,75 +853,58 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
 template <int P>
 __global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
   constexpr int P2 = P * P, P3 = P2 * P;
-  // one thread per node line along z (cell cx, x, y) of the row of cells
-  // (cy, cz) = blockIdx.y; blockIdx.z is the column of a batch
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n[0] * P2) return;
-  const int R = a.stride, col = blockIdx.z;
-  const int cx = i / P2, xy = i - cx * P2;
-  const int x = xy % P, y = xy / P;
+  // one thread per node (cell, x, y, z) of column blockIdx.y; the face
+  // buffer slots of a cell are read by its p^3 threads (cached)
+  const int R = a.stride, col = blockIdx.y;
   const float* d0h = c_tabdf[P - 2].d0h;
   const float* d0l = c_tabdf[P - 2].d0l;
-  const int rows = a.n[1] * a.n[2];
-  for (int row = blockIdx.y; row < rows; row += gridDim.y) {
-    const int cy = row % a.n[1], cz = row / a.n[1];
-    const size_t cell = (size_t)row * a.n[0] + cx;
+  const size_t total = (size_t)a.ncells * P3;
+  const int mode = a.epi.mode;
+  const float2 f0 = make_float2(0.f, 0.f);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t cell = i / P3;
+    const int loc = (int)(i - cell * P3);
+    const int x = loc % P, y = (loc / P) % P, z = loc / P2;
+    const int cx = (int)(cell % a.n[0]), cy = (int)((cell / a.n[0]) % a.n[1]),
+              cz = (int)(cell / ((size_t)a.n[0] * a.n[1]));
     const float2* fb = a.fb + cell * 6 * P2 * R + col;
-    double* out = a.dst + (cell * P3 + xy) * R + col;
-    // every load first (one memory round trip); slots of boundary faces
-    // are read but not used
-    const float2 f0 = make_float2(0.f, 0.f);
-    double u[P];
-    float2 gx[P], vx[P], gy[P], vy[P];
-#pragma unroll
-    for (int z = 0; z < P; ++z) {
-      u[z] = out[(size_t)z * P2 * R];
-      gx[z] = fb[(size_t)(1 * P2 + y + P * z) * R];
-      vx[z] = x == 0 ? fb[(size_t)(0 * P2 + y + P * z) * R] : f0;
-      gy[z] = fb[(size_t)(3 * P2 + x + P * z) * R];
-      vy[z] = y == 0 ? fb[(size_t)(2 * P2 + x + P * z) * R] : f0;
+    const size_t gi = i * R + col;
+    // every load first: the cell-kernel result, the face-buffer terms of the
+    // lower faces inside the mesh, the fused update's inputs
+    const double u = a.dst[gi];
+    const float2 gx = cx > 0 ? fb[(size_t)(1 * P2 + y + P * z) * R] : f0;
+    const float2 vx =
+        cx > 0 && x == 0 ? fb[(size_t)(0 * P2 + y + P * z) * R] : f0;
+    const float2 gy = cy > 0 ? fb[(size_t)(3 * P2 + x + P * z) * R] : f0;
+    const float2 vy =
+        cy > 0 && y == 0 ? fb[(size_t)(2 * P2 + x + P * z) * R] : f0;
+    const float2 gz = cz > 0 ? fb[(size_t)(5 * P2 + x + P * y) * R] : f0;
+    const float2 vz =
+        cz > 0 && z == 0 ? fb[(size_t)(4 * P2 + x + P * y) * R] : f0;
+    const double eb = mode != EPI_STORE ? a.epi.b[gi] : 0.0;
+    const double edi = mode >= EPI_CHEB_FIRST ? a.epi.dinv[i] : 0.0;
+    const double ex = mode >= EPI_CHEB_FIRST ? a.epi.x[gi] : 0.0;
+    const double ed = mode == EPI_CHEB_STEP ? a.epi.d[gi] : 0.0;
+    // the slope part on every layer along the face normal (weight dphi_l(0)),
+    // the value part on layer 0
+    const df uz = df_from_double(u);
+    dacc s;
+    s.h = uz.h;
+    s.l = uz.l;
+    if (cx > 0) {
+      acc_mac(s, d0h[x], d0l[x], gx.x, gx.y);
+      if (x == 0) acc_add(s, df_make(vx.x, vx.y));
     }
-    const float2 gz = fb[(size_t)(5 * P2 + xy) * R];
-    const float2 vz = fb[(size_t)(4 * P2 + xy) * R];
-    // the fused update's inputs, loaded with the rest (no store comes
-    // before them, so they are all in flight together)
-    const size_t dof = cell * P3 + xy;
-    const int mode = a.epi.mode;
-    double eb[P], edi[P], ed[P], ex[P];
-#pragma unroll
-    for (int z = 0; z < P; ++z) {
-      const size_t gi = (dof + (size_t)z * P2) * R + col;
-      eb[z] = mode != EPI_STORE ? a.epi.b[gi] : 0.0;
-      edi[z] = mode >= EPI_CHEB_FIRST ? a.epi.dinv[dof + (size_t)z * P2] : 0.0;
-      ex[z] = mode >= EPI_CHEB_FIRST ? a.epi.x[gi] : 0.0;
-      ed[z] = mode == EPI_CHEB_STEP ? a.epi.d[gi] : 0.0;
+    if (cy > 0) {
+      acc_mac(s, d0h[y], d0l[y], gy.x, gy.y);
+      if (y == 0) acc_add(s, df_make(vy.x, vy.y));
     }
-    // lower faces inside the mesh: the slope part on every layer along the
-    // face normal (weight dphi_l(0)), the value part on layer 0
-    const float wxh = d0h[x], wxl = d0l[x], wyh = d0h[y], wyl = d0l[y];
-    dacc s[P];
-#pragma unroll
-    for (int z = 0; z < P; ++z) {
-      const df uz = df_from_double(u[z]);
-      s[z].h = uz.h;
-      s[z].l = uz.l;
-      if (cx > 0) {
-        acc_mac(s[z], wxh, wxl, gx[z].x, gx[z].y);
-        if (x == 0) acc_add(s[z], df_make(vx[z].x, vx[z].y));
-      }
-      if (cy > 0) {
-        acc_mac(s[z], wyh, wyl, gy[z].x, gy[z].y);
-        if (y == 0) acc_add(s[z], df_make(vy[z].x, vy[z].y));
-      }
-      if (cz > 0) {
-        acc_mac(s[z], d0h[z], d0l[z], gz.x, gz.y);
-        if (z == 0) acc_add(s[z], df_make(vz.x, vz.y));
-      }
+    if (cz > 0) {
+      acc_mac(s, d0h[z], d0l[z], gz.x, gz.y);
+      if (z == 0) acc_add(s, df_make(vz.x, vz.y));
     }
-#pragma unroll
-    for (int z = 0; z < P; ++z)
-      epi_finish_df(a, (dof + (size_t)z * P2) * R + col, acc_get(s[z]), eb[z],
-                    edi[z], ed[z], ex[z]);
+    epi_finish_df(a, gi, acc_get(s), eb, edi, ed, ex);
   }
 }
 
@@ -1019,11 +1002,11 @@ void run_apply_df_cols(const ApplyArgsDF& a0, int R, int cells_req,
   if constexpr (DG) {
     MFP_REQUIRE(a0.fb, "SIPG face buffer missing");
     const int threads = 256;
-    const int bx = (a0.n[0] * P2 + threads - 1) / threads;
-    const int rows = a0.n[1] * a0.n[2];
-    const int by = rows < 65535 ? rows : 65535;
+    const int64_t total = (int64_t)a0.ncells * P2 * P;
+    const int64_t want = (total + threads - 1) / threads;
+    const int bx = (int)(want < (1 << 30) ? want : (1 << 30));
     if (a0.ncells > 0) {
-      k_dg_face_add<P><<<dim3(bx, by, R), threads, 0, s>>>(a0);
+      k_dg_face_add<P><<<dim3(bx, R), threads, 0, s>>>(a0);
       MFP_CHECK_CUDA(cudaGetLastError());
       note_launch();
     }
