@@ -225,7 +225,9 @@ mfp_status mfp_rhs_noalloc(mfp_ctx* ctx, int f_kind, const double* params_host,
  * cell-major blocks of 4 (k+1)^3 nodal values (the SIPG cell layout per
  * field), 4 ncells (k+1)^3 doubles each, distinct.  Any mapping; the
  * coefficient is the constant one or the per-point values of
- * mfp_set_coefficient (cell and face values both needed).  The first call
+ * mfp_set_coefficient (cell and face values both needed).  The arithmetic
+ * follows fp64_arith (double-float on the FP32 pipes by default, DFMA for
+ * MFP_ARITH_NATIVE); x and y are float64 either way.  The first call
  * allocates the context's trace buffer (nfaces (k+1)^2 doubles) and, on
  * curved cells, per-point geometry (10 doubles per cell point, 4 per face
  * point): make it outside a stream capture.  Calls on one context share
@@ -309,10 +311,13 @@ mfp_status mfp_gradient(mfp_ctx* ctx, const double* u_dev,
  * precision `prec` for n_rhs columns with every admissible number of cells
  * per thread block (1..32, at most 1024 threads per block), on scratch
  * vectors it allocates and frees itself, and keeps the fastest choice in the
- * context for later applies with the same (level, prec, n_rhs); captured
- * V-cycles are re-captured.  Synchronises `stream`.  cells_out / ms_out
- * receive the choice and its time per apply (may be NULL).  The environment
- * variable MFP_CELLS_PER_BLOCK overrides every choice. */
+ * context for later applies with the same (level, prec, n_rhs); for float
+ * CG applies with k <= 4 and one column it also times the kernel that gives
+ * each cell one warp (reported as cells_out = 0).  Captured V-cycles are
+ * re-captured.  Synchronises `stream`.  cells_out / ms_out receive the choice
+ * and its time per apply (may be NULL).  The environment variable
+ * MFP_CELLS_PER_BLOCK overrides every choice (1000 selects the warp-per-cell
+ * kernel where it applies). */
 mfp_status mfp_autotune(mfp_ctx* ctx, int level, int prec, int n_rhs,
                         int* cells_out, double* ms_out, void* stream);
 

@@ -1201,6 +1201,27 @@ mfp_status mfp_autotune(mfp_ctx* c, int level, int prec, int n_rhs,
         best = cells;
       }
     }
+    // the warp-per-cell kernel of float CG applies (k <= 4, one column)
+    if (L.disc == MFP_CG && pr == MFP_FP32 && n_rhs == 1 && L.p <= 5) {
+      c->tuned.push_back({key, kWarpCells});
+      auto run = [&]() {
+        apply_level<float>(c, L, static_cast<const float*>(src),
+                           static_cast<float*>(dst), n_rhs, s);
+      };
+      run();
+      MFP_CHECK_CUDA(cudaEventRecord(e0, s));
+      for (int it = 0; it < 3; ++it) run();
+      MFP_CHECK_CUDA(cudaEventRecord(e1, s));
+      MFP_CHECK_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      MFP_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= 3;
+      c->tuned.pop_back();
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = kWarpCells;
+      }
+    }
   } catch (...) {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -1217,7 +1238,7 @@ mfp_status mfp_autotune(mfp_ctx* c, int level, int prec, int n_rhs,
   clear_error();
   c->tuned.push_back({key, best});
   drop_graphs(c);  // captured V-cycles used the previous launch shapes
-  if (cells_out) *cells_out = best;
+  if (cells_out) *cells_out = best == kWarpCells ? 0 : best;
   if (ms_out) *ms_out = best_ms;
   API_END
 }

@@ -1,5 +1,5 @@
 // Operator-apply kernels: cg discretization, float arithmetic.
-#include "k_apply.cuh"
+#include "k_apply_warp.cuh"
 
 namespace mfp {
 
@@ -11,6 +11,14 @@ void launch_apply_cg(const Level& L, const LevelData<float>& D,
   a.stride = nrhs;
   dispatch_p(L.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;
+    // cells == kWarpCells: one warp per cell (k <= 4, one column)
+    if (cells == kWarpCells && nrhs == 1) {
+      const bool done = L.curved ? run_apply_cg_warp<P, float, true>(a, s)
+                                 : run_apply_cg_warp<P, float, false>(a, s);
+      if (done) return;
+      cells = 0;
+    }
+    if (cells == kWarpCells) cells = 0;
     if (L.curved)
       run_apply_cols<P, float, false, true>(a, nrhs, cells, s);
     else

@@ -17,8 +17,11 @@
 // -<v, tau u> + <w . n, lambda> + <v, tau lambda> on the face-layer nodes.
 // tau = tau_factor times the largest coefficient on the face (Sec. 4.2).
 // Cartesian cells use their constant Jacobian; curved ones read w det J and
-// J^{-1} per cell point and dA and the unit normal per face point.  Plain
-// float64 arithmetic.
+// J^{-1} per cell point and dA and the unit normal per face point.  The
+// kernels are generic over the arithmetic: float64 (DFMA) for native-FP64
+// contexts, double-float pairs on the FP32 pipes for double-float ones (the
+// default), with the vectors float64 either way.
+#include "df.cuh"
 #include "dev_tables.cuh"
 
 namespace mfp {
@@ -49,37 +52,85 @@ __device__ __forceinline__ double face_tau(const HdgArgs& a, size_t f) {
   return a.tau_factor * m;
 }
 
+// Arithmetic of the HDG kernels: V the value type, S its shared-memory
+// element, Acc a dot-product accumulator.
+template <typename V>
+struct HT;
+template <>
+struct HT<double> {
+  using S = double;
+  using Acc = double;
+  static __device__ __forceinline__ double v(S x) { return x; }
+  static __device__ __forceinline__ S s(double x) { return x; }
+  static __device__ __forceinline__ double d2v(double x) { return x; }
+  static __device__ __forceinline__ double v2d(double x) { return x; }
+  static __device__ __forceinline__ Acc zero() { return 0.0; }
+  static __device__ __forceinline__ void mac(Acc& a, S m, S x) { a += m * x; }
+  static __device__ __forceinline__ double get(const Acc& a) { return a; }
+  static __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+};
+template <>
+struct HT<df> {
+  using S = float2;
+  using Acc = dacc;
+  static __device__ __forceinline__ df v(S x) { return df_make(x.x, x.y); }
+  static __device__ __forceinline__ S s(df x) { return make_float2(x.h, x.l); }
+  static __device__ __forceinline__ df d2v(double x) {
+    return df_from_double(x);
+  }
+  static __device__ __forceinline__ double v2d(df x) { return df_to_double(x); }
+  static __device__ __forceinline__ Acc zero() {
+    Acc a;
+    a.h = 0.f;
+    a.l = 0.f;
+    return a;
+  }
+  static __device__ __forceinline__ void mac(Acc& a, S m, S x) {
+    acc_mac(a, m.x, m.y, x.x, x.y);
+  }
+  static __device__ __forceinline__ df get(const Acc& a) { return acc_get(a); }
+  // 1/x: the float reciprocal refined by one Newton step in double-float
+  static __device__ __forceinline__ df recip(df x) {
+    const df y = df_make(__frcp_rn(x.h));
+    return y + y * (df_make(1.f) - x * y);
+  }
+};
+
 // out = M (or M^T) applied along `axis` of nf fields of p^3 values
-template <int P>
-__device__ void sweep3(const double* M, bool tr, int axis, const double* in,
-                       double* out, int nf) {
+template <int P, typename V>
+__device__ void sweep3(const typename HT<V>::S* M, bool tr, int axis,
+                       const typename HT<V>::S* in, typename HT<V>::S* out,
+                       int nf) {
+  using H = HT<V>;
   constexpr int N = P * P * P;
   const int st = axis == 0 ? 1 : (axis == 1 ? P : P * P);
   for (int t = threadIdx.x; t < nf * N; t += blockDim.x) {
     const int i = t % N;
     const int ii = axis == 0 ? i % P : (axis == 1 ? (i / P) % P : i / (P * P));
-    const double* src = in + (t - i) + (i - ii * st);
-    double acc = 0;
+    const typename H::S* src = in + (t - i) + (i - ii * st);
+    typename H::Acc acc = H::zero();
     for (int j = 0; j < P; ++j)
-      acc += (tr ? M[j * P + ii] : M[ii * P + j]) * src[j * st];
-    out[t] = acc;
+      H::mac(acc, tr ? M[j * P + ii] : M[ii * P + j], src[j * st]);
+    out[t] = H::s(H::get(acc));
   }
 }
 
 // the same on nf fields of p^2 face values (axis 0: a, 1: b)
-template <int P>
-__device__ void sweep2(const double* M, bool tr, int axis, const double* in,
-                       double* out, int nf) {
+template <int P, typename V>
+__device__ void sweep2(const typename HT<V>::S* M, bool tr, int axis,
+                       const typename HT<V>::S* in, typename HT<V>::S* out,
+                       int nf) {
+  using H = HT<V>;
   constexpr int F = P * P;
   const int st = axis == 0 ? 1 : P;
   for (int t = threadIdx.x; t < nf * F; t += blockDim.x) {
     const int i = t % F;
     const int ii = axis == 0 ? i % P : i / P;
-    const double* src = in + (t - i) + (i - ii * st);
-    double acc = 0;
+    const typename H::S* src = in + (t - i) + (i - ii * st);
+    typename H::Acc acc = H::zero();
     for (int j = 0; j < P; ++j)
-      acc += (tr ? M[j * P + ii] : M[ii * P + j]) * src[j * st];
-    out[t] = acc;
+      H::mac(acc, tr ? M[j * P + ii] : M[ii * P + j], src[j * st]);
+    out[t] = H::s(H::get(acc));
   }
 }
 
@@ -93,16 +144,17 @@ __device__ __forceinline__ int layer_node(int D, int s, int ja, int jb) {
   return ii[0] + P * (ii[1] + P * ii[2]);
 }
 
-
 // One block per face of direction D: lambda at the face Gauss points,
 //   lambda = sum_sides (q . n_out + tau u) / (tau * number of sides),
 // n_out the side's outward unit normal (+n for the cell below the face, -n
 // for the one above; n = e_D on Cartesian cells).
-template <int P>
+template <int P, typename V>
 __global__ void k_hdg_trace(HdgArgs a, int D) {
+  using H = HT<V>;
+  using S = typename H::S;
   constexpr int F = P * P, N = P * P * P;
-  __shared__ double sS[P * P];
-  __shared__ double lay[8 * F], tmp[8 * F];  // [side][q_x, q_y, q_z, u][F]
+  __shared__ S sS[P * P];
+  __shared__ S lay[8 * F], tmp[8 * F];  // [side][q_x, q_y, q_z, u][F]
   int m[3] = {a.n[0], a.n[1], a.n[2]};
   m[D] += 1;
   const int fl = blockIdx.x;
@@ -119,37 +171,39 @@ __global__ void k_hdg_trace(HdgArgs a, int D) {
   const int cellL = hasL ? cL[0] + a.n[0] * (cL[1] + a.n[1] * cL[2]) : 0;
   const int cellR = hasR ? fc[0] + a.n[0] * (fc[1] + a.n[1] * fc[2]) : 0;
   for (int i = threadIdx.x; i < P * P; i += blockDim.x)
-    sS[i] = c_tab64[P - 2].S[i];
+    sS[i] = H::s(H::d2v(c_tab64[P - 2].S[i]));
   for (int t = threadIdx.x; t < 8 * F; t += blockDim.x) {
     const int sf = t / F, j = t % F;  // side 0: lower cell, 1: upper cell
-    const int s = sf / 4, fld = sf % 4;
-    const bool has = s == 0 ? hasL : hasR;
-    const int loc = layer_node<P>(D, s == 0 ? 1 : 0, j % P, j / P);
-    const double* xc = a.x + (size_t)(s == 0 ? cellL : cellR) * 4 * N;
-    lay[t] = has ? xc[fld * N + loc] : 0.0;
+    const int sd = sf / 4, fld = sf % 4;
+    const bool has = sd == 0 ? hasL : hasR;
+    const int loc = layer_node<P>(D, sd == 0 ? 1 : 0, j % P, j / P);
+    const double* xc = a.x + (size_t)(sd == 0 ? cellL : cellR) * 4 * N;
+    lay[t] = H::s(H::d2v(has ? xc[fld * N + loc] : 0.0));
   }
   __syncthreads();
-  sweep2<P>(sS, false, 0, lay, tmp, 8);
+  sweep2<P, V>(sS, false, 0, lay, tmp, 8);
   __syncthreads();
-  sweep2<P>(sS, false, 1, tmp, lay, 8);
+  sweep2<P, V>(sS, false, 1, tmp, lay, 8);
   __syncthreads();
-  const double tau = face_tau<P>(a, f);
+  const V tau = H::d2v(face_tau<P>(a, f));
+  const V inv = H::recip(H::d2v((hasL && hasR ? 2.0 : 1.0) *
+                                face_tau<P>(a, f)));
   for (int q = threadIdx.x; q < F; q += blockDim.x) {
-    double nv[3] = {0.0, 0.0, 0.0};
+    V nv[3] = {H::d2v(0.0), H::d2v(0.0), H::d2v(0.0)};
     if (a.gf) {
-      for (int e = 0; e < 3; ++e) nv[e] = a.gf[(f * 4 + 1 + e) * F + q];
+      for (int e = 0; e < 3; ++e) nv[e] = H::d2v(a.gf[(f * 4 + 1 + e) * F + q]);
     } else {
-      nv[D] = 1.0;
+      nv[D] = H::d2v(1.0);
     }
-    double num = 0, den = 0;
-    for (int s = 0; s < 2; ++s) {
-      if (!(s == 0 ? hasL : hasR)) continue;
-      const double* L = lay + 4 * s * F;
-      const double qn = nv[0] * L[q] + nv[1] * L[F + q] + nv[2] * L[2 * F + q];
-      num += (s == 0 ? qn : -qn) + tau * L[3 * F + q];
-      den += tau;
+    V num = H::d2v(0.0);
+    for (int sd = 0; sd < 2; ++sd) {
+      if (!(sd == 0 ? hasL : hasR)) continue;
+      const S* L = lay + 4 * sd * F;
+      const V qn = nv[0] * H::v(L[q]) + nv[1] * H::v(L[F + q]) +
+                   nv[2] * H::v(L[2 * F + q]);
+      num = num + (sd == 0 ? qn : V(-qn)) + tau * H::v(L[3 * F + q]);
     }
-    a.lam[f * F + q] = num / den;
+    a.lam[f * F + q] = H::v2d(num * inv);
   }
 }
 
@@ -159,21 +213,23 @@ constexpr size_t hdg_cell_smem() {
 }
 
 // Geometry of cell point t: w det J and J^{-1}[e][d] (row e, column d).
-template <int P>
+template <int P, typename V>
 __device__ __forceinline__ void point_geo(const HdgArgs& a, int cell, int t,
-                                          const double* sw, double& wdet,
-                                          double (&Ji)[3][3]) {
+                                          const double* sw, V& wdet,
+                                          V (&Ji)[3][3]) {
+  using H = HT<V>;
   constexpr int N = P * P * P;
   if (a.gc) {
     const double* g = a.gc + (size_t)cell * 10 * N + t;
-    wdet = g[0];
+    wdet = H::d2v(g[0]);
     for (int e = 0; e < 3; ++e)
-      for (int d = 0; d < 3; ++d) Ji[e][d] = g[(1 + 3 * e + d) * N];
+      for (int d = 0; d < 3; ++d) Ji[e][d] = H::d2v(g[(1 + 3 * e + d) * N]);
   } else {
-    wdet = sw[t % P] * sw[(t / P) % P] * sw[t / (P * P)] * a.h[0] * a.h[1] *
-           a.h[2];
+    wdet = H::d2v(sw[t % P] * sw[(t / P) % P] * sw[t / (P * P)] * a.h[0] *
+                  a.h[1] * a.h[2]);
     for (int e = 0; e < 3; ++e)
-      for (int d = 0; d < 3; ++d) Ji[e][d] = e == d ? 1.0 / a.h[d] : 0.0;
+      for (int d = 0; d < 3; ++d)
+        Ji[e][d] = H::d2v(e == d ? 1.0 / a.h[d] : 0.0);
   }
 }
 
@@ -181,88 +237,93 @@ __device__ __forceinline__ void point_geo(const HdgArgs& a, int cell, int t,
 // Gauss points (w det = w_q det J, J^{-1} = dxi/dx):
 //   q_d rows: w det kappa^-1 q_d - sum_e D_e^T (w det J^{-1}[e][d] u)
 //   u rows:   -w det sum_{d,e} J^{-1}[e][d] D_e q_d
-template <int P>
+template <int P, typename V>
 __global__ void k_hdg_cell(HdgArgs a) {
+  using H = HT<V>;
+  using S = typename H::S;
   constexpr int F = P * P, N = P * P * P;
-  __shared__ double sS[P * P], sD[P * P], sw[P];
-  extern __shared__ __align__(16) double hsm[];
-  double* A = hsm;
-  double* B = hsm + 4 * N;
-  double* FS = hsm + 8 * N;
+  __shared__ S sS[P * P], sD[P * P];
+  __shared__ double sw[P];
+  extern __shared__ __align__(16) unsigned char hraw[];
+  S* A = reinterpret_cast<S*>(hraw);
+  S* B = A + 4 * N;
+  S* FS = A + 8 * N;
   const int cell = blockIdx.x;
   const int c3[3] = {cell % a.n[0], (cell / a.n[0]) % a.n[1],
                      cell / (a.n[0] * a.n[1])};
   for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
-    sS[i] = c_tab64[P - 2].S[i];
-    sD[i] = c_tab64[P - 2].D[i];
+    sS[i] = H::s(H::d2v(c_tab64[P - 2].S[i]));
+    sD[i] = H::s(H::d2v(c_tab64[P - 2].D[i]));
   }
   for (int i = threadIdx.x; i < P; i += blockDim.x) sw[i] = c_tab64[P - 2].w[i];
   const double* xc = a.x + (size_t)cell * 4 * N;
-  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) A[t] = xc[t];
+  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) A[t] = H::s(H::d2v(xc[t]));
   __syncthreads();
   // values of the four fields at the Gauss points
-  sweep3<P>(sS, false, 0, A, B, 4);
+  sweep3<P, V>(sS, false, 0, A, B, 4);
   __syncthreads();
-  sweep3<P>(sS, false, 1, B, A, 4);
+  sweep3<P, V>(sS, false, 1, B, A, 4);
   __syncthreads();
-  sweep3<P>(sS, false, 2, A, B, 4);
+  sweep3<P, V>(sS, false, 2, A, B, 4);
   __syncthreads();
   const int st[3] = {1, P, P * P};
   // u rows and the mass part of the q rows
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     const int ii[3] = {t % P, (t / P) % P, t / (P * P)};
-    double wdet, Ji[3][3];
-    point_geo<P>(a, cell, t, sw, wdet, Ji);
-    const double kinv =
-        1.0 / (a.kcell ? a.kcell[(size_t)cell * N + t] : a.kappa);
-    double dv = 0;
+    V wdet, Ji[3][3];
+    point_geo<P, V>(a, cell, t, sw, wdet, Ji);
+    const V kinv =
+        a.kcell ? H::recip(H::d2v(a.kcell[(size_t)cell * N + t]))
+                : H::d2v(1.0 / a.kappa);
+    V dv = H::d2v(0.0);
     for (int d = 0; d < 3; ++d) {
       for (int e = 0; e < 3; ++e) {
         if (!a.gc && e != d) continue;
         const int base = t - ii[e] * st[e];
-        double s1 = 0;
+        typename H::Acc s1 = H::zero();
         for (int j = 0; j < P; ++j)
-          s1 += sD[ii[e] * P + j] * B[d * N + base + j * st[e]];
-        dv += Ji[e][d] * s1;
+          H::mac(s1, sD[ii[e] * P + j], B[d * N + base + j * st[e]]);
+        dv = dv + Ji[e][d] * H::get(s1);
       }
-      A[d * N + t] = wdet * kinv * B[d * N + t];
+      A[d * N + t] = H::s(wdet * kinv * H::v(B[d * N + t]));
     }
-    A[3 * N + t] = -wdet * dv;
+    A[3 * N + t] = H::s(V(-(wdet * dv)));
   }
   __syncthreads();
   // -sum_e D_e^T (w det J^{-1}[e][d] u) into the q_d rows, one d at a time
   // (the q values at the points in B are no longer needed)
   for (int d = 0; d < 3; ++d) {
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
-      double wdet, Ji[3][3];
-      point_geo<P>(a, cell, t, sw, wdet, Ji);
-      for (int e = 0; e < 3; ++e) B[e * N + t] = wdet * Ji[e][d] * B[3 * N + t];
+      V wdet, Ji[3][3];
+      point_geo<P, V>(a, cell, t, sw, wdet, Ji);
+      for (int e = 0; e < 3; ++e)
+        B[e * N + t] = H::s(wdet * Ji[e][d] * H::v(B[3 * N + t]));
     }
     __syncthreads();
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
       const int ii[3] = {t % P, (t / P) % P, t / (P * P)};
-      double s2 = 0;
+      typename H::Acc s2 = H::zero();
       for (int e = 0; e < 3; ++e) {
         if (!a.gc && e != d) continue;
         const int base = t - ii[e] * st[e];
         for (int j = 0; j < P; ++j)
-          s2 += sD[j * P + ii[e]] * B[e * N + base + j * st[e]];
+          H::mac(s2, sD[j * P + ii[e]], B[e * N + base + j * st[e]]);
       }
-      A[d * N + t] -= s2;
+      A[d * N + t] = H::s(H::v(A[d * N + t]) - H::get(s2));
     }
     __syncthreads();
   }
-  sweep3<P>(sS, true, 2, A, B, 4);
+  sweep3<P, V>(sS, true, 2, A, B, 4);
   __syncthreads();
-  sweep3<P>(sS, true, 1, B, A, 4);
+  sweep3<P, V>(sS, true, 1, B, A, 4);
   __syncthreads();
-  sweep3<P>(sS, true, 0, A, B, 4);
+  sweep3<P, V>(sS, true, 0, A, B, 4);
   __syncthreads();
   // faces: scratch FS (10 p^2 values)
-  double* ul = FS;           // u layer, then u at the face points
-  double* ut = FS + F;       // sweep temporary
-  double* gcf = FS + 2 * F;  // [w_x, w_y, w_z, v] terms at the face points
-  double* gt = FS + 6 * F;   // sweep temporary for the four fields
+  S* ul = FS;           // u layer, then u at the face points
+  S* ut = FS + F;       // sweep temporary
+  S* gcf = FS + 2 * F;  // [w_x, w_y, w_z, v] terms at the face points
+  S* gt = FS + 6 * F;   // sweep temporary for the four fields
   for (int D = 0; D < 3; ++D) {
     const int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
     int m[3] = {a.n[0], a.n[1], a.n[2]};
@@ -273,42 +334,67 @@ __global__ void k_hdg_cell(HdgArgs a) {
       const size_t f = (size_t)a.face_off[D] + fc[0] +
                        (size_t)m[0] * (fc[1] + (size_t)m[1] * fc[2]);
       for (int j = threadIdx.x; j < F; j += blockDim.x)
-        ul[j] = xc[3 * N + layer_node<P>(D, s, j % P, j / P)];
+        ul[j] = H::s(H::d2v(xc[3 * N + layer_node<P>(D, s, j % P, j / P)]));
       __syncthreads();
-      sweep2<P>(sS, false, 0, ul, ut, 1);
+      sweep2<P, V>(sS, false, 0, ul, ut, 1);
       __syncthreads();
-      sweep2<P>(sS, false, 1, ut, ul, 1);
+      sweep2<P, V>(sS, false, 1, ut, ul, 1);
       __syncthreads();
-      const double tau = face_tau<P>(a, f);
-      const double so = s ? 1.0 : -1.0;  // outward: +n on the upper face
+      const V tau = H::d2v(face_tau<P>(a, f));
       for (int q = threadIdx.x; q < F; q += blockDim.x) {
-        double dA, nv[3] = {0.0, 0.0, 0.0};
+        V dA, nv[3] = {H::d2v(0.0), H::d2v(0.0), H::d2v(0.0)};
         if (a.gf) {
-          dA = a.gf[(f * 4) * F + q];
-          for (int e = 0; e < 3; ++e) nv[e] = a.gf[(f * 4 + 1 + e) * F + q];
+          dA = H::d2v(a.gf[(f * 4) * F + q]);
+          for (int e = 0; e < 3; ++e)
+            nv[e] = H::d2v(a.gf[(f * 4 + 1 + e) * F + q]);
         } else {
-          dA = sw[q % P] * sw[q / P] * a.h[T1] * a.h[T2];
-          nv[D] = 1.0;
+          dA = H::d2v(sw[q % P] * sw[q / P] * a.h[T1] * a.h[T2]);
+          nv[D] = H::d2v(1.0);
         }
-        const double lq = a.lam[f * F + q];
+        // outward normal: +n on the upper face (s = 1), -n on the lower one
+        const V lq = H::d2v(a.lam[f * F + q]);
+        const V dl = s ? V(dA * lq) : V(-(dA * lq));
         for (int e = 0; e < 3; ++e)
-          gcf[e * F + q] = dA * so * nv[e] * lq;       // <w . n, lambda>
-        gcf[3 * F + q] = dA * tau * (lq - ul[q]);      // <v, tau (lambda - u)>
+          gcf[e * F + q] = H::s(dl * nv[e]);              // <w . n, lambda>
+        gcf[3 * F + q] = H::s(dA * tau * (lq - H::v(ul[q])));  // <v, tau(lambda-u)>
       }
       __syncthreads();
-      sweep2<P>(sS, true, 1, gcf, gt, 4);
+      sweep2<P, V>(sS, true, 1, gcf, gt, 4);
       __syncthreads();
-      sweep2<P>(sS, true, 0, gt, gcf, 4);
+      sweep2<P, V>(sS, true, 0, gt, gcf, 4);
       __syncthreads();
       for (int j = threadIdx.x; j < F; j += blockDim.x) {
         const int loc = layer_node<P>(D, s, j % P, j / P);
-        for (int e = 0; e < 4; ++e) B[e * N + loc] += gcf[e * F + j];
+        for (int e = 0; e < 4; ++e)
+          B[e * N + loc] = H::s(H::v(B[e * N + loc]) + H::v(gcf[e * F + j]));
       }
       __syncthreads();
     }
   }
   double* yc = a.y + (size_t)cell * 4 * N;
-  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) yc[t] = B[t];
+  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) yc[t] = H::v2d(H::v(B[t]));
+}
+
+template <typename V>
+void run_hdg(const Level& L, const HdgArgs& a, cudaStream_t s) {
+  dispatch_p(L.p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
+    for (int D = 0; D < 3; ++D) {
+      int m[3] = {L.n[0], L.n[1], L.n[2]};
+      m[D] += 1;
+      k_hdg_trace<P, V><<<m[0] * m[1] * m[2], 64, 0, s>>>(a, D);
+      MFP_CHECK_CUDA(cudaGetLastError());
+      note_launch();
+    }
+    constexpr size_t smem = hdg_cell_smem<P>();
+    if (smem > 48 * 1024)
+      MFP_CHECK_CUDA(cudaFuncSetAttribute(
+          k_hdg_cell<P, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          (int)smem));
+    k_hdg_cell<P, V><<<(int)L.ncells, 128, smem, s>>>(a);
+    MFP_CHECK_CUDA(cudaGetLastError());
+    note_launch();
+  });
 }
 
 }  // namespace
@@ -333,24 +419,10 @@ void launch_hdg_apply(const Level& L, double tau_factor, double* lam,
   a.kface = L.d64.kface;
   a.gc = hdg_cell;
   a.gf = hdg_face;
-  dispatch_p(L.p, [&](auto pc) {
-    constexpr int P = decltype(pc)::value;
-    for (int D = 0; D < 3; ++D) {
-      int m[3] = {L.n[0], L.n[1], L.n[2]};
-      m[D] += 1;
-      k_hdg_trace<P><<<m[0] * m[1] * m[2], 64, 0, s>>>(a, D);
-      MFP_CHECK_CUDA(cudaGetLastError());
-      note_launch();
-    }
-    constexpr size_t smem = hdg_cell_smem<P>();
-    if (smem > 48 * 1024)
-      MFP_CHECK_CUDA(cudaFuncSetAttribute(
-          k_hdg_cell<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-          (int)smem));
-    k_hdg_cell<P><<<(int)L.ncells, 128, smem, s>>>(a);
-    MFP_CHECK_CUDA(cudaGetLastError());
-    note_launch();
-  });
+  if (L.df_arith)
+    run_hdg<df>(L, a, s);
+  else
+    run_hdg<double>(L, a, s);
 }
 
 }  // namespace mfp

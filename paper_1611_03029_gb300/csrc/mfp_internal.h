@@ -120,6 +120,7 @@ enum ScalarSlot {
 constexpr int kMaxRedBlocks = 1024;
 constexpr int kMaxRhs = 256;
 constexpr int kMaxGaussTerms = 4096;  // forcing terms of mfp_rhs (f_kind 1, 2)
+constexpr int kWarpCells = 1000;  // cells-per-block value of the warp-per-cell CG kernel
 constexpr int kDenseMax = 2048;   // dofs of a coarsest level stored dense
 constexpr int kDenseRows = 128;   // rows per block of k_dense_apply
 constexpr int kDenseSplit = 32;   // column ranges per row block

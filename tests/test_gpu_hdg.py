@@ -1,7 +1,7 @@
 """The HDG mixed matrix-free operator (Sec. 3, "HDG mixed matrix-free") of
 the CUDA library against the oracle's assembled mixed operator, element by
-element, 1e-12 of the largest entry (float64 arithmetic, the tolerance of
-the other float64 applies)."""
+element, 1e-12 of the largest entry (the tolerance of the other float64
+applies), in the default double-float arithmetic and in IEEE float64."""
 import numpy as np
 import pytest
 import torch
@@ -32,6 +32,22 @@ def test_hdg_apply_matches_oracle(mfp, k, n, sides, box, kappa):
     # repeated applies are identical (no atomics)
     y2 = op.hdg_apply(torch.from_numpy(x).cuda()).cpu().numpy()
     assert np.array_equal(y, y2)
+
+
+@pytest.mark.parametrize("k,mapping", [(2, "identity"), (4, "sine")])
+def test_hdg_apply_native_fp64(mfp, k, mapping):
+    # the IEEE float64 (DFMA) kernels of a native context; the default
+    # contexts above run the double-float ones
+    n, sides = (2, 3, 2), (0, 2, 4)
+    amp = 0.1 if mapping == "sine" else 0.0
+    op = mfp.Poisson(*n, k, disc="dg", n_levels=1, neumann_sides=sides,
+                     mapping=mapping, map_param=amp, fp64_arith="native")
+    P = fem.Problem(*n, k, disc="dg", neumann_sides=sides, mapping=mapping,
+                    amp=amp)
+    A = hdg.mixed_operator(P)
+    x = synthetic.random_vector(A.shape[0], seed=90 + k)
+    y = op.hdg_apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel_err(y, A @ x) <= 1e-12
 
 
 def test_hdg_apply_full_size_sampled_cells(mfp):

@@ -129,3 +129,29 @@ def test_rhs_matches_oracle(mfp):
         b = op.rhs(1, g).cpu().numpy()
         ref = fem.load_vector(P, synthetic.gaussian_forcing(g))
         assert rel_err(b, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("mapping", ["identity", "sine"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_warp_per_cell_cg_float(mfp, mapping, k, monkeypatch):
+    # the float CG kernel that gives each cell one warp (k <= 4), selected by
+    # the cells-per-block override 1000, on a mesh with several warps' worth
+    # of cells and a ragged tail; also through a V-cycle of the float
+    # hierarchy (every level)
+    amp = 0.1 if mapping == "sine" else 0.0
+    n = (5, 3, 4)
+    P = fem.Problem(*n, k, mapping=mapping, amp=amp)
+    u = synthetic.random_vector(P.n_dofs, seed=300 + k)
+    op = mfp.Poisson(*n, k, mapping=mapping, map_param=amp, n_levels=1,
+                     mg_precision="fp32")
+    ref = fem.assemble(P) @ u
+    y0 = op.apply(torch.from_numpy(u).float().cuda()).cpu().numpy()
+    monkeypatch.setenv("MFP_CELLS_PER_BLOCK", "1000")
+    y = op.apply(torch.from_numpy(u).float().cuda()).cpu().numpy()
+    assert rel_err(y, ref) <= TOL32
+    assert rel_err(y, y0) <= TOL32
+    monkeypatch.delenv("MFP_CELLS_PER_BLOCK")
+    cells, ms = op.autotune(prec="fp32")
+    assert cells >= 0 and ms > 0
+    y1 = op.apply(torch.from_numpy(u).float().cuda()).cpu().numpy()
+    assert rel_err(y1, ref) <= TOL32
