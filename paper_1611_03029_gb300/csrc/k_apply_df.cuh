@@ -853,21 +853,23 @@ __global__ void __maxnreg__((df_max_regs<P, DG>() > 255 ? 255
 template <int P>
 __global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
   constexpr int P2 = P * P, P3 = P2 * P;
-  // one thread per node (cell, x, y, z) of column blockIdx.y; the face
-  // buffer slots of a cell are read by its p^3 threads (cached)
-  const int R = a.stride, col = blockIdx.y;
+  // one thread per node (cell, x, y, z) of a row of cells (cy, cz) =
+  // blockIdx.y, column blockIdx.z; the face buffer slots of a cell are read
+  // by its p^3 threads (cached)
+  const int R = a.stride, col = blockIdx.z;
   const float* d0h = c_tabdf[P - 2].d0h;
   const float* d0l = c_tabdf[P - 2].d0l;
-  const size_t total = (size_t)a.ncells * P3;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.n[0] * P3) return;
+  const int cx = t / P3, loc = t - cx * P3;
+  const int x = loc % P, y = (loc / P) % P, z = loc / P2;
   const int mode = a.epi.mode;
   const float2 f0 = make_float2(0.f, 0.f);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const size_t cell = i / P3;
-    const int loc = (int)(i - cell * P3);
-    const int x = loc % P, y = (loc / P) % P, z = loc / P2;
-    const int cx = (int)(cell % a.n[0]), cy = (int)((cell / a.n[0]) % a.n[1]),
-              cz = (int)(cell / ((size_t)a.n[0] * a.n[1]));
+  const int rows = a.n[1] * a.n[2];
+  for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+    const int cy = row % a.n[1], cz = row / a.n[1];
+    const size_t cell = (size_t)row * a.n[0] + cx;
+    const size_t i = cell * P3 + loc;
     const float2* fb = a.fb + cell * 6 * P2 * R + col;
     const size_t gi = i * R + col;
     // every load first: the cell-kernel result, the face-buffer terms of the
@@ -1002,11 +1004,11 @@ void run_apply_df_cols(const ApplyArgsDF& a0, int R, int cells_req,
   if constexpr (DG) {
     MFP_REQUIRE(a0.fb, "SIPG face buffer missing");
     const int threads = 256;
-    const int64_t total = (int64_t)a0.ncells * P2 * P;
-    const int64_t want = (total + threads - 1) / threads;
-    const int bx = (int)(want < (1 << 30) ? want : (1 << 30));
+    const int bx = (a0.n[0] * P2 * P + threads - 1) / threads;
+    const int rows = a0.n[1] * a0.n[2];
+    const int by = rows < 65535 ? rows : 65535;
     if (a0.ncells > 0) {
-      k_dg_face_add<P><<<dim3(bx, R), threads, 0, s>>>(a0);
+      k_dg_face_add<P><<<dim3(bx, by, R), threads, 0, s>>>(a0);
       MFP_CHECK_CUDA(cudaGetLastError());
       note_launch();
     }
