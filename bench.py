@@ -222,7 +222,7 @@ def fp64_pipe_peak_tflops(sm_count, sm_mhz):
 # DRAM traffic (read + write) per launch of the dominant kernel from one ncu
 # capture, keyed by a hash of the sources it was compiled from; a kernel
 # changed since its capture reports null.
-TRAFFIC = {"dee6cd16a4158dcf": 431.08e6}  # ncu, Q4 32^3 curved, 1 launch
+TRAFFIC = {"8b860ca0624869ae": 501.96e6}  # ncu, Q4 32^3 curved: k_apply_df + k_dg_face_add
 
 
 def kernel_hash():
