@@ -293,40 +293,57 @@ __device__ __noinline__ void face_lower_gp(const ApplyArgs<T>& a, int col,
 // Adds the terms that the cell below each interior face left for the cell
 // above it (face buffer slots 2D: value part on the face layer, 2D + 1:
 // normal-slope part on every layer with the weight dphi_l(0)) and applies the
-// fused update; one thread per node (cell, x, y, z) of a row of cells
-// (cy, cz) = blockIdx.y, column blockIdx.z.
+// fused update; one thread per node line along z of a row of cells
+// (blockIdx.y: cy, cz; blockIdx.z: column).  Float values are cheap to keep
+// in registers, so a thread takes the whole line and every load of it is in
+// flight at once (the double-float kernel works per node instead).
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_dg_face_add_t(const ApplyArgs<T> a) {
   constexpr int P2 = P * P, P3 = P2 * P;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n[0] * P2) return;
   const int R = a.stride, col = blockIdx.z;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.n[0] * P3) return;
-  const int cx = t / P3, loc = t - cx * P3;
-  const int x = loc % P, y = (loc / P) % P, z = loc / P2;
-  const int mode = a.epi.mode;
+  const int cx = i / P2, xy = i - cx * P2;
+  const int x = xy % P, y = xy / P;
   const int rows = a.n[1] * a.n[2];
   for (int row = blockIdx.y; row < rows; row += gridDim.y) {
     const int cy = row % a.n[1], cz = row / a.n[1];
     const size_t cell = (size_t)row * a.n[0] + cx;
-    const size_t i = cell * P3 + loc;
     const T* fb = a.fb + cell * 6 * P2 * R + col;
-    const size_t gi = i * R + col;
-    const T u = a.dst[gi];
-    const T gx = cx > 0 ? fb[(size_t)(1 * P2 + y + P * z) * R] : T(0);
-    const T vx = cx > 0 && x == 0 ? fb[(size_t)(0 * P2 + y + P * z) * R] : T(0);
-    const T gy = cy > 0 ? fb[(size_t)(3 * P2 + x + P * z) * R] : T(0);
-    const T vy = cy > 0 && y == 0 ? fb[(size_t)(2 * P2 + x + P * z) * R] : T(0);
-    const T gz = cz > 0 ? fb[(size_t)(5 * P2 + x + P * y) * R] : T(0);
-    const T vz = cz > 0 && z == 0 ? fb[(size_t)(4 * P2 + x + P * y) * R] : T(0);
-    const T eb = mode != EPI_STORE ? a.epi.b[gi] : T(0);
-    const T edi = mode >= EPI_CHEB_FIRST ? a.epi.dinv[i] : T(0);
-    const T ex = mode >= EPI_CHEB_FIRST ? a.epi.x[gi] : T(0);
-    const T ed = mode == EPI_CHEB_STEP ? a.epi.d[gi] : T(0);
-    T s = u;
-    if (cx > 0) s += fma(tv<T, P, T_DPHI0>(x), gx, vx);
-    if (cy > 0) s += fma(tv<T, P, T_DPHI0>(y), gy, vy);
-    if (cz > 0) s += fma(tv<T, P, T_DPHI0>(z), gz, vz);
-    epi_finish(a.epi, a.dst, gi, s, eb, edi, ed, ex);
+    T* out = a.dst + (cell * P3 + xy) * R + col;
+    T u[P], gx[P], vx[P], gy[P], vy[P];
+#pragma unroll
+    for (int z = 0; z < P; ++z) {
+      u[z] = out[(size_t)z * P2 * R];
+      gx[z] = fb[(size_t)(1 * P2 + y + P * z) * R];
+      vx[z] = x == 0 ? fb[(size_t)(0 * P2 + y + P * z) * R] : T(0);
+      gy[z] = fb[(size_t)(3 * P2 + x + P * z) * R];
+      vy[z] = y == 0 ? fb[(size_t)(2 * P2 + x + P * z) * R] : T(0);
+    }
+    const T gz = fb[(size_t)(5 * P2 + xy) * R];
+    const T vz = fb[(size_t)(4 * P2 + xy) * R];
+    const T wx = tv<T, P, T_DPHI0>(x), wy = tv<T, P, T_DPHI0>(y);
+    // the fused update's inputs, loaded with the rest
+    const size_t dof = cell * P3 + xy;
+    const int mode = a.epi.mode;
+    T eb[P], edi[P], ed[P], ex[P];
+#pragma unroll
+    for (int z = 0; z < P; ++z) {
+      const size_t gi = (dof + (size_t)z * P2) * R + col;
+      eb[z] = mode != EPI_STORE ? a.epi.b[gi] : T(0);
+      edi[z] = mode >= EPI_CHEB_FIRST ? a.epi.dinv[dof + (size_t)z * P2] : T(0);
+      ex[z] = mode >= EPI_CHEB_FIRST ? a.epi.x[gi] : T(0);
+      ed[z] = mode == EPI_CHEB_STEP ? a.epi.d[gi] : T(0);
+    }
+#pragma unroll
+    for (int z = 0; z < P; ++z) {
+      T s = u[z];
+      if (cx > 0) s += fma(wx, gx[z], vx[z]);
+      if (cy > 0) s += fma(wy, gy[z], vy[z]);
+      if (cz > 0) s += fma(tv<T, P, T_DPHI0>(z), gz, z == 0 ? vz : T(0));
+      epi_finish(a.epi, a.dst, (dof + (size_t)z * P2) * R + col, s, eb[z],
+                 edi[z], ed[z], ex[z]);
+    }
   }
 }
 
@@ -734,7 +751,7 @@ void run_apply_cols(const ApplyArgs<T>& a0, int R, int cells_req,
   if constexpr (DG) {
     MFP_REQUIRE(a0.fb, "SIPG face buffer missing");
     const int threads = 256;
-    const int bx = (a0.n[0] * P2 * P + threads - 1) / threads;
+    const int bx = (a0.n[0] * P2 + threads - 1) / threads;
     const int rows = a0.n[1] * a0.n[2];
     const int by = rows < 65535 ? rows : 65535;
     if (a0.ncells > 0) {

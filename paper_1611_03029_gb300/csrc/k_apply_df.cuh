@@ -866,47 +866,65 @@ __global__ void __launch_bounds__(256) k_dg_face_add(const ApplyArgsDF a) {
   const int mode = a.epi.mode;
   const float2 f0 = make_float2(0.f, 0.f);
   const int rows = a.n[1] * a.n[2];
-  for (int row = blockIdx.y; row < rows; row += gridDim.y) {
-    const int cy = row % a.n[1], cz = row / a.n[1];
+  // the inputs of one node: the cell-kernel result, the face-buffer terms of
+  // the lower faces inside the mesh, the fused update's inputs
+  struct In {
+    size_t gi;
+    int cx, cy, cz;
+    double u, eb, edi, ex, ed;
+    float2 gx, vx, gy, vy, gz, vz;
+  };
+  auto load = [&](int row) {
+    In v;
+    v.cx = cx;
+    v.cy = row % a.n[1];
+    v.cz = row / a.n[1];
     const size_t cell = (size_t)row * a.n[0] + cx;
     const size_t i = cell * P3 + loc;
     const float2* fb = a.fb + cell * 6 * P2 * R + col;
-    const size_t gi = i * R + col;
-    // every load first: the cell-kernel result, the face-buffer terms of the
-    // lower faces inside the mesh, the fused update's inputs
-    const double u = a.dst[gi];
-    const float2 gx = cx > 0 ? fb[(size_t)(1 * P2 + y + P * z) * R] : f0;
-    const float2 vx =
-        cx > 0 && x == 0 ? fb[(size_t)(0 * P2 + y + P * z) * R] : f0;
-    const float2 gy = cy > 0 ? fb[(size_t)(3 * P2 + x + P * z) * R] : f0;
-    const float2 vy =
-        cy > 0 && y == 0 ? fb[(size_t)(2 * P2 + x + P * z) * R] : f0;
-    const float2 gz = cz > 0 ? fb[(size_t)(5 * P2 + x + P * y) * R] : f0;
-    const float2 vz =
-        cz > 0 && z == 0 ? fb[(size_t)(4 * P2 + x + P * y) * R] : f0;
-    const double eb = mode != EPI_STORE ? a.epi.b[gi] : 0.0;
-    const double edi = mode >= EPI_CHEB_FIRST ? a.epi.dinv[i] : 0.0;
-    const double ex = mode >= EPI_CHEB_FIRST ? a.epi.x[gi] : 0.0;
-    const double ed = mode == EPI_CHEB_STEP ? a.epi.d[gi] : 0.0;
-    // the slope part on every layer along the face normal (weight dphi_l(0)),
-    // the value part on layer 0
-    const df uz = df_from_double(u);
+    v.gi = i * R + col;
+    v.u = a.dst[v.gi];
+    v.gx = v.cx > 0 ? fb[(size_t)(1 * P2 + y + P * z) * R] : f0;
+    v.vx = v.cx > 0 && x == 0 ? fb[(size_t)(0 * P2 + y + P * z) * R] : f0;
+    v.gy = v.cy > 0 ? fb[(size_t)(3 * P2 + x + P * z) * R] : f0;
+    v.vy = v.cy > 0 && y == 0 ? fb[(size_t)(2 * P2 + x + P * z) * R] : f0;
+    v.gz = v.cz > 0 ? fb[(size_t)(5 * P2 + x + P * y) * R] : f0;
+    v.vz = v.cz > 0 && z == 0 ? fb[(size_t)(4 * P2 + x + P * y) * R] : f0;
+    v.eb = mode != EPI_STORE ? a.epi.b[v.gi] : 0.0;
+    v.edi = mode >= EPI_CHEB_FIRST ? a.epi.dinv[i] : 0.0;
+    v.ex = mode >= EPI_CHEB_FIRST ? a.epi.x[v.gi] : 0.0;
+    v.ed = mode == EPI_CHEB_STEP ? a.epi.d[v.gi] : 0.0;
+    return v;
+  };
+  // the slope part on every layer along the face normal (weight dphi_l(0)),
+  // the value part on layer 0; then the update
+  auto finish = [&](const In& v) {
+    const df uz = df_from_double(v.u);
     dacc s;
     s.h = uz.h;
     s.l = uz.l;
-    if (cx > 0) {
-      acc_mac(s, d0h[x], d0l[x], gx.x, gx.y);
-      if (x == 0) acc_add(s, df_make(vx.x, vx.y));
+    if (v.cx > 0) {
+      acc_mac(s, d0h[x], d0l[x], v.gx.x, v.gx.y);
+      if (x == 0) acc_add(s, df_make(v.vx.x, v.vx.y));
     }
-    if (cy > 0) {
-      acc_mac(s, d0h[y], d0l[y], gy.x, gy.y);
-      if (y == 0) acc_add(s, df_make(vy.x, vy.y));
+    if (v.cy > 0) {
+      acc_mac(s, d0h[y], d0l[y], v.gy.x, v.gy.y);
+      if (y == 0) acc_add(s, df_make(v.vy.x, v.vy.y));
     }
-    if (cz > 0) {
-      acc_mac(s, d0h[z], d0l[z], gz.x, gz.y);
-      if (z == 0) acc_add(s, df_make(vz.x, vz.y));
+    if (v.cz > 0) {
+      acc_mac(s, d0h[z], d0l[z], v.gz.x, v.gz.y);
+      if (z == 0) acc_add(s, df_make(v.vz.x, v.vz.y));
     }
-    epi_finish_df(a, gi, acc_get(s), eb, edi, ed, ex);
+    epi_finish_df(a, v.gi, acc_get(s), v.eb, v.edi, v.ed, v.ex);
+  };
+  // two rows per iteration, every load of both first
+  for (int row = blockIdx.y; row < rows; row += 2 * gridDim.y) {
+    const int row2 = row + gridDim.y;
+    const In v0 = load(row);
+    In v1;
+    if (row2 < rows) v1 = load(row2);
+    finish(v0);
+    if (row2 < rows) finish(v1);
   }
 }
 
@@ -1005,7 +1023,7 @@ void run_apply_df_cols(const ApplyArgsDF& a0, int R, int cells_req,
     MFP_REQUIRE(a0.fb, "SIPG face buffer missing");
     const int threads = 256;
     const int bx = (a0.n[0] * P2 * P + threads - 1) / threads;
-    const int rows = a0.n[1] * a0.n[2];
+    const int rows = (a0.n[1] * a0.n[2] + 1) / 2;  // two rows per block
     const int by = rows < 65535 ? rows : 65535;
     if (a0.ncells > 0) {
       k_dg_face_add<P><<<dim3(bx, by, R), threads, 0, s>>>(a0);
