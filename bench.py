@@ -440,11 +440,15 @@ def run_ours(args):
     ops = {d: make(d) for d in ("cg", "dg")}
     mixed = {d: make(d, mg_precision="fp32") for d in ("cg", "dg")}
     native = {d: make(d, fp64_arith="native") for d in ("cg", "dg")}
+    # cells per block of every level's applies (the coarse levels are
+    # latency-bound and may prefer other shapes than the finest)
     tuned = {}
     for d in ("cg", "dg"):
-        tuned["f64_" + d] = ops[d].autotune(prec="fp64")[0]
-        tuned["f64_native_" + d] = native[d].autotune(prec="fp64")[0]
-        tuned["f32_" + d] = mixed[d].autotune(prec="fp32")[0]
+        for tag, opx, pr in (("f64_", ops[d], "fp64"),
+                             ("f64_native_", native[d], "fp64"),
+                             ("f32_", mixed[d], "fp32")):
+            tuned[tag + d] = [opx.autotune(level=lv, prec=pr)[0]
+                              for lv in range(opx.n_levels - 1, 0, -1)]
     b = {d: ops[d].rhs(0) for d in ops}
     x = {d: torch.empty_like(b[d]) for d in ops}
     N = {d: ops[d].n_dofs() for d in ops}
