@@ -202,7 +202,7 @@ def apply_bytes(disc, k, n, curved, word=8):
 # the scope (12 sweeps of p^4 multiply-adds per cell, about 15 flops per
 # point, faces at the Cartesian cost); apply_flops also counts the curved
 # tangential face terms, so the line reports the fraction at both counts.
-SURVEY_DG_FLOPS_PER_DOF = {1: 156, 2: 165, 3: 182, 4: 201, 6: 244, 8: 289}
+SCOPE_DG_FLOPS_PER_DOF = {1: 156, 2: 165, 3: 182, 4: 201, 6: 244, 8: 289}
 
 
 def fp32_pipe_peak_tflops(sm_count, sm_mhz):
@@ -221,7 +221,7 @@ def fp64_pipe_peak_tflops(sm_count, sm_mhz):
 # DRAM traffic (read + write) per launch of the dominant kernel from one ncu
 # capture, keyed by a hash of the sources it was compiled from; a kernel
 # changed since its capture reports null.
-TRAFFIC = {"8b860ca0624869ae": 501.96e6}  # ncu, Q4 32^3 curved: k_apply_df + k_dg_face_add
+TRAFFIC = {"a9df6cdbb879da26": 502.05e6}  # ncu, Q4 32^3 curved: k_apply_df + k_dg_face_add
 
 
 def kernel_hash():
@@ -470,20 +470,24 @@ def run_ours(args):
     side = {d: torch.cuda.Stream() for d in ("cg", "dg")}
     pool = cf.ThreadPoolExecutor(max_workers=2)
 
-    def solve_on(opset, d, start):
+    def solve_on(opset, d, start, mark):
         torch.cuda.set_device(local)  # a worker thread's current device
         st_ = side[d]
         st_.wait_event(start)
+        if mark:  # NVTX ranges are per thread: the launch-list window
+            torch.cuda.nvtx.range_push("timed_step")
         _, it, rel = opset[d].solve(b[d], x[d], rtol=RTOL, max_it=200,
                                     stream=st_)
+        if mark:
+            torch.cuda.nvtx.range_pop()
         done = torch.cuda.Event()
         done.record(st_)
         return (it[0], rel[0]), done
 
-    def step(opset):
+    def step(opset, mark=False):
         start = torch.cuda.Event()
         start.record(stream)
-        futs = {d: pool.submit(solve_on, opset, d, start)
+        futs = {d: pool.submit(solve_on, opset, d, start, mark)
                 for d in ("cg", "dg")}
         its = {}
         for d, f in futs.items():
@@ -506,9 +510,7 @@ def run_ours(args):
         for i in range(args.steps):
             flush.fill_(float(i))
             starts[i].record(stream)
-            torch.cuda.nvtx.range_push("timed_step")  # launch-list window
-            its = step(ops)
-            torch.cuda.nvtx.range_pop()
+            its = step(ops, mark=True)
             ends[i].record(stream)
         torch.cuda.synchronize()
         if dist:
@@ -636,7 +638,7 @@ def run_ours(args):
     t_dom = dom["launch"]["mean_ms"] * 1e-3
     fl = apply_flops("dg", DEGREE, n ** 3, True)
     ach = DF_FLOPS_PER_FP64_FLOP * fl / t_dom / 1e12
-    fl_s = SURVEY_DG_FLOPS_PER_DOF[DEGREE] * N["dg"]
+    fl_s = SCOPE_DG_FLOPS_PER_DOF[DEGREE] * N["dg"]
     roof = {"kernel": "k_apply_df<P=5,DG,curved> + k_dg_face_add",
             "bound": "alu", "achieved": ach, "peak": p32, "unit": "TFLOP/s",
             "frac": ach / p32,
@@ -648,7 +650,7 @@ def run_ours(args):
                     "each face once with the curved tangential terms) x 7 "
                     "FP32-pipe flops per float64 flop (one double-float "
                     "multiply-add: FMUL + 3 FFMA + 8 FADD = 14 flops)",
-            "frac_at_survey_flop_count": (DF_FLOPS_PER_FP64_FLOP * fl_s
+            "frac_at_scope_flop_count": (DF_FLOPS_PER_FP64_FLOP * fl_s
                                           / t_dom / 1e12 / p32),
             "algorithmic_bytes": dom["algorithmic_bytes"],
             "hbm_frac": dom["hbm_frac"],

@@ -1104,10 +1104,11 @@ mfp_status mfp_solve(mfp_ctx* c, const double* b, double* x, int R,
   MFP_CHECK_CUDA(cudaStreamSynchronize(s));
   {
     int herr = 0;  // a staged kernel gave up waiting for its copies
-    MFP_CHECK_CUDA(cudaMemcpy(&herr, c->dev_err, sizeof(int),
-                              cudaMemcpyDeviceToHost));
+    MFP_CHECK_CUDA(cudaMemcpyAsync(&herr, c->dev_err, sizeof(int),
+                                   cudaMemcpyDeviceToHost, s));
+    MFP_CHECK_CUDA(cudaStreamSynchronize(s));
     if (herr) {
-      MFP_CHECK_CUDA(cudaMemset(c->dev_err, 0, sizeof(int)));
+      MFP_CHECK_CUDA(cudaMemsetAsync(c->dev_err, 0, sizeof(int), s));
       set_error("a kernel's shared-memory copy wait timed out; the result "
                 "is invalid");
       return MFP_ERR_CUDA;

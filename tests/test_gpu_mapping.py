@@ -69,3 +69,57 @@ def test_folded_mesh_is_rejected(mfp):
     with pytest.raises(mfp.MfpError) as e:
         mfp.Poisson(*n, k, mapping="nodes", map_nodes=nodes)
     assert e.value.status == mfp.MFP_ERR_ARG
+
+
+@pytest.mark.parametrize("disc", ["cg", "dg"])
+def test_neumann_sides_and_boundary_data(mfp, disc):
+    # given nodes with Neumann sides: the operator and the f_kind 2
+    # right-hand side (Dirichlet and Neumann data of a Gaussian sum) on the
+    # curved faces
+    n, k, sides = (3, 2, 3), 2, (0, 3)
+    nodes = synthetic.perturbed_lattice_nodes(n, k, seed=11)
+    op = mfp.Poisson(*n, k, disc=disc, mapping="nodes", map_nodes=nodes,
+                     n_levels=1, neumann_sides=sides)
+    P = fem.Problem(*n, k, disc=disc, mapping="nodes", map_nodes=nodes,
+                    neumann_sides=sides)
+    u = synthetic.random_vector(P.n_dofs, seed=12)
+    y = op.apply(torch.from_numpy(u).cuda()).cpu().numpy()
+    assert rel_err(y, fem.assemble(P) @ u) <= 1e-12
+    g = np.array([[0.3, 0.6, 0.4, 0.3, 1.5], [0.7, 0.2, 0.8, 0.25, -0.5]])
+    f = synthetic.gaussian_forcing(g)
+
+    def uex(x):
+        return f(x)
+
+    def grad(x):
+        out = np.zeros(x.shape)
+        for cx, cy, cz, w, a in g:
+            d = x - np.array([cx, cy, cz])
+            e = a * np.exp(-np.sum(d * d, -1) / w ** 2)
+            out += (-2.0 / w ** 2) * d * e[..., None]
+        return out
+
+    def lap(x):
+        out = np.zeros(x.shape[:-1])
+        for cx, cy, cz, w, a in g:
+            d = x - np.array([cx, cy, cz])
+            r2 = np.sum(d * d, -1)
+            out += a * np.exp(-r2 / w ** 2) * (4 * r2 / w ** 4 - 6 / w ** 2)
+        return -out
+    ref = fem.manufactured_rhs(P, lap, uex, grad)
+    got = op.rhs(2, g).cpu().numpy()
+    assert rel_err(got, ref) <= 1e-11
+
+
+def test_batched_apply_columns(mfp):
+    n, k, R = (3, 2, 2), 3, 4
+    nodes = synthetic.perturbed_lattice_nodes(n, k, seed=13)
+    op = mfp.Poisson(*n, k, disc="dg", mapping="nodes", map_nodes=nodes,
+                     n_levels=1)
+    N = op.n_dofs()
+    X = synthetic.random_vector(N, seed=14, ncols=R)
+    Y = op.apply(torch.from_numpy(np.ascontiguousarray(X)).cuda().reshape(-1),
+                 n_rhs=R).cpu().numpy().reshape(N, R)
+    for r in range(R):
+        y1 = op.apply(torch.from_numpy(X[:, r].copy()).cuda()).cpu().numpy()
+        assert rel_err(Y[:, r], y1) <= 1e-13
