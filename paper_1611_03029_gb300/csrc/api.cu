@@ -93,10 +93,10 @@ void epi_after(const Level& L, const T* y, T* dst, int R, const Epi<T>* epi,
     launch_residual<T>(epi->b, y, dst, n * R, s);
   else if (epi->mode == EPI_CHEB_FIRST)
     launch_cheb_first<T>(epi->b, epi->dinv, epi->d, epi->x, y, epi->c1, n, R,
-                         s, L.df_arith);
+                         s);
   else
     launch_cheb_step<T>(epi->b, epi->dinv, epi->d, epi->x, y, epi->c1,
-                        epi->c2, n, R, s, L.df_arith);
+                        epi->c2, n, R, s);
 }
 
 template <typename T>
@@ -185,7 +185,7 @@ void smooth(mfp_ctx* c, int l, const T* b, T* x, bool zero, int R,
   Epi<T> e{EPI_CHEB_FIRST, b, D.dinv, d, x, 1.0 / theta, 0.0};
   if (zero)
     launch_cheb_first<T>(b, D.dinv, d, x, nullptr, 1.0 / theta, L.ndofs, R,
-                         s, L.df_arith);
+                         s);
   else
     apply_level<T>(c, L, x, res, R, s, &e);
   for (int i = 1; i < L.cheb_degree; ++i) {

@@ -35,7 +35,11 @@ struct HdgArgs {
   int face_off[3];
   int neumann;  // bit 2d + s: side (d, s) has Neumann data
   double h[3];  // physical cell size (Cartesian cells)
+  double ih[3];  // 1 / h (host-computed: no float64 divisions per point)
+  double vol;    // h_x h_y h_z
+  double fa[3];  // area of a face normal to d: h_a h_b
   double kappa;  // constant coefficient (when kcell / kface are null)
+  double kinv;   // 1 / kappa
   double tau_factor;
   const double* __restrict__ kcell;  // [cell][p^3] or null
   const double* __restrict__ kface;  // [face][p^2] or null
@@ -212,10 +216,12 @@ constexpr size_t hdg_cell_smem() {
   return (size_t)(8 * P * P * P + 10 * P * P) * sizeof(double);
 }
 
-// Geometry of cell point t: w det J and J^{-1}[e][d] (row e, column d).
+// Geometry of cell point t: w det J and J^{-1}[e][d] (row e, column d); on
+// Cartesian cells from the block's table of w_q det J (sW3) and 1/h.
 template <int P, typename V>
 __device__ __forceinline__ void point_geo(const HdgArgs& a, int cell, int t,
-                                          const double* sw, V& wdet,
+                                          const typename HT<V>::S* sW3,
+                                          const V (&ih)[3], V& wdet,
                                           V (&Ji)[3][3]) {
   using H = HT<V>;
   constexpr int N = P * P * P;
@@ -225,11 +231,9 @@ __device__ __forceinline__ void point_geo(const HdgArgs& a, int cell, int t,
     for (int e = 0; e < 3; ++e)
       for (int d = 0; d < 3; ++d) Ji[e][d] = H::d2v(g[(1 + 3 * e + d) * N]);
   } else {
-    wdet = H::d2v(sw[t % P] * sw[(t / P) % P] * sw[t / (P * P)] * a.h[0] *
-                  a.h[1] * a.h[2]);
+    wdet = H::v(sW3[t]);
     for (int e = 0; e < 3; ++e)
-      for (int d = 0; d < 3; ++d)
-        Ji[e][d] = H::d2v(e == d ? 1.0 / a.h[d] : 0.0);
+      for (int d = 0; d < 3; ++d) Ji[e][d] = e == d ? ih[d] : H::d2v(0.0);
   }
 }
 
@@ -243,6 +247,7 @@ __global__ void k_hdg_cell(HdgArgs a) {
   using S = typename H::S;
   constexpr int F = P * P, N = P * P * P;
   __shared__ S sS[P * P], sD[P * P];
+  __shared__ S sW3[P * P * P], sW2[P * P];  // w_q det J (Cartesian), w_a w_b
   __shared__ double sw[P];
   extern __shared__ __align__(16) unsigned char hraw[];
   S* A = reinterpret_cast<S*>(hraw);
@@ -256,6 +261,16 @@ __global__ void k_hdg_cell(HdgArgs a) {
     sD[i] = H::s(H::d2v(c_tab64[P - 2].D[i]));
   }
   for (int i = threadIdx.x; i < P; i += blockDim.x) sw[i] = c_tab64[P - 2].w[i];
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const double* w = c_tab64[P - 2].w;
+    sW3[t] = H::s(H::d2v(w[t % P] * w[(t / P) % P] * w[t / (P * P)] * a.vol));
+  }
+  for (int q = threadIdx.x; q < F; q += blockDim.x) {
+    const double* w = c_tab64[P - 2].w;
+    sW2[q] = H::s(H::d2v(w[q % P] * w[q / P]));
+  }
+  const V ih[3] = {H::d2v(a.ih[0]), H::d2v(a.ih[1]), H::d2v(a.ih[2])};
+  const V kconst = H::d2v(a.kinv);
   const double* xc = a.x + (size_t)cell * 4 * N;
   for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) A[t] = H::s(H::d2v(xc[t]));
   __syncthreads();
@@ -271,10 +286,9 @@ __global__ void k_hdg_cell(HdgArgs a) {
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     const int ii[3] = {t % P, (t / P) % P, t / (P * P)};
     V wdet, Ji[3][3];
-    point_geo<P, V>(a, cell, t, sw, wdet, Ji);
+    point_geo<P, V>(a, cell, t, sW3, ih, wdet, Ji);
     const V kinv =
-        a.kcell ? H::recip(H::d2v(a.kcell[(size_t)cell * N + t]))
-                : H::d2v(1.0 / a.kappa);
+        a.kcell ? H::recip(H::d2v(a.kcell[(size_t)cell * N + t])) : kconst;
     V dv = H::d2v(0.0);
     for (int d = 0; d < 3; ++d) {
       for (int e = 0; e < 3; ++e) {
@@ -295,7 +309,7 @@ __global__ void k_hdg_cell(HdgArgs a) {
   for (int d = 0; d < 3; ++d) {
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
       V wdet, Ji[3][3];
-      point_geo<P, V>(a, cell, t, sw, wdet, Ji);
+      point_geo<P, V>(a, cell, t, sW3, ih, wdet, Ji);
       for (int e = 0; e < 3; ++e)
         B[e * N + t] = H::s(wdet * Ji[e][d] * H::v(B[3 * N + t]));
     }
@@ -325,7 +339,6 @@ __global__ void k_hdg_cell(HdgArgs a) {
   S* gcf = FS + 2 * F;  // [w_x, w_y, w_z, v] terms at the face points
   S* gt = FS + 6 * F;   // sweep temporary for the four fields
   for (int D = 0; D < 3; ++D) {
-    const int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
     int m[3] = {a.n[0], a.n[1], a.n[2]};
     m[D] += 1;
     for (int s = 0; s < 2; ++s) {
@@ -348,7 +361,7 @@ __global__ void k_hdg_cell(HdgArgs a) {
           for (int e = 0; e < 3; ++e)
             nv[e] = H::d2v(a.gf[(f * 4 + 1 + e) * F + q]);
         } else {
-          dA = H::d2v(sw[q % P] * sw[q / P] * a.h[T1] * a.h[T2]);
+          dA = H::v(sW2[q]) * H::d2v(a.fa[D]);
           nv[D] = H::d2v(1.0);
         }
         // outward normal: +n on the upper face (s = 1), -n on the lower one
@@ -414,6 +427,12 @@ void launch_hdg_apply(const Level& L, double tau_factor, double* lam,
   }
   a.neumann = L.bc.neumann;
   a.kappa = L.kappa;
+  a.kinv = 1.0 / L.kappa;
+  for (int d = 0; d < 3; ++d) a.ih[d] = 1.0 / L.h[d];
+  a.vol = L.h[0] * L.h[1] * L.h[2];
+  a.fa[0] = L.h[1] * L.h[2];
+  a.fa[1] = L.h[0] * L.h[2];
+  a.fa[2] = L.h[0] * L.h[1];
   a.tau_factor = tau_factor;
   a.kcell = L.d64.kcell;
   a.kface = L.d64.kface;

@@ -87,45 +87,6 @@ __global__ void k_cheb_step(const T* __restrict__ b,
   }
 }
 
-// The same two updates for the float64 vectors of a double-float context, in
-// double-float arithmetic on the FP32 pipes: at 5 operations per entry the
-// FP64 pipe would hold them to about the memory rate.  Inputs are split with
-// integer operations; each float64 output takes one FP64 addition.
-__global__ void k_cheb_first_df(const double* __restrict__ b,
-                                const double* __restrict__ dinv,
-                                double* __restrict__ d, double* __restrict__ x,
-                                const double* __restrict__ ax, df c, int64_t n,
-                                int nrhs) {
-  GRID_STRIDE(i, n * nrhs) {
-    df r = df_from_double(b[i]);
-    if (ax) r = r - df_from_double(ax[i]);
-    const df di = c * (df_from_double(dinv[nrhs == 1 ? i : i / nrhs]) * r);
-    d[i] = df_to_double(di);
-    x[i] = ax ? df_to_double(df_from_double(x[i]) + di) : df_to_double(di);
-  }
-}
-
-__global__ void k_cheb_step_df(const double* __restrict__ b,
-                               const double* __restrict__ dinv,
-                               double* __restrict__ d, double* __restrict__ x,
-                               const double* __restrict__ ax, df cd, df cr,
-                               int64_t n, int nrhs) {
-  GRID_STRIDE(i, n * nrhs) {
-    const df r = df_from_double(b[i]) - df_from_double(ax[i]);
-    const df di = cd * df_from_double(d[i]) +
-                  cr * (df_from_double(dinv[nrhs == 1 ? i : i / nrhs]) * r);
-    d[i] = df_to_double(di);
-    x[i] = df_to_double(df_from_double(x[i]) + di);
-  }
-}
-
-inline df host_pair(double v) {
-  df r;
-  r.h = (float)v;
-  r.l = (float)(v - (double)r.h);
-  return r;
-}
-
 template <typename T>
 __global__ void k_residual(const T* b, const T* ax, T* r, int64_t n) {
   GRID_STRIDE(i, n) r[i] = b[i] - ax[i];
@@ -620,17 +581,7 @@ void launch_to_double(const float* a, double* b, int64_t n, cudaStream_t s) {
 
 template <typename T>
 void launch_cheb_first(const T* b, const T* dinv, T* d, T* x, const T* ax,
-                       double c, int64_t n, int nrhs, cudaStream_t s,
-                       bool dfa) {
-  if constexpr (std::is_same<T, double>::value) {
-    if (dfa) {
-      k_cheb_first_df<<<vec_grid(n * nrhs), kVecThreads, 0, s>>>(
-          b, dinv, d, x, ax, host_pair(c), n, nrhs);
-      MFP_CHECK_CUDA(cudaGetLastError());
-      note_launch();
-      return;
-    }
-  }
+                       double c, int64_t n, int nrhs, cudaStream_t s) {
   k_cheb_first<T><<<vec_grid(n * nrhs), kVecThreads, 0, s>>>(b, dinv, d, x,
                                                               ax, (T)c, n,
                                                               nrhs);
@@ -640,16 +591,7 @@ void launch_cheb_first(const T* b, const T* dinv, T* d, T* x, const T* ax,
 template <typename T>
 void launch_cheb_step(const T* b, const T* dinv, T* d, T* x, const T* ax,
                       double cd, double cr, int64_t n, int nrhs,
-                      cudaStream_t s, bool dfa) {
-  if constexpr (std::is_same<T, double>::value) {
-    if (dfa) {
-      k_cheb_step_df<<<vec_grid(n * nrhs), kVecThreads, 0, s>>>(
-          b, dinv, d, x, ax, host_pair(cd), host_pair(cr), n, nrhs);
-      MFP_CHECK_CUDA(cudaGetLastError());
-      note_launch();
-      return;
-    }
-  }
+                      cudaStream_t s) {
   k_cheb_step<T><<<vec_grid(n * nrhs), kVecThreads, 0, s>>>(
       b, dinv, d, x, ax, (T)cd, (T)cr, n, nrhs);
   MFP_CHECK_CUDA(cudaGetLastError());
@@ -670,11 +612,10 @@ void launch_axpy(T* y, const T* x, double a, int64_t n, cudaStream_t s) {
 }
 #define INST_VEC(T)                                                           \
   template void launch_cheb_first<T>(const T*, const T*, T*, T*, const T*,   \
-                                     double, int64_t, int, cudaStream_t,      \
-                                     bool);                                   \
+                                     double, int64_t, int, cudaStream_t);     \
   template void launch_cheb_step<T>(const T*, const T*, T*, T*, const T*,    \
                                     double, double, int64_t, int,            \
-                                    cudaStream_t, bool);                      \
+                                    cudaStream_t);                            \
   template void launch_residual<T>(const T*, const T*, T*, int64_t,          \
                                    cudaStream_t);                             \
   template void launch_axpy<T>(T*, const T*, double, int64_t, cudaStream_t);

@@ -394,15 +394,13 @@ template <typename T>
 void launch_dense_apply(const T* A, const T* x, T* y, int n, int R,
                         double* part, unsigned* cnt, cudaStream_t s);
 void launch_to_double(const float* a, double* b, int64_t n, cudaStream_t s);
-// dfa: float64 vectors of a double-float context (double-float arithmetic)
 template <typename T>
 void launch_cheb_first(const T* b, const T* dinv, T* d, T* x, const T* ax,
-                       double c, int64_t n, int nrhs, cudaStream_t s,
-                       bool dfa = false);
+                       double c, int64_t n, int nrhs, cudaStream_t s);
 template <typename T>
 void launch_cheb_step(const T* b, const T* dinv, T* d, T* x, const T* ax,
                       double cd, double cr, int64_t n, int nrhs,
-                      cudaStream_t s, bool dfa = false);
+                      cudaStream_t s);
 template <typename T>
 void launch_residual(const T* b, const T* ax, T* r, int64_t n,
                      cudaStream_t s);
