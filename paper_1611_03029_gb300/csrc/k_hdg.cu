@@ -152,7 +152,7 @@ __device__ __forceinline__ int layer_node(int D, int s, int ja, int jb) {
 //   lambda = sum_sides (q . n_out + tau u) / (tau * number of sides),
 // n_out the side's outward unit normal (+n for the cell below the face, -n
 // for the one above; n = e_D on Cartesian cells).
-template <int P, typename V, bool CURVED>
+template <int P, typename V>
 __global__ void k_hdg_trace(HdgArgs a, int D) {
   using H = HT<V>;
   using S = typename H::S;
@@ -194,7 +194,7 @@ __global__ void k_hdg_trace(HdgArgs a, int D) {
                                 face_tau<P>(a, f)));
   for (int q = threadIdx.x; q < F; q += blockDim.x) {
     V nv[3] = {H::d2v(0.0), H::d2v(0.0), H::d2v(0.0)};
-    if constexpr (CURVED) {
+    if (a.gf) {
       for (int e = 0; e < 3; ++e) nv[e] = H::d2v(a.gf[(f * 4 + 1 + e) * F + q]);
     } else {
       nv[D] = H::d2v(1.0);
@@ -218,14 +218,14 @@ constexpr size_t hdg_cell_smem() {
 
 // Geometry of cell point t: w det J and J^{-1}[e][d] (row e, column d); on
 // Cartesian cells from the block's table of w_q det J (sW3) and 1/h.
-template <int P, typename V, bool CURVED>
+template <int P, typename V>
 __device__ __forceinline__ void point_geo(const HdgArgs& a, int cell, int t,
                                           const typename HT<V>::S* sW3,
                                           const V (&ih)[3], V& wdet,
                                           V (&Ji)[3][3]) {
   using H = HT<V>;
   constexpr int N = P * P * P;
-  if constexpr (CURVED) {
+  if (a.gc) {
     const double* g = a.gc + (size_t)cell * 10 * N + t;
     wdet = H::d2v(g[0]);
     for (int e = 0; e < 3; ++e)
@@ -241,7 +241,7 @@ __device__ __forceinline__ void point_geo(const HdgArgs& a, int cell, int t,
 // Gauss points (w det = w_q det J, J^{-1} = dxi/dx):
 //   q_d rows: w det kappa^-1 q_d - sum_e D_e^T (w det J^{-1}[e][d] u)
 //   u rows:   -w det sum_{d,e} J^{-1}[e][d] D_e q_d
-template <int P, typename V, bool CURVED>
+template <int P, typename V>
 __global__ void k_hdg_cell(HdgArgs a) {
   using H = HT<V>;
   using S = typename H::S;
@@ -286,13 +286,13 @@ __global__ void k_hdg_cell(HdgArgs a) {
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     const int ii[3] = {t % P, (t / P) % P, t / (P * P)};
     V wdet, Ji[3][3];
-    point_geo<P, V, CURVED>(a, cell, t, sW3, ih, wdet, Ji);
+    point_geo<P, V>(a, cell, t, sW3, ih, wdet, Ji);
     const V kinv =
         a.kcell ? H::recip(H::d2v(a.kcell[(size_t)cell * N + t])) : kconst;
     V dv = H::d2v(0.0);
     for (int d = 0; d < 3; ++d) {
       for (int e = 0; e < 3; ++e) {
-        if (!CURVED && e != d) continue;
+        if (!a.gc && e != d) continue;
         const int base = t - ii[e] * st[e];
         typename H::Acc s1 = H::zero();
         for (int j = 0; j < P; ++j)
@@ -309,7 +309,7 @@ __global__ void k_hdg_cell(HdgArgs a) {
   for (int d = 0; d < 3; ++d) {
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
       V wdet, Ji[3][3];
-      point_geo<P, V, CURVED>(a, cell, t, sW3, ih, wdet, Ji);
+      point_geo<P, V>(a, cell, t, sW3, ih, wdet, Ji);
       for (int e = 0; e < 3; ++e)
         B[e * N + t] = H::s(wdet * Ji[e][d] * H::v(B[3 * N + t]));
     }
@@ -318,7 +318,7 @@ __global__ void k_hdg_cell(HdgArgs a) {
       const int ii[3] = {t % P, (t / P) % P, t / (P * P)};
       typename H::Acc s2 = H::zero();
       for (int e = 0; e < 3; ++e) {
-        if (!CURVED && e != d) continue;
+        if (!a.gc && e != d) continue;
         const int base = t - ii[e] * st[e];
         for (int j = 0; j < P; ++j)
           H::mac(s2, sD[j * P + ii[e]], B[e * N + base + j * st[e]]);
@@ -356,7 +356,7 @@ __global__ void k_hdg_cell(HdgArgs a) {
       const V tau = H::d2v(face_tau<P>(a, f));
       for (int q = threadIdx.x; q < F; q += blockDim.x) {
         V dA, nv[3] = {H::d2v(0.0), H::d2v(0.0), H::d2v(0.0)};
-        if constexpr (CURVED) {
+        if (a.gf) {
           dA = H::d2v(a.gf[(f * 4) * F + q]);
           for (int e = 0; e < 3; ++e)
             nv[e] = H::d2v(a.gf[(f * 4 + 1 + e) * F + q]);
@@ -388,23 +388,23 @@ __global__ void k_hdg_cell(HdgArgs a) {
   for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) yc[t] = H::v2d(H::v(B[t]));
 }
 
-template <typename V, bool CURVED>
+template <typename V>
 void run_hdg(const Level& L, const HdgArgs& a, cudaStream_t s) {
   dispatch_p(L.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;
     for (int D = 0; D < 3; ++D) {
       int m[3] = {L.n[0], L.n[1], L.n[2]};
       m[D] += 1;
-      k_hdg_trace<P, V, CURVED><<<m[0] * m[1] * m[2], 64, 0, s>>>(a, D);
+      k_hdg_trace<P, V><<<m[0] * m[1] * m[2], 64, 0, s>>>(a, D);
       MFP_CHECK_CUDA(cudaGetLastError());
       note_launch();
     }
     constexpr size_t smem = hdg_cell_smem<P>();
     if (smem > 48 * 1024)
       MFP_CHECK_CUDA(cudaFuncSetAttribute(
-          k_hdg_cell<P, V, CURVED>,
-          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_hdg_cell<P, V, CURVED><<<(int)L.ncells, 128, smem, s>>>(a);
+          k_hdg_cell<P, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          (int)smem));
+    k_hdg_cell<P, V><<<(int)L.ncells, 128, smem, s>>>(a);
     MFP_CHECK_CUDA(cudaGetLastError());
     note_launch();
   });
@@ -438,18 +438,10 @@ void launch_hdg_apply(const Level& L, double tau_factor, double* lam,
   a.kface = L.d64.kface;
   a.gc = hdg_cell;
   a.gf = hdg_face;
-  const bool curved = hdg_cell != nullptr;
-  if (L.df_arith) {
-    if (curved)
-      run_hdg<df, true>(L, a, s);
-    else
-      run_hdg<df, false>(L, a, s);
-  } else {
-    if (curved)
-      run_hdg<double, true>(L, a, s);
-    else
-      run_hdg<double, false>(L, a, s);
-  }
+  if (L.df_arith)
+    run_hdg<df>(L, a, s);
+  else
+    run_hdg<double>(L, a, s);
 }
 
 }  // namespace mfp
