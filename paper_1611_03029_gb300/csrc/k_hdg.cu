@@ -11,7 +11,7 @@
 // as the Gauss rule, so its inverse acts point by point; on a curved face
 // both sides see the same area element); it is zero on Dirichlet faces,
 // whose traces are data.  k_hdg_trace (one block per face) forms lambda,
-// k_hdg_cell (one block per cell) adds the cell integrals by sum
+// k_hdg_cell (a few cells per block) adds the cell integrals by sum
 // factorization (values at the Gauss points by S, reference derivatives by
 // the Gauss collocation matrix D, mapped by J^{-1}) and the six faces' terms
 // -<v, tau u> + <w . n, lambda> + <v, tau lambda> on the face-layer nodes.
@@ -211,9 +211,17 @@ __global__ void k_hdg_trace(HdgArgs a, int D) {
   }
 }
 
+// Shared memory of one cell of the cell kernel: A and B (4 fields of p^3
+// values each) and the face scratch (10 p^2 values).
 template <int P>
-constexpr size_t hdg_cell_smem() {
+constexpr size_t hdg_cell_bytes() {
   return (size_t)(8 * P * P * P + 10 * P * P) * sizeof(double);
+}
+// Cells per block: several cells share each barrier interval, up to 40 KB.
+template <int P>
+constexpr int hdg_cells_per_block() {
+  const int c = (int)((40 * 1024) / hdg_cell_bytes<P>());
+  return c < 1 ? 1 : (c > 16 ? 16 : c);
 }
 
 // Geometry of cell point t: w det J and J^{-1}[e][d] (row e, column d); on
@@ -237,7 +245,10 @@ __device__ __forceinline__ void point_geo(const HdgArgs& a, int cell, int t,
   }
 }
 
-// One block per cell: cell integrals and the terms of its six faces.  At the
+// Cell kernel: a block takes C = hdg_cells_per_block<P>() consecutive cells,
+// their cell integrals and the terms of their six faces.  The C cells' four
+// fields lie one after the other in shared memory, so every sweep runs over
+// 4 C fields at once and each barrier interval holds C cells' work.  At the
 // Gauss points (w det = w_q det J, J^{-1} = dxi/dx):
 //   q_d rows: w det kappa^-1 q_d - sum_e D_e^T (w det J^{-1}[e][d] u)
 //   u rows:   -w det sum_{d,e} J^{-1}[e][d] D_e q_d
@@ -245,17 +256,18 @@ template <int P, typename V>
 __global__ void k_hdg_cell(HdgArgs a) {
   using H = HT<V>;
   using S = typename H::S;
-  constexpr int F = P * P, N = P * P * P;
+  constexpr int F = P * P, N = P * P * P, C = hdg_cells_per_block<P>();
   __shared__ S sS[P * P], sD[P * P];
   __shared__ S sW3[P * P * P], sW2[P * P];  // w_q det J (Cartesian), w_a w_b
   __shared__ double sw[P];
   extern __shared__ __align__(16) unsigned char hraw[];
-  S* A = reinterpret_cast<S*>(hraw);
-  S* B = A + 4 * N;
-  S* FS = A + 8 * N;
-  const int cell = blockIdx.x;
-  const int c3[3] = {cell % a.n[0], (cell / a.n[0]) % a.n[1],
-                     cell / (a.n[0] * a.n[1])};
+  S* A = reinterpret_cast<S*>(hraw);  // [C][4][N]
+  S* B = A + 4 * C * N;                 // [C][4][N]
+  S* ul = B + 4 * C * N;                // [C][F]: u layer, then u at the points
+  S* ut = ul + C * F;                   // [C][F]: sweep temporary
+  S* gcf = ut + C * F;                  // [C][4][F]: w_x, w_y, w_z, v terms
+  S* gt = gcf + 4 * C * F;              // [C][4][F]: sweep temporary
+  const int cell0 = blockIdx.x * C;
   for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
     sS[i] = H::s(H::d2v(c_tab64[P - 2].S[i]));
     sD[i] = H::s(H::d2v(c_tab64[P - 2].D[i]));
@@ -271,19 +283,27 @@ __global__ void k_hdg_cell(HdgArgs a) {
   }
   const V ih[3] = {H::d2v(a.ih[0]), H::d2v(a.ih[1]), H::d2v(a.ih[2])};
   const V kconst = H::d2v(a.kinv);
-  const double* xc = a.x + (size_t)cell * 4 * N;
-  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) A[t] = H::s(H::d2v(xc[t]));
+  const int ncells = a.n[0] * a.n[1] * a.n[2];
+  // cells past the last one compute on zeros and store nothing
+  for (int t = threadIdx.x; t < 4 * C * N; t += blockDim.x) {
+    const int cell = cell0 + t / (4 * N);
+    A[t] = H::s(H::d2v(cell < ncells ? a.x[(size_t)cell0 * 4 * N + t] : 0.0));
+  }
   __syncthreads();
   // values of the four fields at the Gauss points
-  sweep3<P, V>(sS, false, 0, A, B, 4);
+  sweep3<P, V>(sS, false, 0, A, B, 4 * C);
   __syncthreads();
-  sweep3<P, V>(sS, false, 1, B, A, 4);
+  sweep3<P, V>(sS, false, 1, B, A, 4 * C);
   __syncthreads();
-  sweep3<P, V>(sS, false, 2, A, B, 4);
+  sweep3<P, V>(sS, false, 2, A, B, 4 * C);
   __syncthreads();
   const int st[3] = {1, P, P * P};
   // u rows and the mass part of the q rows
-  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+  for (int tt = threadIdx.x; tt < C * N; tt += blockDim.x) {
+    const int c = tt / N, t = tt - c * N;
+    const int cell = cell0 + c < ncells ? cell0 + c : ncells - 1;
+    S* Ac = A + c * 4 * N;
+    const S* Bc = B + c * 4 * N;
     const int ii[3] = {t % P, (t / P) % P, t / (P * P)};
     V wdet, Ji[3][3];
     point_geo<P, V>(a, cell, t, sW3, ih, wdet, Ji);
@@ -296,65 +316,76 @@ __global__ void k_hdg_cell(HdgArgs a) {
         const int base = t - ii[e] * st[e];
         typename H::Acc s1 = H::zero();
         for (int j = 0; j < P; ++j)
-          H::mac(s1, sD[ii[e] * P + j], B[d * N + base + j * st[e]]);
+          H::mac(s1, sD[ii[e] * P + j], Bc[d * N + base + j * st[e]]);
         dv = dv + Ji[e][d] * H::get(s1);
       }
-      A[d * N + t] = H::s(wdet * kinv * H::v(B[d * N + t]));
+      Ac[d * N + t] = H::s(wdet * kinv * H::v(Bc[d * N + t]));
     }
-    A[3 * N + t] = H::s(V(-(wdet * dv)));
+    Ac[3 * N + t] = H::s(V(-(wdet * dv)));
   }
   __syncthreads();
   // -sum_e D_e^T (w det J^{-1}[e][d] u) into the q_d rows, one d at a time
   // (the q values at the points in B are no longer needed)
   for (int d = 0; d < 3; ++d) {
-    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    for (int tt = threadIdx.x; tt < C * N; tt += blockDim.x) {
+      const int c = tt / N, t = tt - c * N;
+      const int cell = cell0 + c < ncells ? cell0 + c : ncells - 1;
+      S* Bc = B + c * 4 * N;
       V wdet, Ji[3][3];
       point_geo<P, V>(a, cell, t, sW3, ih, wdet, Ji);
       for (int e = 0; e < 3; ++e)
-        B[e * N + t] = H::s(wdet * Ji[e][d] * H::v(B[3 * N + t]));
+        Bc[e * N + t] = H::s(wdet * Ji[e][d] * H::v(Bc[3 * N + t]));
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    for (int tt = threadIdx.x; tt < C * N; tt += blockDim.x) {
+      const int c = tt / N, t = tt - c * N;
+      S* Ac = A + c * 4 * N;
+      const S* Bc = B + c * 4 * N;
       const int ii[3] = {t % P, (t / P) % P, t / (P * P)};
       typename H::Acc s2 = H::zero();
       for (int e = 0; e < 3; ++e) {
         if (!a.gc && e != d) continue;
         const int base = t - ii[e] * st[e];
         for (int j = 0; j < P; ++j)
-          H::mac(s2, sD[j * P + ii[e]], B[e * N + base + j * st[e]]);
+          H::mac(s2, sD[j * P + ii[e]], Bc[e * N + base + j * st[e]]);
       }
-      A[d * N + t] = H::s(H::v(A[d * N + t]) - H::get(s2));
+      Ac[d * N + t] = H::s(H::v(Ac[d * N + t]) - H::get(s2));
     }
     __syncthreads();
   }
-  sweep3<P, V>(sS, true, 2, A, B, 4);
+  sweep3<P, V>(sS, true, 2, A, B, 4 * C);
   __syncthreads();
-  sweep3<P, V>(sS, true, 1, B, A, 4);
+  sweep3<P, V>(sS, true, 1, B, A, 4 * C);
   __syncthreads();
-  sweep3<P, V>(sS, true, 0, A, B, 4);
+  sweep3<P, V>(sS, true, 0, A, B, 4 * C);
   __syncthreads();
-  // faces: scratch FS (10 p^2 values)
-  S* ul = FS;           // u layer, then u at the face points
-  S* ut = FS + F;       // sweep temporary
-  S* gcf = FS + 2 * F;  // [w_x, w_y, w_z, v] terms at the face points
-  S* gt = FS + 6 * F;   // sweep temporary for the four fields
+  // faces, one (direction, side) at a time for all C cells of the block
   for (int D = 0; D < 3; ++D) {
     int m[3] = {a.n[0], a.n[1], a.n[2]};
     m[D] += 1;
     for (int s = 0; s < 2; ++s) {
-      int fc[3] = {c3[0], c3[1], c3[2]};
-      fc[D] += s;
-      const size_t f = (size_t)a.face_off[D] + fc[0] +
-                       (size_t)m[0] * (fc[1] + (size_t)m[1] * fc[2]);
-      for (int j = threadIdx.x; j < F; j += blockDim.x)
-        ul[j] = H::s(H::d2v(xc[3 * N + layer_node<P>(D, s, j % P, j / P)]));
+      for (int tt = threadIdx.x; tt < C * F; tt += blockDim.x) {
+        const int c = tt / F, j = tt - c * F;
+        const int cell = cell0 + c;
+        ul[tt] = H::s(H::d2v(
+            cell < ncells ? a.x[(size_t)cell * 4 * N + 3 * N +
+                                layer_node<P>(D, s, j % P, j / P)]
+                          : 0.0));
+      }
       __syncthreads();
-      sweep2<P, V>(sS, false, 0, ul, ut, 1);
+      sweep2<P, V>(sS, false, 0, ul, ut, C);
       __syncthreads();
-      sweep2<P, V>(sS, false, 1, ut, ul, 1);
+      sweep2<P, V>(sS, false, 1, ut, ul, C);
       __syncthreads();
-      const V tau = H::d2v(face_tau<P>(a, f));
-      for (int q = threadIdx.x; q < F; q += blockDim.x) {
+      for (int tt = threadIdx.x; tt < C * F; tt += blockDim.x) {
+        const int c = tt / F, q = tt - c * F;
+        const int cell = cell0 + c < ncells ? cell0 + c : ncells - 1;
+        int fc[3] = {cell % a.n[0], (cell / a.n[0]) % a.n[1],
+                     cell / (a.n[0] * a.n[1])};
+        fc[D] += s;
+        const size_t f = (size_t)a.face_off[D] + fc[0] +
+                         (size_t)m[0] * (fc[1] + (size_t)m[1] * fc[2]);
+        const V tau = H::d2v(face_tau<P>(a, f));
         V dA, nv[3] = {H::d2v(0.0), H::d2v(0.0), H::d2v(0.0)};
         if (a.gf) {
           dA = H::d2v(a.gf[(f * 4) * F + q]);
@@ -367,25 +398,30 @@ __global__ void k_hdg_cell(HdgArgs a) {
         // outward normal: +n on the upper face (s = 1), -n on the lower one
         const V lq = H::d2v(a.lam[f * F + q]);
         const V dl = s ? V(dA * lq) : V(-(dA * lq));
+        S* g = gcf + c * 4 * F;
         for (int e = 0; e < 3; ++e)
-          gcf[e * F + q] = H::s(dl * nv[e]);              // <w . n, lambda>
-        gcf[3 * F + q] = H::s(dA * tau * (lq - H::v(ul[q])));  // <v, tau(lambda-u)>
+          g[e * F + q] = H::s(dl * nv[e]);                       // <w . n, lambda>
+        g[3 * F + q] = H::s(dA * tau * (lq - H::v(ul[tt])));     // <v, tau(lambda-u)>
       }
       __syncthreads();
-      sweep2<P, V>(sS, true, 1, gcf, gt, 4);
+      sweep2<P, V>(sS, true, 1, gcf, gt, 4 * C);
       __syncthreads();
-      sweep2<P, V>(sS, true, 0, gt, gcf, 4);
+      sweep2<P, V>(sS, true, 0, gt, gcf, 4 * C);
       __syncthreads();
-      for (int j = threadIdx.x; j < F; j += blockDim.x) {
+      for (int tt = threadIdx.x; tt < C * F; tt += blockDim.x) {
+        const int c = tt / F, j = tt - c * F;
         const int loc = layer_node<P>(D, s, j % P, j / P);
+        S* Bc = B + c * 4 * N;
+        const S* g = gcf + c * 4 * F;
         for (int e = 0; e < 4; ++e)
-          B[e * N + loc] = H::s(H::v(B[e * N + loc]) + H::v(gcf[e * F + j]));
+          Bc[e * N + loc] = H::s(H::v(Bc[e * N + loc]) + H::v(g[e * F + j]));
       }
       __syncthreads();
     }
   }
-  double* yc = a.y + (size_t)cell * 4 * N;
-  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) yc[t] = H::v2d(H::v(B[t]));
+  for (int t = threadIdx.x; t < 4 * C * N; t += blockDim.x)
+    if (cell0 + t / (4 * N) < ncells)
+      a.y[(size_t)cell0 * 4 * N + t] = H::v2d(H::v(B[t]));
 }
 
 template <typename V>
@@ -399,12 +435,14 @@ void run_hdg(const Level& L, const HdgArgs& a, cudaStream_t s) {
       MFP_CHECK_CUDA(cudaGetLastError());
       note_launch();
     }
-    constexpr size_t smem = hdg_cell_smem<P>();
+    constexpr int C = hdg_cells_per_block<P>();
+    constexpr size_t smem = C * hdg_cell_bytes<P>();
     if (smem > 48 * 1024)
       MFP_CHECK_CUDA(cudaFuncSetAttribute(
           k_hdg_cell<P, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
           (int)smem));
-    k_hdg_cell<P, V><<<(int)L.ncells, 128, smem, s>>>(a);
+    const int blocks = (int)((L.ncells + C - 1) / C);
+    k_hdg_cell<P, V><<<blocks, C > 1 ? 256 : 128, smem, s>>>(a);
     MFP_CHECK_CUDA(cudaGetLastError());
     note_launch();
   });
