@@ -15,6 +15,8 @@
 // the upper neighbour's share in a face buffer that k_dg_face_add_t adds.
 #pragma once
 
+#include <map>
+
 #include "bulk_copy.cuh"
 #include "dev_tables.cuh"
 
@@ -46,6 +48,7 @@ struct ApplyArgs {
   int col;     // first column of this launch
   int cpb;     // cells per block
   int ncols;   // columns per block
+  int cs;      // shared-memory stride of a virtual cell (pick_cell_stride)
   Epi<T> epi;  // SIPG: update fused into k_dg_face_add_t
   int* err;    // set to 1 by a staged kernel whose copy wait timed out
 };
@@ -55,15 +58,141 @@ __device__ __forceinline__ int idx3(int x, int y, int z) {
   return x + P * (y + P * z);
 }
 
-// Shared-memory stride of one virtual cell, odd so that the columns of a
-// batch (adjacent threads, one virtual cell each) fall into distinct banks.
-template <typename T, int P, bool DG>
-__host__ __device__ constexpr int cell_smem_elems() {
-  return ((DG ? 4 : 3) * P * P * P + (DG ? 8 * P * P : 0)) | 1;
+// Shared-memory layout of a virtual cell.  Its arrays of p^3 values are
+// indexed x + p y + zs z, with the z stride padded (lay_zs) so that the
+// lines of all three sweep directions spread over the 32 banks; a cell holds
+// Aq, GX, GY (SIPG also U and the face scratch of 8 p^2 values) at multiples
+// of the array size lay_arr, and the virtual cells of a block follow each
+// other at a cell stride chosen per launch shape (pick_cell_stride).
+template <int P>
+__host__ __device__ constexpr int lay_zs() {
+  return P == 2 ? 5 : P == 3 ? 11 : P == 4 ? 19 : P == 5 ? 29
+       : P == 6 ? 37 : P == 7 ? 53 : P == 8 ? 65 : 85;
+}
+template <int P>
+__host__ __device__ constexpr int lay_arr() {
+  return (P - 1) * (1 + P + lay_zs<P>()) + 1;
+}
+template <int P>
+__host__ __device__ constexpr int sidx(int x, int y, int z) {
+  return x + P * y + lay_zs<P>() * z;
+}
+template <int P, bool DG>
+__host__ __device__ constexpr int cell_min_elems() {
+  return (DG ? 4 : 3) * lay_arr<P>() + (DG ? 8 * P * P : 0);
 }
 template <int P>
 __host__ __device__ constexpr int table_smem_elems() {
   return 3 * P * P + 3 * P;
+}
+
+// Shared-memory wavefronts above one per warp access that a launch shape
+// (cpb cells x nc columns per block, p^2 threads per virtual cell, columns
+// adjacent) would cost at cell stride cs: the z-lines, one per thread in
+// thread order, plus the y- and x-lines that the greedy assignment of
+// assign_line cannot give a bank of their own.
+template <int P>
+int layout_conflicts(int cpb, int nc, int cs) {
+  constexpr int P2 = P * P, ZS = lay_zs<P>();
+  const int items = cpb * nc * P2, nthr = (items + 31) / 32 * 32,
+            nw = nthr / 32;
+  int cost = 0;
+  for (int w = 0; w < nw; ++w) {  // z-lines: distinct starts per bank
+    int addr[32], n = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int t = w * 32 + l;
+      if (t >= items) break;
+      const int rest = t / nc, rr = t % nc, m = rest % P2;
+      addr[n++] = ((rest / P2) * nc + rr) * cs + m % P + P * (m / P);
+    }
+    int worst = 0;
+    for (int b = 0; b < 32; ++b) {
+      int cnt = 0;
+      for (int i = 0; i < n; ++i) {
+        if ((addr[i] & 31) != b) continue;
+        bool dup = false;
+        for (int j = 0; j < i; ++j) dup |= addr[j] == addr[i];
+        cnt += !dup;
+      }
+      worst = cnt > worst ? cnt : worst;
+    }
+    cost += worst > 1 ? (worst - 1) * 32 : 0;
+  }
+  for (int mode = 0; mode < 2; ++mode) {  // y-, x-lines: per bank <= nw
+    int cnt[32] = {0};
+    for (int v = 0; v < cpb * nc; ++v)
+      for (int m = 0; m < P2; ++m) {
+        const int a = m % P, b = m / P;
+        ++cnt[(v * cs + (mode == 0 ? a + ZS * b : P * a + ZS * b)) & 31];
+      }
+    for (int b = 0; b < 32; ++b) cost += cnt[b] > nw ? cnt[b] - nw : 0;
+  }
+  return cost;
+}
+
+// Cell stride of a launch shape: of the 32 strides from the cell's size up,
+// the one with the fewest bank conflicts (cached per shape).
+template <int P, bool DG>
+int pick_cell_stride(int cpb, int nc) {
+  static std::mutex mu;
+  static std::map<long long, int> cache;
+  const long long key = (long long)cpb * 4096 + nc;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  const int base = cell_min_elems<P, DG>();
+  int best = base, best_cost = -1;
+  for (int cs = base; cs < base + 32; ++cs) {
+    const int c = layout_conflicts<P>(cpb, nc, cs);
+    if (best_cost < 0 || c < best_cost) {
+      best = cs;
+      best_cost = c;
+    }
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = best;
+  return best;
+}
+
+// Greedy assignment of the block's lines of one sweep direction (mode 0:
+// y-lines, start x + zs z; mode 1: x-lines, start p y + zs z, for every
+// virtual cell) to its threads, so that the lanes of a warp read and write
+// distinct banks: the k-th line whose start falls into bank r goes to lane r
+// of warp k, the lines left over (more than one per warp in a bank) to the
+// threads still without one.  Returns the shared-memory offset of the
+// thread's line start, or -1 for none.  scr: 34 + 2 blockDim.x ints of
+// scratch; every thread of the block calls it.
+template <int P>
+__device__ int assign_line(int* scr, int nv, int cs, int mode) {
+  constexpr int P2 = P * P, ZS = lay_zs<P>();
+  const int nthr = blockDim.x, tid = threadIdx.x, nw = nthr >> 5;
+  int* cnt = scr;
+  int* tab = scr + 34;
+  int* ovf = tab + nthr;
+  for (int i = tid; i < 34; i += nthr) scr[i] = 0;
+  tab[tid] = -1;
+  __syncthreads();
+  for (int i = tid; i < nv * P2; i += nthr) {
+    const int v = i / P2, m = i - v * P2;
+    const int a = m % P, b = m / P;
+    const int st = v * cs + (mode == 0 ? a + ZS * b : P * a + ZS * b);
+    const int r = st & 31;
+    const int k = atomicAdd(&cnt[r], 1);
+    if (k < nw)
+      tab[(k << 5) + r] = st;
+    else
+      ovf[atomicAdd(&scr[32], 1)] = st;
+  }
+  __syncthreads();
+  int my = tab[tid];
+  if (my < 0) {
+    const int j = atomicAdd(&scr[33], 1);
+    if (j < scr[32]) my = ovf[j];
+  }
+  __syncthreads();
+  return my;
 }
 
 // One face of the own cell (axis D a runtime value), SIPG (Eq. 6, mirror
@@ -89,9 +218,13 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
   constexpr int GV = S ? T_GV1 : T_GV0;
   constexpr int GD = S ? T_GD1 : T_GD0;
   const int t = ta + P * tb;
-  // point (l, ta, tb) of the own line normal to D is n0 + l * ls
+  // point (l, ta, tb) of the own line normal to D: n0 + l * ls in the nodal
+  // vectors, s0 + l * ss in the shared arrays
+  constexpr int ZS = lay_zs<P>();
   const int ls = D == 0 ? 1 : (D == 1 ? P : P2);
   const int n0 = D == 0 ? P * t : (D == 1 ? ta + P2 * tb : t);
+  const int ss = D == 0 ? 1 : (D == 1 ? P : ZS);
+  const int s0 = D == 0 ? P * ta + ZS * tb : (D == 1 ? ta + ZS * tb : t);
   const int cD = D == 0 ? cx : (D == 1 ? cy : cz);
   const int f = a.face_off[D] + cx + (D == 0 ? S : 0) +
                 (a.n[0] + (D == 0)) *
@@ -109,7 +242,7 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
   T uo = T(0), so = T(0);
 #pragma unroll
   for (int l = 0; l < P; ++l) {
-    const T u = U[n0 + l * ls];
+    const T u = U[s0 + l * ss];
     uo = fma(tv<T, P, GV>(l), u, uo);
     so = fma(tv<T, P, GD>(l), u, so);
   }
@@ -242,7 +375,7 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
   if (own) {
 #pragma unroll
     for (int l = 0; l < P; ++l) {
-      T& y = Aq[n0 + l * ls];
+      T& y = Aq[s0 + l * ss];
       y = fma(tv<T, P, GV>(l), vo, fma(tv<T, P, GD>(l), c0o, y));
     }
   }
@@ -356,34 +489,40 @@ __host__ __device__ constexpr size_t stage_g_bytes(int cpb) {
   return (size_t)cpb * 6 * P * P * P * sizeof(T);
 }
 // offset of the staging buffers in the dynamic shared memory (16-aligned)
-template <int P, typename T, bool DG>
-__host__ __device__ constexpr size_t stage_offset(int cpb, int ncols) {
-  return (((size_t)(cpb * ncols + 1) * cell_smem_elems<T, P, DG>() +
-           table_smem_elems<P>()) * sizeof(T) + 15) / 16 * 16;
+template <int P, typename T>
+__host__ __device__ constexpr size_t stage_offset(int cpb, int ncols, int cs) {
+  return (((size_t)(cpb * ncols + 1) * cs + table_smem_elems<P>()) *
+              sizeof(T) + 15) / 16 * 16;
 }
 
 // Work decomposition: a block owns `cpb` cells and `ncols` right-hand-side
 // columns; each (cell, column) pair is a virtual cell worked on by p*p
-// threads (thread = one line of each sweep).  The block is padded to whole
-// warps; padding threads work on a dummy virtual cell and write nothing to
-// global memory.  Columns of one cell are adjacent threads, so batched
-// vectors [N][R] are read coalesced and the geometry of a cell is loaded
-// once per point for all its columns (same address across the warp).
+// threads.  A thread owns one z-line of its virtual cell (gather, the
+// quadrature-point operation, scatter); the y- and x-lines of the block's
+// cells are dealt to its threads by assign_line so that the lanes of a warp
+// use distinct shared-memory banks.  The block is padded to whole warps;
+// padding threads work on a dummy virtual cell and write nothing to global
+// memory.  Columns of one cell are adjacent threads, so batched vectors
+// [N][R] are read coalesced and the geometry of a cell is loaded once per
+// point for all its columns (same address across the warp).
 // STAGE (float, curved, one column): the cells' stored geometry is staged
 // through shared memory by bulk copies (see stage_g_bytes) instead of
 // per-thread loads; a block's successive cell groups alternate between two
 // buffers, each completed on its own mbarrier.
 template <int P, typename T, bool DG, bool CURVED, bool STAGE = false>
 __global__ void k_apply(const ApplyArgs<T> a) {
-  constexpr int P2 = P * P, P3 = P2 * P;
+  constexpr int P2 = P * P, P3 = P2 * P, ZS = lay_zs<P>(), AR = lay_arr<P>();
   // float geometry is prefetched into registers during the gather (the float
   // apply is latency-bound) unless it is staged; float64 is bound by the
   // FP64 pipe instead
   constexpr bool PREFETCH = !STAGE && CURVED && sizeof(T) == 4 && P <= 7;
+  // 32-bit values: y- and x-lines dealt by bank (64-bit accesses keep the
+  // thread's own lines)
+  constexpr bool DEAL = sizeof(T) == 4;
   static_assert(!STAGE || CURVED, "staging is for stored geometry");
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
-  const int cpb = a.cpb, nc = a.ncols;
+  const int cpb = a.cpb, nc = a.ncols, cs = a.cs;
   const int items = cpb * nc * P2;
   const int tid = threadIdx.x;
   const bool item_ok = tid < items;
@@ -392,13 +531,12 @@ __global__ void k_apply(const ApplyArgs<T> a) {
   const int ta = rest % P, tb = (rest / P) % P;
   const int lc = item_ok ? rest / P2 : 0;
   const int v = item_ok ? lc * nc + rr : cpb * nc;  // dummy slot for padding
-  T* base = sm + (size_t)v * cell_smem_elems<T, P, DG>();
+  T* base = sm + (size_t)v * cs;
   T* Aq = base;
-  T* GX = base + P3;
-  T* GY = base + 2 * P3;
-  T* U = base + 3 * P3;   // DG: values at the Gauss points
-  T* FS = base + 4 * P3;  // DG: face scratch [8][p^2]
-  T* tabs = sm + (size_t)(cpb * nc + 1) * cell_smem_elems<T, P, DG>();
+  T* U = base + 3 * AR;   // DG: values at the Gauss points
+  T* FS = base + 4 * AR;  // DG: face scratch [8][p^2]
+  const int own = v * cs + ta + P * tb;  // own z-line: own + ZS * z
+  T* tabs = sm + (size_t)(cpb * nc + 1) * cs;
   T* sS = tabs;
   T* sD = tabs + P2;
   T* sDphi = tabs + 2 * P2;
@@ -419,8 +557,21 @@ __global__ void k_apply(const ApplyArgs<T> a) {
     bulk_load(gbuf + (size_t)slot * cpb * 6 * P3,
               a.G + (size_t)c0 * 6 * P3, bytes, &bars[slot]);
   };
+  // the thread's y-line (offset yl, step p) and x-line (xl, step 1), -1:
+  // none; the assignment's scratch (apply_smem_bytes covers it) is free
+  // again when it returns
+  int yl, xl;
+  if constexpr (DEAL) {
+    int* scr = reinterpret_cast<int*>(sm);
+    yl = assign_line<P>(scr, cpb * nc, cs, 0);
+    xl = assign_line<P>(scr, cpb * nc, cs, 1);
+  } else {
+    yl = v * cs + ta + ZS * tb;
+    xl = v * cs + P * ta + ZS * tb;
+  }
+  const bool hy = yl >= 0, hx = xl >= 0;
   if constexpr (STAGE) {
-    const size_t off = stage_offset<P, T, DG>(cpb, nc);
+    const size_t off = stage_offset<P, T>(cpb, nc, cs);
     gbuf = reinterpret_cast<T*>(smraw + off);
     bars = reinterpret_cast<uint64_t*>(smraw + off +
                                        2 * stage_g_bytes<P, T>(cpb));
@@ -485,36 +636,42 @@ __global__ void k_apply(const ApplyArgs<T> a) {
     // ---- values at Gauss points: z (registers), y, x
     mv<T, P, T_S>(r, o);
 #pragma unroll
-    for (int z = 0; z < P; ++z) Aq[idx3<P>(ta, tb, z)] = o[z];
+    for (int z = 0; z < P; ++z) sm[own + ZS * z] = o[z];
     __syncthreads();
+    if (hy) {
 #pragma unroll
-    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(ta, j, tb)];
-    mv<T, P, T_S>(r, o);
+      for (int j = 0; j < P; ++j) r[j] = sm[yl + P * j];
+      mv<T, P, T_S>(r, o);
 #pragma unroll
-    for (int j = 0; j < P; ++j) Aq[idx3<P>(ta, j, tb)] = o[j];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(j, ta, tb)];
-    mv<T, P, T_S>(r, o);
-#pragma unroll
-    for (int j = 0; j < P; ++j) Aq[idx3<P>(j, ta, tb)] = o[j];
-    if constexpr (DG) {  // values at the Gauss points for the face terms
-#pragma unroll
-      for (int j = 0; j < P; ++j) U[idx3<P>(j, ta, tb)] = o[j];
+      for (int j = 0; j < P; ++j) sm[yl + P * j] = o[j];
     }
-    mv<T, P, T_D>(o, r);
+    __syncthreads();
+    if (hx) {
 #pragma unroll
-    for (int j = 0; j < P; ++j) GX[idx3<P>(j, ta, tb)] = r[j];
+      for (int j = 0; j < P; ++j) r[j] = sm[xl + j];
+      mv<T, P, T_S>(r, o);
+#pragma unroll
+      for (int j = 0; j < P; ++j) sm[xl + j] = o[j];
+      if constexpr (DG) {  // values at the Gauss points for the face terms
+#pragma unroll
+        for (int j = 0; j < P; ++j) sm[xl + 3 * AR + j] = o[j];
+      }
+      mv<T, P, T_D>(o, r);
+#pragma unroll
+      for (int j = 0; j < P; ++j) sm[xl + AR + j] = r[j];  // GX
+    }
     __syncthreads();
     // ---- reference gradient: y into GY, z kept in registers
+    if (hy) {
 #pragma unroll
-    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(ta, j, tb)];
-    mv<T, P, T_D>(r, o);
+      for (int j = 0; j < P; ++j) r[j] = sm[yl + P * j];
+      mv<T, P, T_D>(r, o);
 #pragma unroll
-    for (int j = 0; j < P; ++j) GY[idx3<P>(ta, j, tb)] = o[j];
+      for (int j = 0; j < P; ++j) sm[yl + 2 * AR + P * j] = o[j];  // GY
+    }
     T gz[P];
 #pragma unroll
-    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(ta, tb, j)];
+    for (int j = 0; j < P; ++j) r[j] = sm[own + ZS * j];
     mv<T, P, T_D>(r, gz);
     __syncthreads();
     // ---- quadrature-point operation t = G_q grad u (Eq. 12)
@@ -527,8 +684,9 @@ __global__ void k_apply(const ApplyArgs<T> a) {
       const T wab = sw[ta] * sw[tb];
 #pragma unroll
       for (int qz = 0; qz < P; ++qz) {
-        const int q = idx3<P>(ta, tb, qz);
-        const T ux = GX[q], uy = GY[q], uz = gz[qz];
+        const int q = idx3<P>(ta, tb, qz);  // in the cell's global blocks
+        const int qs = own + ZS * qz;       // in shared memory
+        const T ux = sm[qs + AR], uy = sm[qs + 2 * AR], uz = gz[qz];
         const T kap = a.kcell ? a.kcell[(size_t)cc * P3 + q] : a.kappa;
         T tx, ty, tz;
         if constexpr (CURVED) {
@@ -553,31 +711,37 @@ __global__ void k_apply(const ApplyArgs<T> a) {
           ty = wk * a.gs[1] * uy;
           tz = wk * a.gs[2] * uz;
         }
-        GX[q] = tx;
-        GY[q] = ty;
+        sm[qs + AR] = tx;
+        sm[qs + 2 * AR] = ty;
         r[qz] = tz;
       }
       mtv<T, P, T_D>(r, o);
 #pragma unroll
-      for (int j = 0; j < P; ++j) Aq[idx3<P>(ta, tb, j)] = o[j];
+      for (int j = 0; j < P; ++j) sm[own + ZS * j] = o[j];
     }
     __syncthreads();
     // ---- transposed derivative y (added), x (added) then S^T x, y, z
+    if (hy) {
 #pragma unroll
-    for (int j = 0; j < P; ++j) r[j] = GY[idx3<P>(ta, j, tb)];
-    mtv<T, P, T_D>(r, o);
+      for (int j = 0; j < P; ++j) r[j] = sm[yl + 2 * AR + P * j];
+      mtv<T, P, T_D>(r, o);
 #pragma unroll
-    for (int j = 0; j < P; ++j) Aq[idx3<P>(ta, j, tb)] += o[j];
+      for (int j = 0; j < P; ++j) sm[yl + P * j] += o[j];
+    }
     __syncthreads();
+    if (hx) {
 #pragma unroll
-    for (int j = 0; j < P; ++j) r[j] = GX[idx3<P>(j, ta, tb)];
-    mtv<T, P, T_D>(r, o);
+      for (int j = 0; j < P; ++j) r[j] = sm[xl + AR + j];
+      mtv<T, P, T_D>(r, o);
 #pragma unroll
-    for (int j = 0; j < P; ++j) o[j] += Aq[idx3<P>(j, ta, tb)];
+      for (int j = 0; j < P; ++j) o[j] += sm[xl + j];
+    }
     if constexpr (DG) {
       // ---- SIPG face terms (Eq. 6, Eq. 7), added at the Gauss points
+      if (hx) {
 #pragma unroll
-      for (int j = 0; j < P; ++j) Aq[idx3<P>(j, ta, tb)] = o[j];
+        for (int j = 0; j < P; ++j) sm[xl + j] = o[j];
+      }
       __syncthreads();
 #pragma unroll 1
       for (int D = 0; D < 3; ++D) {
@@ -591,21 +755,27 @@ __global__ void k_apply(const ApplyArgs<T> a) {
                                  sD, sw, ta, tb);
       }
       __syncthreads();
+      if (hx) {
 #pragma unroll
-      for (int j = 0; j < P; ++j) o[j] = Aq[idx3<P>(j, ta, tb)];
+        for (int j = 0; j < P; ++j) o[j] = sm[xl + j];
+      }
     }
-    mtv<T, P, T_S>(o, r);
+    if (hx) {
+      mtv<T, P, T_S>(o, r);
 #pragma unroll
-    for (int j = 0; j < P; ++j) Aq[idx3<P>(j, ta, tb)] = r[j];
+      for (int j = 0; j < P; ++j) sm[xl + j] = r[j];
+    }
+    __syncthreads();
+    if (hy) {
+#pragma unroll
+      for (int j = 0; j < P; ++j) r[j] = sm[yl + P * j];
+      mtv<T, P, T_S>(r, o);
+#pragma unroll
+      for (int j = 0; j < P; ++j) sm[yl + P * j] = o[j];
+    }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(ta, j, tb)];
-    mtv<T, P, T_S>(r, o);
-#pragma unroll
-    for (int j = 0; j < P; ++j) Aq[idx3<P>(ta, j, tb)] = o[j];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < P; ++j) r[j] = Aq[idx3<P>(ta, tb, j)];
+    for (int j = 0; j < P; ++j) r[j] = sm[own + ZS * j];
     mtv<T, P, T_S>(r, o);
     // ---- scatter
     if constexpr (!DG) {
@@ -657,12 +827,18 @@ inline int default_cpb(int p) {
 
 template <int P, typename T, bool DG, bool STAGE = false>
 size_t apply_smem_bytes(int cpb, int ncols) {
+  const int cs = pick_cell_stride<P, DG>(cpb, ncols);
+  size_t bytes;
   if constexpr (STAGE)
-    return stage_offset<P, T, DG>(cpb, ncols) + 2 * stage_g_bytes<P, T>(cpb) +
-           2 * sizeof(uint64_t);
-  return ((size_t)(cpb * ncols + 1) * cell_smem_elems<T, P, DG>() +
-          table_smem_elems<P>()) *
-         sizeof(T);
+    bytes = stage_offset<P, T>(cpb, ncols, cs) + 2 * stage_g_bytes<P, T>(cpb) +
+            2 * sizeof(uint64_t);
+  else
+    bytes = ((size_t)(cpb * ncols + 1) * cs + table_smem_elems<P>()) *
+            sizeof(T);
+  // the line assignment's scratch (assign_line) at the start
+  const size_t nthr = ((size_t)cpb * ncols * P * P + 31) / 32 * 32;
+  const size_t scratch = (34 + 2 * nthr) * sizeof(int);
+  return bytes > scratch ? bytes : scratch;
 }
 
 // Resident blocks per SM of a launch shape (cached per shape).
@@ -699,6 +875,7 @@ void run_apply(ApplyArgs<T> a, int cpb, int ncols, cudaStream_t s) {
   constexpr int P2 = P * P;
   a.cpb = cpb;
   a.ncols = ncols;
+  a.cs = pick_cell_stride<P, DG>(cpb, ncols);
   const int threads = ((cpb * ncols * P2 + 31) / 32) * 32;
   const size_t smem = apply_smem_bytes<P, T, DG, STAGE>(cpb, ncols);
   auto kern = k_apply<P, T, DG, CURVED, STAGE>;
