@@ -61,9 +61,10 @@ __device__ __forceinline__ int idx3(int x, int y, int z) {
 // Shared-memory layout of a virtual cell.  Its arrays of p^3 values are
 // indexed x + p y + zs z, with the z stride padded (lay_zs) so that the
 // lines of all three sweep directions spread over the 32 banks; a cell holds
-// Aq, GX, GY (SIPG also U and the face scratch of 8 p^2 values) at multiples
-// of the array size lay_arr, and the virtual cells of a block follow each
-// other at a cell stride chosen per launch shape (pick_cell_stride).
+// Aq, GX, GY (SIPG also U) at multiples of the array size lay_arr, and the
+// virtual cells of a block follow each other at a cell stride chosen per
+// launch shape (pick_cell_stride).  The SIPG face scratch (pairs of face
+// arrays, face_gp) lies in a region of its own after the cells and tables.
 template <int P>
 __host__ __device__ constexpr int lay_zs() {
   return P == 2 ? 5 : P == 3 ? 11 : P == 4 ? 19 : P == 5 ? 29
@@ -79,7 +80,7 @@ __host__ __device__ constexpr int sidx(int x, int y, int z) {
 }
 template <int P, bool DG>
 __host__ __device__ constexpr int cell_min_elems() {
-  return (DG ? 4 : 3) * lay_arr<P>() + (DG ? 8 * P * P : 0);
+  return (DG ? 4 : 3) * lay_arr<P>();
 }
 template <int P>
 __host__ __device__ constexpr int table_smem_elems() {
@@ -208,13 +209,42 @@ __device__ int assign_line(int* scr, int nv, int cs, int mode) {
 // go through S^T x S^T to its face nodes and into the face buffer fb (slot
 // 2D: value part, 2D + 1: normal-slope part) for k_dg_face_add_t.  A
 // boundary face is one-sided; an interior lower face (S = 0) adds nothing.
+// The face scratch FS holds pairs of face arrays (two fields that the same
+// sweep takes, read by one 64-bit access): Q0 nodal (vn, dnn), then (vn,
+// c0n) of the neighbour's test terms; Q1 the sweeps' temporary; Q2 (uo,
+// un) for the tangential slopes; Q3, Q4 the tangential test-slope factors
+// (own, neighbour) along a and b.
+template <typename T>
+struct PairOf {
+  using type = float2;
+};
+template <>
+struct PairOf<double> {
+  using type = double2;
+};
+template <typename T>
+using pair_t = typename PairOf<T>::type;
+template <typename T>
+__device__ __forceinline__ pair_t<T> mkpair(T x, T y) {
+  pair_t<T> r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+constexpr int kFacePairs = 5;
+
 template <int P, typename T, bool CURVED, int S>
 __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
                                         bool active, int cx, int cy, int cz,
-                                        const T* U, T* Aq, T* FS, const T* sS,
-                                        const T* sD, const T* sw, int ta,
-                                        int tb) {
+                                        const T* U, T* Aq, pair_t<T>* FS,
+                                        const T* sS, const T* sD, const T* sw,
+                                        int ta, int tb) {
   constexpr int P2 = P * P, P3 = P2 * P;
+  pair_t<T>* Q0 = FS;
+  pair_t<T>* Q1 = FS + P2;
+  pair_t<T>* Q2 = FS + 2 * P2;
+  pair_t<T>* Q3 = FS + 3 * P2;
+  pair_t<T>* Q4 = FS + 4 * P2;
   constexpr int GV = S ? T_GV1 : T_GV0;
   constexpr int GD = S ? T_GD1 : T_GD0;
   const int t = ta + P * tb;
@@ -246,7 +276,7 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
     uo = fma(tv<T, P, GV>(l), u, uo);
     so = fma(tv<T, P, GD>(l), u, so);
   }
-  if constexpr (CURVED) FS[0 * P2 + t] = uo;
+  if constexpr (CURVED) Q2[t].x = uo;
   T un = T(0), q3 = T(0);
   if constexpr (S == 1) {
     // the upper neighbour's face layer and normal slope (nodal), then
@@ -262,8 +292,7 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
         if (l == 0) vn = u;
       }
     }
-    FS[2 * P2 + t] = vn;
-    FS[3 * P2 + t] = dnn;
+    Q0[t] = mkpair(vn, dnn);
     __syncthreads();
     T ra[P];
 #pragma unroll
@@ -271,20 +300,21 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
     T s2 = T(0), s3 = T(0);
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      s2 = fma(ra[j], FS[2 * P2 + j + P * tb], s2);
-      s3 = fma(ra[j], FS[3 * P2 + j + P * tb], s3);
+      const pair_t<T> q = Q0[j + P * tb];
+      s2 = fma(ra[j], q.x, s2);
+      s3 = fma(ra[j], q.y, s3);
     }
-    FS[6 * P2 + t] = s2;
-    FS[7 * P2 + t] = s3;
+    Q1[t] = mkpair(s2, s3);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < P; ++j) ra[j] = sS[tb * P + j];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      un = fma(ra[j], FS[6 * P2 + ta + P * j], un);
-      q3 = fma(ra[j], FS[7 * P2 + ta + P * j], q3);
+      const pair_t<T> q = Q1[ta + P * j];
+      un = fma(ra[j], q.x, un);
+      q3 = fma(ra[j], q.y, q3);
     }
-    if constexpr (CURVED) FS[2 * P2 + t] = un;
+    if constexpr (CURVED) Q2[t].y = un;
   }
   if constexpr (CURVED) __syncthreads();
   // flux at the face quadrature point (ta, tb)
@@ -310,11 +340,12 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
       T t1o = T(0), t2o = T(0), t1n = T(0), t2n = T(0);
 #pragma unroll
       for (int j = 0; j < P; ++j) {
-        t1o = fma(sD[ta * P + j], FS[j + P * tb], t1o);
-        t2o = fma(sD[tb * P + j], FS[ta + P * j], t2o);
+        const pair_t<T> qa = Q2[j + P * tb], qb = Q2[ta + P * j];
+        t1o = fma(sD[ta * P + j], qa.x, t1o);
+        t2o = fma(sD[tb * P + j], qb.x, t2o);
         if constexpr (S == 1) {
-          t1n = fma(sD[ta * P + j], FS[2 * P2 + j + P * tb], t1n);
-          t2n = fma(sD[tb * P + j], FS[2 * P2 + ta + P * j], t2n);
+          t1n = fma(sD[ta * P + j], qa.y, t1n);
+          t2n = fma(sD[tb * P + j], qb.y, t2n);
         }
       }
       // J^-1 n of the lower (L) and upper (R) cell, face-local components
@@ -348,12 +379,8 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
     c0o = cg * gvD;
     c0n = cg * gnD;
     if constexpr (CURVED) {
-      FS[4 * P2 + t] = cg * go1;
-      FS[5 * P2 + t] = cg * go2;
-      if constexpr (S == 1) {
-        FS[6 * P2 + t] = cg * gn1;
-        FS[7 * P2 + t] = cg * gn2;
-      }
+      Q3[t] = mkpair(cg * go1, S == 1 ? cg * gn1 : T(0));
+      Q4[t] = mkpair(cg * go2, S == 1 ? cg * gn2 : T(0));
     }
   }
   // fold the tangential test slopes into the value parts (D^T at the face
@@ -363,11 +390,12 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      vo = fma(sD[j * P + ta], FS[4 * P2 + j + P * tb], vo);
-      vo = fma(sD[j * P + tb], FS[5 * P2 + ta + P * j], vo);
+      const pair_t<T> qa = Q3[j + P * tb], qb = Q4[ta + P * j];
+      vo = fma(sD[j * P + ta], qa.x, vo);
+      vo = fma(sD[j * P + tb], qb.x, vo);
       if constexpr (S == 1) {
-        vn = fma(sD[j * P + ta], FS[6 * P2 + j + P * tb], vn);
-        vn = fma(sD[j * P + tb], FS[7 * P2 + ta + P * j], vn);
+        vn = fma(sD[j * P + ta], qa.y, vn);
+        vn = fma(sD[j * P + tb], qb.y, vn);
       }
     }
   }
@@ -381,8 +409,7 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
   }
   // the neighbour's test terms to its face nodes: S^T along a, then b
   if constexpr (S == 1) {
-    FS[0 * P2 + t] = vn;
-    FS[1 * P2 + t] = c0n;
+    Q0[t] = mkpair(vn, c0n);
     __syncthreads();
     T ra[P];
 #pragma unroll
@@ -390,19 +417,20 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
     T s0 = T(0), s1 = T(0);
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      s0 = fma(ra[j], FS[j + P * tb], s0);
-      s1 = fma(ra[j], FS[P2 + j + P * tb], s1);
+      const pair_t<T> q = Q0[j + P * tb];
+      s0 = fma(ra[j], q.x, s0);
+      s1 = fma(ra[j], q.y, s1);
     }
-    FS[4 * P2 + t] = s0;
-    FS[5 * P2 + t] = s1;
+    Q1[t] = mkpair(s0, s1);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < P; ++j) ra[j] = sS[j * P + tb];
     T r0 = T(0), r1 = T(0);
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      r0 = fma(ra[j], FS[4 * P2 + ta + P * j], r0);
-      r1 = fma(ra[j], FS[5 * P2 + ta + P * j], r1);
+      const pair_t<T> q = Q1[ta + P * j];
+      r0 = fma(ra[j], q.x, r0);
+      r1 = fma(ra[j], q.y, r1);
     }
     if (pair) {
       T* fbn = a.fb + ((size_t)nb * 6 + 2 * D) * P2 * a.stride + col;
@@ -415,7 +443,8 @@ __device__ __forceinline__ void face_gp(const ApplyArgs<T>& a, int col, int D,
 template <int P, typename T, bool CURVED>
 __device__ __noinline__ void face_lower_gp(const ApplyArgs<T>& a, int col,
                                            int D, bool active, int cx, int cy,
-                                           int cz, const T* U, T* Aq, T* FS,
+                                           int cz, const T* U, T* Aq,
+                                           pair_t<T>* FS,
                                            const T* sS, const T* sD,
                                            const T* sw, int ta, int tb) {
   face_gp<P, T, CURVED, 0>(a, col, D, active, cx, cy, cz, U, Aq, FS, sS, sD,
@@ -488,11 +517,35 @@ template <int P, typename T>
 __host__ __device__ constexpr size_t stage_g_bytes(int cpb) {
   return (size_t)cpb * 6 * P * P * P * sizeof(T);
 }
-// offset of the staging buffers in the dynamic shared memory (16-aligned)
+// SIPG face scratch of a virtual cell, in pairs: kFacePairs face arrays,
+// the stride congruent to p^2 modulo the pairs per 128 bytes so that the
+// virtual cells' scratch follows on in bank order
 template <int P, typename T>
-__host__ __device__ constexpr size_t stage_offset(int cpb, int ncols, int cs) {
+__host__ __device__ constexpr int fs_stride() {
+  constexpr int m = 128 / (int)sizeof(pair_t<T>);
+  int st = kFacePairs * P * P;
+  while (st % m != (P * P) % m) ++st;
+  return st;
+}
+// offset of the face scratch (16-aligned), after the cells and the tables
+template <int P, typename T>
+__host__ __device__ constexpr size_t fs_offset(int cpb, int ncols, int cs) {
   return (((size_t)(cpb * ncols + 1) * cs + table_smem_elems<P>()) *
               sizeof(T) + 15) / 16 * 16;
+}
+// bytes of the cells, tables and (SIPG) face scratch
+template <int P, typename T, bool DG>
+__host__ __device__ constexpr size_t cells_bytes(int cpb, int ncols, int cs) {
+  return DG ? fs_offset<P, T>(cpb, ncols, cs) +
+                  (size_t)(cpb * ncols + 1) * fs_stride<P, T>() *
+                      sizeof(pair_t<T>)
+            : ((size_t)(cpb * ncols + 1) * cs + table_smem_elems<P>()) *
+                  sizeof(T);
+}
+// offset of the staging buffers in the dynamic shared memory (16-aligned)
+template <int P, typename T, bool DG>
+__host__ __device__ constexpr size_t stage_offset(int cpb, int ncols, int cs) {
+  return (cells_bytes<P, T, DG>(cpb, ncols, cs) + 15) / 16 * 16;
 }
 
 // Work decomposition: a block owns `cpb` cells and `ncols` right-hand-side
@@ -534,7 +587,10 @@ __global__ void k_apply(const ApplyArgs<T> a) {
   T* base = sm + (size_t)v * cs;
   T* Aq = base;
   T* U = base + 3 * AR;   // DG: values at the Gauss points
-  T* FS = base + 4 * AR;  // DG: face scratch [8][p^2]
+  // DG: face scratch (face_gp)
+  pair_t<T>* FS = reinterpret_cast<pair_t<T>*>(
+                      smraw + fs_offset<P, T>(cpb, nc, cs)) +
+                  (size_t)v * fs_stride<P, T>();
   const int own = v * cs + ta + P * tb;  // own z-line: own + ZS * z
   T* tabs = sm + (size_t)(cpb * nc + 1) * cs;
   T* sS = tabs;
@@ -571,7 +627,7 @@ __global__ void k_apply(const ApplyArgs<T> a) {
   }
   const bool hy = yl >= 0, hx = xl >= 0;
   if constexpr (STAGE) {
-    const size_t off = stage_offset<P, T>(cpb, nc, cs);
+    const size_t off = stage_offset<P, T, DG>(cpb, nc, cs);
     gbuf = reinterpret_cast<T*>(smraw + off);
     bars = reinterpret_cast<uint64_t*>(smraw + off +
                                        2 * stage_g_bytes<P, T>(cpb));
@@ -830,11 +886,10 @@ size_t apply_smem_bytes(int cpb, int ncols) {
   const int cs = pick_cell_stride<P, DG>(cpb, ncols);
   size_t bytes;
   if constexpr (STAGE)
-    bytes = stage_offset<P, T>(cpb, ncols, cs) + 2 * stage_g_bytes<P, T>(cpb) +
-            2 * sizeof(uint64_t);
+    bytes = stage_offset<P, T, DG>(cpb, ncols, cs) +
+            2 * stage_g_bytes<P, T>(cpb) + 2 * sizeof(uint64_t);
   else
-    bytes = ((size_t)(cpb * ncols + 1) * cs + table_smem_elems<P>()) *
-            sizeof(T);
+    bytes = cells_bytes<P, T, DG>(cpb, ncols, cs);
   // the line assignment's scratch (assign_line) at the start
   const size_t nthr = ((size_t)cpb * ncols * P * P + 31) / 32 * 32;
   const size_t scratch = (34 + 2 * nthr) * sizeof(int);
