@@ -10,7 +10,7 @@
 // at the face Gauss points (H is tau times the face mass in a basis as large
 // as the Gauss rule, so its inverse acts point by point; on a curved face
 // both sides see the same area element); it is zero on Dirichlet faces,
-// whose traces are data.  k_hdg_trace (one block per face) forms lambda,
+// whose traces are data.  k_hdg_trace (a few faces per block) forms lambda,
 // k_hdg_cell (a few cells per block) adds the cell integrals by sum
 // factorization (values at the Gauss points by S, reference derivatives by
 // the Gauss collocation matrix D, mapped by J^{-1}) and the six faces' terms
@@ -148,51 +148,96 @@ __device__ __forceinline__ int layer_node(int D, int s, int ja, int jb) {
   return ii[0] + P * (ii[1] + P * ii[2]);
 }
 
-// One block per face of direction D: lambda at the face Gauss points,
-//   lambda = sum_sides (q . n_out + tau u) / (tau * number of sides),
-// n_out the side's outward unit normal (+n for the cell below the face, -n
-// for the one above; n = e_D on Cartesian cells).
-template <int P, typename V>
-__global__ void k_hdg_trace(HdgArgs a, int D) {
-  using H = HT<V>;
-  using S = typename H::S;
-  constexpr int F = P * P, N = P * P * P;
-  __shared__ S sS[P * P];
-  __shared__ S lay[8 * F], tmp[8 * F];  // [side][q_x, q_y, q_z, u][F]
+// Faces of direction D per block of the trace kernel (two layers of 8 face
+// arrays each in static shared memory, under 48 KB).
+template <int P>
+constexpr int hdg_faces_per_block() {
+  return P <= 3 ? 16 : (P <= 5 ? 8 : 4);
+}
+
+// Where face fl of direction D sits: its lower (L) and upper (R) cells, and
+// whether its trace is data (a Dirichlet boundary face).
+struct HdgFace {
+  bool hasL, hasR, dir;
+  int cellL, cellR;
+};
+__device__ __forceinline__ HdgFace hdg_face(const HdgArgs& a, int D, int fl) {
   int m[3] = {a.n[0], a.n[1], a.n[2]};
   m[D] += 1;
-  const int fl = blockIdx.x;
   const int fc[3] = {fl % m[0], (fl / m[0]) % m[1], fl / (m[0] * m[1])};
-  const bool hasL = fc[D] >= 1, hasR = fc[D] < a.n[D];
-  const int side = hasL ? (hasR ? -1 : 2 * D + 1) : 2 * D;
-  const size_t f = (size_t)a.face_off[D] + fl;
-  if (side >= 0 && !((a.neumann >> side) & 1)) {  // Dirichlet: data, not x
-    for (int q = threadIdx.x; q < F; q += blockDim.x) a.lam[f * F + q] = 0.0;
-    return;
-  }
+  HdgFace h;
+  h.hasL = fc[D] >= 1;
+  h.hasR = fc[D] < a.n[D];
+  const int side = h.hasL ? (h.hasR ? -1 : 2 * D + 1) : 2 * D;
+  h.dir = side >= 0 && !((a.neumann >> side) & 1);
   int cL[3] = {fc[0], fc[1], fc[2]};
   cL[D] -= 1;
-  const int cellL = hasL ? cL[0] + a.n[0] * (cL[1] + a.n[1] * cL[2]) : 0;
-  const int cellR = hasR ? fc[0] + a.n[0] * (fc[1] + a.n[1] * fc[2]) : 0;
+  h.cellL = h.hasL ? cL[0] + a.n[0] * (cL[1] + a.n[1] * cL[2]) : 0;
+  h.cellR = h.hasR ? fc[0] + a.n[0] * (fc[1] + a.n[1] * fc[2]) : 0;
+  return h;
+}
+
+// Trace lambda at the Gauss points of the faces of direction D, a few faces
+// per block:
+//   lambda = sum_sides (q . n_out + tau u) / (tau * number of sides),
+// n_out the side's outward unit normal (+n for the cell below the face, -n
+// for the one above; n = e_D on Cartesian cells); zero on Dirichlet faces.
+template <int P, typename V>
+__global__ void __launch_bounds__(256) k_hdg_trace(HdgArgs a, int D) {
+  using H = HT<V>;
+  using S = typename H::S;
+  constexpr int F = P * P, N = P * P * P, C = hdg_faces_per_block<P>();
+  __shared__ S sS[P * P];
+  // [face][side][q_x, q_y, q_z, u][F]
+  __shared__ S lay[C * 8 * F], tmp[C * 8 * F];
+  int m[3] = {a.n[0], a.n[1], a.n[2]};
+  m[D] += 1;
+  const int nface = m[0] * m[1] * m[2];
+  const int fl0 = blockIdx.x * C;
+  // per face: the first x index of each side's four fields, -1 where that
+  // side is missing or the trace is data
+  __shared__ long long xoff[C][2];
+  __shared__ unsigned char fkind[C];  // bit 0: lower cell, 1: upper, 2: data
   for (int i = threadIdx.x; i < P * P; i += blockDim.x)
     sS[i] = H::s(H::d2v(c_tab64[P - 2].S[i]));
-  for (int t = threadIdx.x; t < 8 * F; t += blockDim.x) {
-    const int sf = t / F, j = t % F;  // side 0: lower cell, 1: upper cell
-    const int sd = sf / 4, fld = sf % 4;
-    const bool has = sd == 0 ? hasL : hasR;
-    const int loc = layer_node<P>(D, sd == 0 ? 1 : 0, j % P, j / P);
-    const double* xc = a.x + (size_t)(sd == 0 ? cellL : cellR) * 4 * N;
-    lay[t] = H::s(H::d2v(has ? xc[fld * N + loc] : 0.0));
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    unsigned char k = 4;
+    xoff[c][0] = xoff[c][1] = -1;
+    if (fl0 + c < nface) {
+      const HdgFace h = hdg_face(a, D, fl0 + c);
+      k = (h.hasL ? 1 : 0) | (h.hasR ? 2 : 0) | (h.dir ? 4 : 0);
+      if (!h.dir && h.hasL) xoff[c][0] = (long long)h.cellL * 4 * N;
+      if (!h.dir && h.hasR) xoff[c][1] = (long long)h.cellR * 4 * N;
+    }
+    fkind[c] = k;
   }
   __syncthreads();
-  sweep2<P, V>(sS, false, 0, lay, tmp, 8);
+  for (int t = threadIdx.x; t < C * 8 * F; t += blockDim.x) {
+    const int c = t / (8 * F), r = t - c * 8 * F;
+    const int sf = r / F, j = r - sf * F;  // side 0: lower cell, 1: upper
+    const int sd = sf / 4, fld = sf % 4;
+    const long long o = xoff[c][sd];
+    const int loc = layer_node<P>(D, sd == 0 ? 1 : 0, j % P, j / P);
+    lay[t] = H::s(H::d2v(o >= 0 ? a.x[o + fld * N + loc] : 0.0));
+  }
   __syncthreads();
-  sweep2<P, V>(sS, false, 1, tmp, lay, 8);
+  sweep2<P, V>(sS, false, 0, lay, tmp, 8 * C);
   __syncthreads();
-  const V tau = H::d2v(face_tau<P>(a, f));
-  const V inv = H::recip(H::d2v((hasL && hasR ? 2.0 : 1.0) *
-                                face_tau<P>(a, f)));
-  for (int q = threadIdx.x; q < F; q += blockDim.x) {
+  sweep2<P, V>(sS, false, 1, tmp, lay, 8 * C);
+  __syncthreads();
+  for (int t = threadIdx.x; t < C * F; t += blockDim.x) {
+    const int c = t / F, q = t - c * F;
+    if (fl0 + c >= nface) continue;
+    const int k = fkind[c];
+    const bool hasL = k & 1, hasR = k & 2;
+    const size_t f = (size_t)a.face_off[D] + fl0 + c;
+    if (k & 4) {  // Dirichlet: data, not x
+      a.lam[f * F + q] = 0.0;
+      continue;
+    }
+    const double tf = face_tau<P>(a, f);
+    const V tau = H::d2v(tf);
+    const V inv = H::recip(H::d2v((hasL && hasR ? 2.0 : 1.0) * tf));
     V nv[3] = {H::d2v(0.0), H::d2v(0.0), H::d2v(0.0)};
     if (a.gf) {
       for (int e = 0; e < 3; ++e) nv[e] = H::d2v(a.gf[(f * 4 + 1 + e) * F + q]);
@@ -202,7 +247,7 @@ __global__ void k_hdg_trace(HdgArgs a, int D) {
     V num = H::d2v(0.0);
     for (int sd = 0; sd < 2; ++sd) {
       if (!(sd == 0 ? hasL : hasR)) continue;
-      const S* L = lay + 4 * sd * F;
+      const S* L = lay + (c * 8 + 4 * sd) * F;
       const V qn = nv[0] * H::v(L[q]) + nv[1] * H::v(L[F + q]) +
                    nv[2] * H::v(L[2 * F + q]);
       num = num + (sd == 0 ? qn : V(-qn)) + tau * H::v(L[3 * F + q]);
@@ -431,7 +476,9 @@ void run_hdg(const Level& L, const HdgArgs& a, cudaStream_t s) {
     for (int D = 0; D < 3; ++D) {
       int m[3] = {L.n[0], L.n[1], L.n[2]};
       m[D] += 1;
-      k_hdg_trace<P, V><<<m[0] * m[1] * m[2], 64, 0, s>>>(a, D);
+      constexpr int CF = hdg_faces_per_block<P>();
+      k_hdg_trace<P, V><<<(m[0] * m[1] * m[2] + CF - 1) / CF, 256, 0, s>>>(
+          a, D);
       MFP_CHECK_CUDA(cudaGetLastError());
       note_launch();
     }
