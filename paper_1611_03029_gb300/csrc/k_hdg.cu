@@ -100,40 +100,56 @@ struct HT<df> {
   }
 };
 
-// out = M (or M^T) applied along `axis` of nf fields of p^3 values
-template <int P, typename V>
-__device__ void sweep3(const typename HT<V>::S* M, bool tr, int axis,
+#define HDG_STR2(x) #x
+#define HDG_STR(x) HDG_STR2(x)
+#define HDG_OUT_LOOP _Pragma(HDG_STR(unroll(P <= 4 ? P : 1)))
+
+// out = M (or M^T, TR) applied along AXIS of nf fields of p^3 values, one
+// line of p values per thread: its inputs are read once into registers and
+// the table entries at fixed offsets (broadcast to the warp).
+template <int P, typename V, int AXIS, bool TR>
+__device__ void sweep3(const typename HT<V>::S* M,
                        const typename HT<V>::S* in, typename HT<V>::S* out,
                        int nf) {
   using H = HT<V>;
-  constexpr int N = P * P * P;
-  const int st = axis == 0 ? 1 : (axis == 1 ? P : P * P);
-  for (int t = threadIdx.x; t < nf * N; t += blockDim.x) {
-    const int i = t % N;
-    const int ii = axis == 0 ? i % P : (axis == 1 ? (i / P) % P : i / (P * P));
-    const typename H::S* src = in + (t - i) + (i - ii * st);
-    typename H::Acc acc = H::zero();
-    for (int j = 0; j < P; ++j)
-      H::mac(acc, tr ? M[j * P + ii] : M[ii * P + j], src[j * st]);
-    out[t] = H::s(H::get(acc));
+  constexpr int N = P * P * P, P2 = P * P;
+  constexpr int st = AXIS == 0 ? 1 : (AXIS == 1 ? P : P2);
+  for (int l = threadIdx.x; l < nf * P2; l += blockDim.x) {
+    const int f = l / P2, r = l - f * P2;
+    const int base = f * N + (AXIS == 0 ? P * r
+                              : AXIS == 1 ? r % P + P2 * (r / P) : r);
+    typename H::S x[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) x[j] = in[base + j * st];
+    // unrolled over the outputs up to p = 4 (registers above; measured)
+    HDG_OUT_LOOP
+    for (int q = 0; q < P; ++q) {
+      typename H::Acc acc = H::zero();
+#pragma unroll
+      for (int j = 0; j < P; ++j)
+        H::mac(acc, TR ? M[j * P + q] : M[q * P + j], x[j]);
+      out[base + q * st] = H::s(H::get(acc));
+    }
   }
 }
 
-// the same on nf fields of p^2 face values (axis 0: a, 1: b)
-template <int P, typename V>
-__device__ void sweep2(const typename HT<V>::S* M, bool tr, int axis,
+// the same on nf fields of p^2 face values (AXIS 0: a, 1: b), one output
+// point per thread (the face fields are too few for a line per thread)
+template <int P, typename V, int AXIS, bool TR>
+__device__ void sweep2(const typename HT<V>::S* M,
                        const typename HT<V>::S* in, typename HT<V>::S* out,
                        int nf) {
   using H = HT<V>;
   constexpr int F = P * P;
-  const int st = axis == 0 ? 1 : P;
+  constexpr int st = AXIS == 0 ? 1 : P;
   for (int t = threadIdx.x; t < nf * F; t += blockDim.x) {
     const int i = t % F;
-    const int ii = axis == 0 ? i % P : i / P;
-    const typename H::S* src = in + (t - i) + (i - ii * st);
+    const int ii = AXIS == 0 ? i % P : i / P;
+    const typename H::S* src = in + (t - ii * st);
     typename H::Acc acc = H::zero();
+#pragma unroll
     for (int j = 0; j < P; ++j)
-      H::mac(acc, tr ? M[j * P + ii] : M[ii * P + j], src[j * st]);
+      H::mac(acc, TR ? M[j * P + ii] : M[ii * P + j], src[j * st]);
     out[t] = H::s(H::get(acc));
   }
 }
@@ -221,9 +237,9 @@ __global__ void __launch_bounds__(256) k_hdg_trace(HdgArgs a, int D) {
     lay[t] = H::s(H::d2v(o >= 0 ? a.x[o + fld * N + loc] : 0.0));
   }
   __syncthreads();
-  sweep2<P, V>(sS, false, 0, lay, tmp, 8 * C);
+  sweep2<P, V, 0, false>(sS, lay, tmp, 8 * C);
   __syncthreads();
-  sweep2<P, V>(sS, false, 1, tmp, lay, 8 * C);
+  sweep2<P, V, 1, false>(sS, tmp, lay, 8 * C);
   __syncthreads();
   for (int t = threadIdx.x; t < C * F; t += blockDim.x) {
     const int c = t / F, q = t - c * F;
@@ -336,11 +352,11 @@ __global__ void k_hdg_cell(HdgArgs a) {
   }
   __syncthreads();
   // values of the four fields at the Gauss points
-  sweep3<P, V>(sS, false, 0, A, B, 4 * C);
+  sweep3<P, V, 0, false>(sS, A, B, 4 * C);
   __syncthreads();
-  sweep3<P, V>(sS, false, 1, B, A, 4 * C);
+  sweep3<P, V, 1, false>(sS, B, A, 4 * C);
   __syncthreads();
-  sweep3<P, V>(sS, false, 2, A, B, 4 * C);
+  sweep3<P, V, 2, false>(sS, A, B, 4 * C);
   __syncthreads();
   const int st[3] = {1, P, P * P};
   // u rows and the mass part of the q rows
@@ -398,11 +414,11 @@ __global__ void k_hdg_cell(HdgArgs a) {
     }
     __syncthreads();
   }
-  sweep3<P, V>(sS, true, 2, A, B, 4 * C);
+  sweep3<P, V, 2, true>(sS, A, B, 4 * C);
   __syncthreads();
-  sweep3<P, V>(sS, true, 1, B, A, 4 * C);
+  sweep3<P, V, 1, true>(sS, B, A, 4 * C);
   __syncthreads();
-  sweep3<P, V>(sS, true, 0, A, B, 4 * C);
+  sweep3<P, V, 0, true>(sS, A, B, 4 * C);
   __syncthreads();
   // faces, one (direction, side) at a time for all C cells of the block
   for (int D = 0; D < 3; ++D) {
@@ -418,9 +434,9 @@ __global__ void k_hdg_cell(HdgArgs a) {
                           : 0.0));
       }
       __syncthreads();
-      sweep2<P, V>(sS, false, 0, ul, ut, C);
+      sweep2<P, V, 0, false>(sS, ul, ut, C);
       __syncthreads();
-      sweep2<P, V>(sS, false, 1, ut, ul, C);
+      sweep2<P, V, 1, false>(sS, ut, ul, C);
       __syncthreads();
       for (int tt = threadIdx.x; tt < C * F; tt += blockDim.x) {
         const int c = tt / F, q = tt - c * F;
@@ -449,9 +465,9 @@ __global__ void k_hdg_cell(HdgArgs a) {
         g[3 * F + q] = H::s(dA * tau * (lq - H::v(ul[tt])));     // <v, tau(lambda-u)>
       }
       __syncthreads();
-      sweep2<P, V>(sS, true, 1, gcf, gt, 4 * C);
+      sweep2<P, V, 1, true>(sS, gcf, gt, 4 * C);
       __syncthreads();
-      sweep2<P, V>(sS, true, 0, gt, gcf, 4 * C);
+      sweep2<P, V, 0, true>(sS, gt, gcf, 4 * C);
       __syncthreads();
       for (int tt = threadIdx.x; tt < C * F; tt += blockDim.x) {
         const int c = tt / F, j = tt - c * F;
