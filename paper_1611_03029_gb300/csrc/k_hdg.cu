@@ -104,31 +104,85 @@ struct HT<df> {
 #define HDG_STR(x) HDG_STR2(x)
 #define HDG_OUT_LOOP _Pragma(HDG_STR(unroll(P <= 4 ? P : 1)))
 
-// out = M (or M^T, TR) applied along AXIS of nf fields of p^3 values, one
-// line of p values per thread: its inputs are read once into registers and
-// the table entries at fixed offsets (broadcast to the warp).
-template <int P, typename V, int AXIS, bool TR>
-__device__ void sweep3(const typename HT<V>::S* M,
+// Even-odd split of S or S^T (TR), which are mirror-symmetric
+// (M[p-1-q][p-1-j] = M[q][j]): with h = p/2, e_j = x_j + x_{p-1-j} and
+// o_j = x_j - x_{p-1-j} (j < h),
+//   out_q = A_q + B_q, out_{p-1-q} = A_q - B_q (q < h), out_h = A_h (odd p),
+//   A_q = sum_j ae[q][j] e_j + am[q] x_h,  B_q = sum_j bo[q][j] o_j,
+// ae = (M[q][j] + M[q][p-1-j]) / 2, bo = (M[q][j] - M[q][p-1-j]) / 2 and
+// am = M[q][h] (odd p): the sweep takes (h + p%2)(h + 1) + h^2 multiply-adds
+// per line instead of p^2.  Table layout: ae [h + p%2][h], am [h + p%2],
+// bo [h][h].
+template <int P>
+constexpr int eo_elems() {
+  return (P / 2 + P % 2) * (P / 2) + (P / 2 + P % 2) + (P / 2) * (P / 2);
+}
+template <int P, typename V, bool TR>
+__device__ __forceinline__ void load_eo(typename HT<V>::S* E) {
+  using H = HT<V>;
+  constexpr int Hh = P / 2, MC = Hh + P % 2;
+  const double* S = c_tab64[P - 2].S;
+  auto M = [&](int q, int j) { return TR ? S[j * P + q] : S[q * P + j]; };
+  for (int i = threadIdx.x; i < eo_elems<P>(); i += blockDim.x) {
+    double v;
+    if (i < MC * Hh) {
+      const int q = i / Hh, j = i % Hh;
+      v = 0.5 * (M(q, j) + M(q, P - 1 - j));
+    } else if (i < MC * Hh + MC) {
+      v = P % 2 ? M(i - MC * Hh, Hh) : 0.0;
+    } else {
+      const int r = i - MC * Hh - MC, q = r / Hh, j = r % Hh;
+      v = 0.5 * (M(q, j) - M(q, P - 1 - j));
+    }
+    E[i] = H::s(H::d2v(v));
+  }
+}
+
+// out = M applied along AXIS of nf fields of p^3 values (M = S or S^T as
+// the even-odd table E holds it), one line of p values per thread: its
+// inputs are read once into registers and the table entries at fixed
+// offsets (broadcast to the warp).
+template <int P, typename V, int AXIS>
+__device__ void sweep3(const typename HT<V>::S* E,
                        const typename HT<V>::S* in, typename HT<V>::S* out,
                        int nf) {
   using H = HT<V>;
   constexpr int N = P * P * P, P2 = P * P;
+  constexpr int Hh = P / 2, MC = Hh + P % 2;
   constexpr int st = AXIS == 0 ? 1 : (AXIS == 1 ? P : P2);
+  const typename H::S* am = E + MC * Hh;
+  const typename H::S* bo = am + MC;
   for (int l = threadIdx.x; l < nf * P2; l += blockDim.x) {
     const int f = l / P2, r = l - f * P2;
     const int base = f * N + (AXIS == 0 ? P * r
                               : AXIS == 1 ? r % P + P2 * (r / P) : r);
-    typename H::S x[P];
+    typename H::S x[P], e[Hh], o[Hh];
 #pragma unroll
     for (int j = 0; j < P; ++j) x[j] = in[base + j * st];
-    // unrolled over the outputs up to p = 4 (registers above; measured)
-    HDG_OUT_LOOP
-    for (int q = 0; q < P; ++q) {
-      typename H::Acc acc = H::zero();
 #pragma unroll
-      for (int j = 0; j < P; ++j)
-        H::mac(acc, TR ? M[j * P + q] : M[q * P + j], x[j]);
-      out[base + q * st] = H::s(H::get(acc));
+    for (int j = 0; j < Hh; ++j) {
+      const V xa = H::v(x[j]), xb = H::v(x[P - 1 - j]);
+      e[j] = H::s(xa + xb);
+      o[j] = H::s(xa - xb);
+    }
+    // unrolled over the outputs up to p = 4 (measured faster than 5)
+    HDG_OUT_LOOP
+    for (int q = 0; q < MC; ++q) {
+      typename H::Acc sa = H::zero();
+#pragma unroll
+      for (int j = 0; j < Hh; ++j) H::mac(sa, E[q * Hh + j], e[j]);
+      if constexpr (P % 2 == 1) H::mac(sa, am[q], x[Hh]);
+      const V A = H::get(sa);
+      if (q < Hh) {
+        typename H::Acc sb = H::zero();
+#pragma unroll
+        for (int j = 0; j < Hh; ++j) H::mac(sb, bo[q * Hh + j], o[j]);
+        const V B = H::get(sb);
+        out[base + q * st] = H::s(A + B);
+        out[base + (P - 1 - q) * st] = H::s(A - B);
+      } else {
+        out[base + q * st] = H::s(A);
+      }
     }
   }
 }
@@ -319,6 +373,7 @@ __global__ void k_hdg_cell(HdgArgs a) {
   using S = typename H::S;
   constexpr int F = P * P, N = P * P * P, C = hdg_cells_per_block<P>();
   __shared__ S sS[P * P], sD[P * P];
+  __shared__ S sE[eo_elems<P>()], sET[eo_elems<P>()];  // S, S^T even-odd
   __shared__ S sW3[P * P * P], sW2[P * P];  // w_q det J (Cartesian), w_a w_b
   __shared__ double sw[P];
   extern __shared__ __align__(16) unsigned char hraw[];
@@ -333,6 +388,8 @@ __global__ void k_hdg_cell(HdgArgs a) {
     sS[i] = H::s(H::d2v(c_tab64[P - 2].S[i]));
     sD[i] = H::s(H::d2v(c_tab64[P - 2].D[i]));
   }
+  load_eo<P, V, false>(sE);
+  load_eo<P, V, true>(sET);
   for (int i = threadIdx.x; i < P; i += blockDim.x) sw[i] = c_tab64[P - 2].w[i];
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     const double* w = c_tab64[P - 2].w;
@@ -352,11 +409,11 @@ __global__ void k_hdg_cell(HdgArgs a) {
   }
   __syncthreads();
   // values of the four fields at the Gauss points
-  sweep3<P, V, 0, false>(sS, A, B, 4 * C);
+  sweep3<P, V, 0>(sE, A, B, 4 * C);
   __syncthreads();
-  sweep3<P, V, 1, false>(sS, B, A, 4 * C);
+  sweep3<P, V, 1>(sE, B, A, 4 * C);
   __syncthreads();
-  sweep3<P, V, 2, false>(sS, A, B, 4 * C);
+  sweep3<P, V, 2>(sE, A, B, 4 * C);
   __syncthreads();
   const int st[3] = {1, P, P * P};
   // u rows and the mass part of the q rows
@@ -414,11 +471,11 @@ __global__ void k_hdg_cell(HdgArgs a) {
     }
     __syncthreads();
   }
-  sweep3<P, V, 2, true>(sS, A, B, 4 * C);
+  sweep3<P, V, 2>(sET, A, B, 4 * C);
   __syncthreads();
-  sweep3<P, V, 1, true>(sS, B, A, 4 * C);
+  sweep3<P, V, 1>(sET, B, A, 4 * C);
   __syncthreads();
-  sweep3<P, V, 0, true>(sS, A, B, 4 * C);
+  sweep3<P, V, 0>(sET, A, B, 4 * C);
   __syncthreads();
   // faces, one (direction, side) at a time for all C cells of the block
   for (int D = 0; D < 3; ++D) {

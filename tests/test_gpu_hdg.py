@@ -18,6 +18,8 @@ pytestmark = pytest.mark.gpu
     (2, (3, 2, 4), (0, 2, 4), (-1.0, 1.0), 1.0),
     (3, (2, 3, 2), (1, 5), (-0.5, 2.0), 2.0),
     (4, (2, 2, 3), (0, 2, 4), (-1.0, 1.0), 1.0),
+    # 9 cells: the last block of 4 cells (and of 8 faces) is ragged
+    (4, (3, 1, 3), (1,), (0.0, 1.0), 1.5),
     (6, (2, 1, 2), (3,), (0.0, 1.0), 0.5),
     (8, (1, 2, 1), (), (0.0, 1.0), 1.0)])
 def test_hdg_apply_matches_oracle(mfp, k, n, sides, box, kappa):
@@ -73,6 +75,7 @@ def test_hdg_apply_full_size_sampled_cells(mfp):
     (2, (2, 3, 2), (0, 2, 4), "sine"),
     (3, (2, 2, 3), (1,), "nodes"),
     (4, (2, 2, 2), (0, 3), "sine"),
+    (4, (3, 2, 1), (2,), "nodes"),
     (5, (2, 1, 2), (), "nodes")])
 def test_hdg_apply_curved_variable_coefficient(mfp, k, n, sides, mapping):
     # curved cells (w det J and J^{-1} per point, dA and the normal per face
