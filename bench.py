@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=N_CELLS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch-list", default="fp64", choices=["fp64", "mixed"],
+                    help="the step that the NVTX range timed_step marks (the "
+                         "timed FP64 steps, or one mixed-precision step), for "
+                         "a launch list under ncu --nvtx-include")
     ap.add_argument("--no-extras", action="store_true",
                     help="leave the other workloads out of the contract line")
     ap.add_argument("--workload", default="solve",
@@ -515,7 +519,7 @@ def run_ours(args):
         for i in range(args.steps):
             flush.fill_(float(i))
             starts[i].record(stream)
-            its = step(ops, mark=True)
+            its = step(ops, mark=args.launch_list == "fp64")
             ends[i].record(stream)
         torch.cuda.synchronize()
         if dist:
@@ -531,7 +535,7 @@ def run_ours(args):
             step_sequential(native)
             step(mixed)
             step(native)
-        its_mixed = step(mixed)
+        its_mixed = step(mixed, mark=args.launch_list == "mixed")
         mixed_ts = timed_runs(lambda: step(mixed), stream, 20, flush)
         its_native = step(native)
         native_ts = timed_runs(lambda: step(native), stream, 5, flush)
