@@ -225,7 +225,7 @@ def fp64_pipe_peak_tflops(sm_count, sm_mhz):
 # DRAM traffic (read + write) per launch of the dominant kernel from one ncu
 # capture, keyed by a hash of the sources it was compiled from; a kernel
 # changed since its capture reports null.
-TRAFFIC = {"a9df6cdbb879da26": 502.05e6}  # ncu, Q4 32^3 curved: k_apply_df + k_dg_face_add
+TRAFFIC = {"3952aaef1561c0d7": 499.2e6}  # ncu, Q4 32^3 curved: k_apply_df + k_dg_face_add
 
 
 def kernel_hash():
