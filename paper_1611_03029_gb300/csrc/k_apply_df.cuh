@@ -24,7 +24,11 @@
 // most 128 threads for p <= 5, 256 above), measured on 24^3..64^3 meshes
 // for k = 2..8: more resident warps hide the latency of the shared-memory
 // sweeps and the gathers, down to about 73 registers per thread; CG p >= 7
-// keeps its larger line arrays in registers.
+// keeps its larger line arrays in registers.  At p = 5, with one block per
+// cell group, the concurrent CG and SIPG solves of 32^3 curved cells
+// measured best at 6 (CG, 80 registers) and 8 (SIPG, 64) blocks: 60.7 ->
+// 58.9 ms per pair of solves (SIPG apply alone 0.399 -> 0.412 ms, its
+// solve's coarser levels faster; CG apply 0.181 -> 0.158 ms).
 
 namespace mfp {
 namespace {
@@ -572,8 +576,8 @@ template <int P>
 constexpr int df_max_threads() { return P <= 5 ? 128 : 256; }
 template <int P, bool DG>
 constexpr int df_min_blocks() {
-  if (DG) return P <= 3 ? 5 : (P <= 5 ? 7 : 2);
-  return P <= 5 ? 8 : (P == 6 ? 3 : 1);
+  if (DG) return P <= 3 ? 5 : (P == 4 ? 7 : (P == 5 ? 8 : 2));
+  return P <= 4 ? 8 : (P == 5 ? 6 : (P == 6 ? 3 : 1));
 }
 
 template <int P, bool DG>
