@@ -225,7 +225,7 @@ def fp64_pipe_peak_tflops(sm_count, sm_mhz):
 # DRAM traffic (read + write) per launch of the dominant kernel from one ncu
 # capture, keyed by a hash of the sources it was compiled from; a kernel
 # changed since its capture reports null.
-TRAFFIC = {"3952aaef1561c0d7": 499.2e6}  # ncu, Q4 32^3 curved: k_apply_df + k_dg_face_add
+TRAFFIC = {"4e61a7c9b224f910": 499.1e6}  # ncu, Q4 32^3 curved: k_apply_df + k_dg_face_add
 
 
 def kernel_hash():
