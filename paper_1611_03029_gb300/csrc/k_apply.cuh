@@ -459,15 +459,16 @@ __device__ __noinline__ void face_lower_gp(const ApplyArgs<T>& a, int col,
 // (blockIdx.y: cy, cz; blockIdx.z: column).  Float values are cheap to keep
 // in registers, so a thread takes the whole line and every load of it is in
 // flight at once (the double-float kernel works per node instead).
-// Resident blocks of 256 threads the registers must allow (the line loads
-// would take about 124 registers uncapped, two blocks per SM; three measured
-// 4 % faster at Q4; p >= 8 would spill at three).
-template <int P>
+// Resident blocks of 256 threads the registers must allow: float lines take
+// about 124 registers uncapped (two blocks per SM), three blocks measured 4 %
+// faster at Q4 and p >= 8 would spill at three; float64 lines need twice the
+// registers and stay uncapped.
+template <int P, typename T>
 constexpr int face_add_min_blocks() {
-  return P <= 7 ? 3 : 2;
+  return sizeof(T) == 4 ? (P <= 7 ? 3 : 2) : 1;
 }
 template <int P, typename T>
-__global__ void __launch_bounds__(256, face_add_min_blocks<P>())
+__global__ void __launch_bounds__(256, (face_add_min_blocks<P, T>()))
     k_dg_face_add_t(const ApplyArgs<T> a) {
   constexpr int P2 = P * P, P3 = P2 * P;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
