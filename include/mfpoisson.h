@@ -290,7 +290,9 @@ mfp_status mfp_vcycle(mfp_ctx* ctx, const double* r_dev, double* z_dev,
  * its own).  Synchronises `stream` once per iteration.  iters_host[n_rhs] and
  * relres_host[n_rhs] receive the iteration counts and final relative
  * residuals (may be NULL).  Returns MFP_ERR_NOT_CONVERGED if any column hit
- * max_it. */
+ * max_it.  The V-cycle runs as a CUDA graph, captured once per column count
+ * on a stream of the context and replayed on `stream`; the environment
+ * variable MFP_CUDA_GRAPHS=0 launches its kernels one by one instead. */
 mfp_status mfp_solve(mfp_ctx* ctx, const double* b_dev, double* x_dev,
                      int n_rhs, double rtol, int max_it, int* iters_host,
                      double* relres_host, void* stream);
